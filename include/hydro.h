@@ -1,0 +1,169 @@
+/*
+ * hydro.h -- C ABI of the B300 relativistic-hydrodynamics step library.
+ *
+ * The library advances the (3+1)D ideal relativistic hydrodynamic equations
+ * with a jet source, d_mu T^{mu nu} = S^nu (arXiv:1511.02137, Sec. 1, Eq. 1),
+ * T^{mu nu} = (e+p) u^mu u^nu - p g^{mu nu}, EOS p = e/3 (Fig. 3 caption), on a
+ * uniform Cartesian grid, by third-order Runge-Kutta steps (Sec. 1) of a
+ * finite-difference 7th-order WENO scheme (Sec. 1) applied component-wise to
+ * local Lax-Friedrichs split fluxes.  Jets are light-speed point sources
+ * (Eq. 2) losing energy at the rate of Eq. 3.
+ *
+ * Conventions shared by every entry point:
+ *  - Fields are 5 arrays of nx*ny*nz values each, x fastest, then y, then z
+ *    ("SoA"): conserved (E = T^00, M^x, M^y, M^z, R = n gamma) or primitive
+ *    (e, u^x, u^y, u^z, n) with u^i the spatial four-velocity.
+ *    Units: fm, fm/c, GeV/fm^3 (E, M, e), fm^-3 (R, n), GeV (T).
+ *  - Cell (i, j, k) has centre ((i + 1/2 - nx/2) dx, (j + 1/2 - ny/2) dx,
+ *    (k + 1/2 - nz/2) dx): the grid is centred on the origin.
+ *  - Every function returns a hydro_status and never aborts, prints or throws.
+ *  - Host buffers are owned by the caller and only used during the call.
+ *  - All device work is issued on the stream given in hydro_config; every
+ *    call that returns data synchronises that stream before returning.
+ *  - A context is not thread safe; use one context per thread.
+ */
+#ifndef HYDRO_H
+#define HYDRO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HYDRO_OK = 0,
+  HYDRO_EINVAL = 1,      /* bad argument or configuration */
+  HYDRO_ENOMEM = 2,      /* device allocation failed, or the given workspace is too small */
+  HYDRO_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+  HYDRO_EUNPHYSICAL = 4, /* NaN or Inf appeared in the state during a step */
+  HYDRO_ECFL = 5,        /* max signal speed * dt / dx exceeded cfl_limit */
+  HYDRO_ETIMEOUT = 6,    /* a bounded device-side wait expired */
+  HYDRO_ESTATE = 7       /* call out of order (e.g. hydro_step before hydro_set_initial) */
+} hydro_status;
+
+enum { HYDRO_FP64 = 0, HYDRO_FP32 = 1, HYDRO_MIXED = 2 };     /* hydro_config.precision */
+enum { HYDRO_OUTFLOW = 0, HYDRO_PERIODIC = 1 };              /* hydro_config.boundary */
+enum { HYDRO_PRIMITIVE = 0, HYDRO_CONSERVED = 1 };           /* field kinds */
+
+#define HYDRO_MAX_JETS 16
+
+/* Run configuration.  hydro_config_default() fills the paper's values. */
+typedef struct {
+  int32_t nx, ny, nz;   /* cells per axis, each >= 1 */
+  int32_t precision;    /* HYDRO_FP64: everything in FP64.
+                           HYDRO_FP32: storage and arithmetic in FP32.
+                           HYDRO_MIXED: FP64 storage, FP64 conserved-to-primitive recovery
+                           and RK3 accumulation; FP32 WENO weights, fluxes and divergence. */
+  int32_t boundary;     /* HYDRO_OUTFLOW (zero-gradient ghosts) or HYDRO_PERIODIC */
+  int32_t weno_order;   /* 7 (WENO7, Sec. 1) or 5 (WENO5, Sec. 1) */
+  double dx;            /* cell edge [fm] (0.1 in Fig. 3 caption) */
+  double dt;            /* time step [fm/c] (0.02 in Fig. 3 caption) */
+  double t0;            /* time of the initial state [fm/c] (1 in Sec. 2) */
+  double k_rad;         /* kappa_rad of Eq. 3 (4) */
+  double k_coll;        /* kappa_coll of Eq. 3 (2.5) */
+  double cr_over_cf;    /* C_R/C_F of Eq. 3 (1) */
+  double hbarc;         /* hbar c [GeV fm] (0.1973) */
+  double dof;           /* degrees of freedom in e = (pi^2/30) dof T^4/(hbar c)^3 (47.5) */
+  double e_floor;       /* floor on E in the primitive recovery [GeV/fm^3] */
+  double weno_eps;      /* epsilon of the WENO weights (1e-6) */
+  double cfl_limit;     /* hydro_step returns HYDRO_ECFL when max speed * dt/dx exceeds it; <= 0: off */
+  void* cuda_stream;    /* cudaStream_t for all device work; NULL = legacy default stream */
+  void* workspace;      /* device buffer of >= hydro_workspace_size() bytes, 256-byte aligned,
+                           owned by the caller and kept alive until hydro_destroy; NULL: the
+                           library allocates (cudaMalloc) and frees it itself */
+  size_t workspace_bytes;
+} hydro_config;
+
+typedef struct hydro_ctx hydro_ctx;
+
+/* Diagnostics of a context (hydro_get_diag). */
+typedef struct {
+  double t;                     /* time of the current state [fm/c] */
+  int64_t steps;                /* completed RK3 steps */
+  double max_speed;             /* largest spectral radius |lambda| over cells and axes at the
+                                   first stage of the last step (units of c) */
+  int64_t floor_hits;           /* cells whose primitive recovery needed a floor, all stages */
+  double dep_E;                 /* energy deposited by all jets, RK3-weighted, [GeV] */
+  double dep_M[3];              /* momentum deposited by all jets, [GeV] */
+  int32_t njet;
+  int32_t jet_cell[HYDRO_MAX_JETS][3]; /* cell where each jet deposited at the last stage, as
+                                          recorded by the device; -1 if it deposited nothing */
+  int32_t status;               /* first error status raised on the device since creation */
+} hydro_diag;
+
+/* Paper defaults (Sec. 1, Sec. 2, Fig. 3 caption) for an nx x ny x nz grid, FP64,
+ * outflow, WENO7.  Never fails. */
+void hydro_config_default(hydro_config* cfg, int32_t nx, int32_t ny, int32_t nz);
+
+/* Bytes of device workspace a context with this configuration needs: three
+ * state copies and one right-hand-side accumulator (5 fields each) plus a
+ * small diagnostics block.  HYDRO_EINVAL for an invalid configuration. */
+hydro_status hydro_workspace_size(const hydro_config* cfg, size_t* bytes);
+
+/* Validates cfg, sets up device memory and returns a new context in *out.
+ * HYDRO_EINVAL: invalid configuration (non-positive sizes or steps, unknown
+ * enum values, workspace not aligned); HYDRO_ENOMEM: workspace too small or
+ * cudaMalloc failed; HYDRO_ECUDA: other CUDA failure.  On failure *out = NULL. */
+hydro_status hydro_create(const hydro_config* cfg, hydro_ctx** out);
+
+/* Uploads the state at t0 from host memory.  kind = HYDRO_PRIMITIVE takes
+ * (e, u^x, u^y, u^z, n) and converts to conserved variables on the device
+ * (Eq. 1 with p = e/3); kind = HYDRO_CONSERVED takes (E, M^x, M^y, M^z, R).
+ * host5 holds 5*nx*ny*nz doubles (pinned memory makes the copy asynchronous).
+ * Resets time to t0 and the step counter to 0; keeps the jets.
+ * HYDRO_EINVAL: NULL pointer, unknown kind, or e < 0 / non-finite values. */
+hydro_status hydro_set_initial(hydro_ctx* ctx, int32_t kind, const double* host5);
+
+/* Adds a jet that starts at x0 [fm] at time t_start [fm/c] and flies at light
+ * speed along dir (normalised inside: n = dir/|dir|).  It deposits energy at
+ * the rate of Eq. 3 and momentum n times that (Eq. 2) into the cell that holds
+ * it at each RK stage time.  *jet_id (may be NULL) receives its index.
+ * HYDRO_EINVAL: zero or non-finite direction, or HYDRO_MAX_JETS reached. */
+hydro_status hydro_add_jet(hydro_ctx* ctx, const double x0[3], const double dir[3], double t_start,
+                           int32_t* jet_id);
+
+/* Advances nsteps SSP-RK3 steps of length dt (Shu-Osher form, Sec. 1):
+ *   U1 = U + dt L(U, t),  U2 = 3/4 U + 1/4 (U1 + dt L(U1, t+dt)),
+ *   U  = 1/3 U + 2/3 (U2 + dt L(U2, t+dt/2)),
+ * with L = -div F + S.  Synchronises the stream at the end and returns the
+ * first error raised: HYDRO_EUNPHYSICAL (NaN/Inf), HYDRO_ECFL, HYDRO_ECUDA;
+ * HYDRO_ESTATE before hydro_set_initial; HYDRO_EINVAL for nsteps < 0. */
+hydro_status hydro_step(hydro_ctx* ctx, int32_t nsteps);
+
+/* Copies the current state to host memory as FP64 (FP32 storage is widened):
+ * kind = HYDRO_CONSERVED gives (E, M^x, M^y, M^z, R); kind = HYDRO_PRIMITIVE
+ * gives (e, u^x, u^y, u^z, n), recovered on the device in FP64 with the same
+ * closed form the step uses.  host5 holds 5*nx*ny*nz doubles. */
+hydro_status hydro_read_fields(hydro_ctx* ctx, int32_t kind, double* host5);
+
+/* Fills *out with the context's diagnostics (synchronises the stream). */
+hydro_status hydro_get_diag(hydro_ctx* ctx, hydro_diag* out);
+
+/* Per-kernel timing with CUDA events on the context's stream, for profiling.
+ * hydro_profile_enable(ctx, 1) starts recording (and clears the counters);
+ * hydro_profile_query returns, for kernel kind k (see HYDRO_KERNEL_*), the
+ * summed device time in ms and the launch count of the launches recorded so
+ * far (synchronises the stream).  HYDRO_EINVAL for an unknown kind. */
+enum {
+  HYDRO_KERNEL_SWEEP_X = 0,   /* x flux divergence into the RHS accumulator */
+  HYDRO_KERNEL_SWEEP_Y = 1,   /* y flux divergence added to the RHS accumulator */
+  HYDRO_KERNEL_SWEEP_Z = 2,   /* z flux divergence + jet source + RK3 stage combination */
+  HYDRO_KERNEL_OTHER = 3,     /* initial-state conversion, field read-back */
+  HYDRO_KERNEL_COUNT = 4
+};
+hydro_status hydro_profile_enable(hydro_ctx* ctx, int32_t on);
+hydro_status hydro_profile_query(hydro_ctx* ctx, int32_t kind, double* total_ms, int64_t* launches);
+
+/* Releases the context and any memory the library allocated.  NULL is a no-op. */
+void hydro_destroy(hydro_ctx* ctx);
+
+/* Static string naming a status code. */
+const char* hydro_status_string(hydro_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HYDRO_H */

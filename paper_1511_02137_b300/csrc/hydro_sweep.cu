@@ -1,0 +1,392 @@
+// Directional flux sweeps of one RK3 stage (arXiv:1511.02137, Sec. 1, Eqs. 1-3).
+//
+// A stage evaluates L(U) = -sum_d (Fhat_{i+1/2} - Fhat_{i-1/2})/dx + S and
+// combines it with the step's start state.  It runs as three sweeps, one per
+// axis, each a tiled kernel:
+//
+//   phase 1  stage a halo-padded tile of cells into shared memory: load the
+//            5 conserved fields (coalesced along x), recover primitives in
+//            closed form, and keep U, the half physical flux F_d/2 and the
+//            spectral radius rho_d of every cell;
+//   phase 2  one thread per interface: alpha = max rho_d over the interface's
+//            stencil, local Lax-Friedrichs split f_pm = F/2 +- alpha U/2, and
+//            component-wise WENO reconstruction of f+ (left-biased) and f-
+//            (right-biased, mirrored); Fhat = f+ + f-;
+//   phase 3  one thread per cell: the flux difference goes into the
+//            right-hand-side accumulator (x: write, y: add); the z sweep adds
+//            the jet source at the jet cells and writes the stage combination
+//            a U0 + b (U + dt L) in storage precision.
+//
+// Ghost cells are never stored: halo loads clamp the index (outflow,
+// zero-gradient) or wrap it (periodic).  The x sweep of each stage counts
+// primitive-recovery floors; at the first stage of a step every sweep folds
+// its spectral radii into the step's maximum signal speed with a warp-shuffle
+// reduction and one atomic per block.
+#include <cstdint>
+
+#include "hydro.h"
+#include "hydro_internal.h"
+#include "hydro_math.cuh"
+
+namespace hydro {
+
+template <int PREC> struct Types;
+template <> struct Types<HYDRO_FP64> { using Store = double; using Prim = double; using Flux = double; };
+template <> struct Types<HYDRO_FP32> { using Store = float; using Prim = float; using Flux = float; };
+template <> struct Types<HYDRO_MIXED> { using Store = double; using Prim = double; using Flux = float; };
+
+// Tile shape per sweep axis: SEG cells along the sweep axis, LANES lines.  The
+// lines of the y and z sweeps run along x so that loads stay coalesced.
+template <int DIR> struct Tile;
+template <> struct Tile<0> { static constexpr int SEG = 64, LANES = 4; };
+template <> struct Tile<1> { static constexpr int SEG = 16, LANES = 16; };
+template <> struct Tile<2> { static constexpr int SEG = 16, LANES = 16; };
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ int map_along(int i, int n, int periodic) {
+  if (periodic) {
+    i %= n;
+    return i < 0 ? i + n : i;
+  }
+  return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+// Block-wide max of the spectral radius and sum of floor hits, published with
+// one atomic each.  Must be reached by every thread of the block.
+__device__ __forceinline__ void publish_block(double vmax, unsigned hits, DevDiag* d, bool speed, bool floors) {
+  __shared__ double wmax[kThreads / 32];
+  __shared__ unsigned whits[kThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    hits += __shfl_xor_sync(0xffffffffu, hits, o);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    wmax[w] = vmax;
+    whits[w] = hits;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    unsigned long long h = 0;
+    for (int i = 0; i < kThreads / 32; ++i) {
+      m = fmax(m, wmax[i]);
+      h += whits[i];
+    }
+    // non-negative doubles order like their bit patterns
+    if (speed) atomicMax(&d->vmax_bits, (unsigned long long)__double_as_longlong(m));
+    if (floors && h) atomicAdd(&d->floor_hits, h);
+  }
+}
+
+template <int PREC, int ORDER, int DIR, bool FINAL>
+__global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a) {
+  using Store = typename Types<PREC>::Store;
+  using Prim = typename Types<PREC>::Prim;
+  using F = typename Types<PREC>::Flux;
+  constexpr int SEG = Tile<DIR>::SEG;
+  constexpr int LANES = Tile<DIR>::LANES;
+  constexpr int G = (ORDER == 7) ? 4 : 3;   // halo width = half the interface stencil
+  constexpr int W = SEG + 2 * G;            // staged cells per line
+  constexpr int NCS = LANES * W;            // staged cells
+  constexpr int NIF = LANES * (SEG + 1);    // interfaces
+  constexpr int NC = LANES * SEG;           // updated cells
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  F* sU = reinterpret_cast<F*>(smem_raw);   // [5][NCS] conserved
+  F* sF = sU + 5 * NCS;                     // [5][NCS] F_d / 2
+  F* sR = sF + 5 * NCS;                     // [NCS]    rho_d
+  F* sH = sR + NCS;                         // [5][NIF] numerical flux
+
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const size_t N = (size_t)nx * ny * nz;
+  int a0, l0, fixed, n_along, n_lane;
+  if (DIR == 0) {
+    a0 = blockIdx.x * SEG; l0 = blockIdx.y * LANES; fixed = blockIdx.z; n_along = nx; n_lane = ny;
+  } else if (DIR == 1) {
+    l0 = blockIdx.x * LANES; a0 = blockIdx.y * SEG; fixed = blockIdx.z; n_along = ny; n_lane = nx;
+  } else {
+    l0 = blockIdx.x * LANES; a0 = blockIdx.y * SEG; fixed = blockIdx.z; n_along = nz; n_lane = nx;
+  }
+  auto offset = [&](int along, int lane) -> size_t {
+    if (DIR == 0) return ((size_t)fixed * ny + lane) * nx + along;
+    if (DIR == 1) return ((size_t)fixed * ny + along) * nx + lane;
+    return ((size_t)along * ny + fixed) * nx + lane;
+  };
+  // staged cell (lane, s) and interface/cell (lane, j) index maps; consecutive
+  // threads walk the contiguous (x) direction in every phase
+  auto sidx = [&](int lane, int s) { return DIR == 0 ? lane * W + s : s * LANES + lane; };
+  auto hidx = [&](int lane, int j) { return DIR == 0 ? lane * (SEG + 1) + j : j * LANES + lane; };
+
+  // ---------------- phase 1: stage cells, primitives, half fluxes, rho
+  const Store* __restrict__ U = static_cast<const Store*>(a.U);
+  const Prim e_floor = (Prim)a.e_floor;
+  double vmax = 0.0;
+  unsigned hits = 0;
+  for (int c = threadIdx.x; c < NCS; c += kThreads) {
+    int lane, s;
+    if (DIR == 0) { lane = c / W; s = c - lane * W; }
+    else { s = c / LANES; lane = c - s * LANES; }
+    const int ga = a0 - G + s;
+    const int gl = l0 + lane;
+    const size_t o = offset(map_along(ga, n_along, a.periodic), gl < n_lane ? gl : n_lane - 1);
+    const Prim E = (Prim)U[o], Mx = (Prim)U[N + o], My = (Prim)U[2 * N + o], Mz = (Prim)U[3 * N + o];
+    const Prim R = (Prim)U[4 * N + o];
+    Prim e, vx, vy, vz;
+    int hit = 0;
+    cons_to_prim(E, Mx, My, Mz, e_floor, e, vx, vy, vz, hit);
+    const Prim p = e * Prim(1.0 / 3.0);
+    const Prim vd = DIR == 0 ? vx : (DIR == 1 ? vy : vz);
+    const Prim rho = spectral_radius(vd, vx * vx + vy * vy + vz * vz);
+    const Prim Md = DIR == 0 ? Mx : (DIR == 1 ? My : Mz);
+    sU[0 * NCS + c] = (F)E;
+    sU[1 * NCS + c] = (F)Mx;
+    sU[2 * NCS + c] = (F)My;
+    sU[3 * NCS + c] = (F)Mz;
+    sU[4 * NCS + c] = (F)R;
+    sF[0 * NCS + c] = (F)(Prim(0.5) * Md);
+    sF[1 * NCS + c] = (F)(Prim(0.5) * (Mx * vd + (DIR == 0 ? p : Prim(0))));
+    sF[2 * NCS + c] = (F)(Prim(0.5) * (My * vd + (DIR == 1 ? p : Prim(0))));
+    sF[3 * NCS + c] = (F)(Prim(0.5) * (Mz * vd + (DIR == 2 ? p : Prim(0))));
+    sF[4 * NCS + c] = (F)(Prim(0.5) * (R * vd));
+    sR[c] = (F)rho;
+    if (s >= G && s < G + SEG && ga < n_along && gl < n_lane) {
+      vmax = fmax(vmax, (double)rho);
+      hits += (unsigned)hit;
+    }
+  }
+  if (a.reduce_speed || a.count_floors) publish_block(vmax, hits, a.diag, a.reduce_speed, a.count_floors);
+  __syncthreads();
+
+  // ---------------- phase 2: numerical flux at every interface of the tile
+  const F eps = (ORDER == 7) ? (F)(240.0 * a.eps) : (F)a.eps;
+  for (int it = threadIdx.x; it < NIF; it += kThreads) {
+    int lane, j;
+    if (DIR == 0) { lane = it / (SEG + 1); j = it - lane * (SEG + 1); }
+    else { j = it / LANES; lane = it - j * LANES; }
+    // the interface left of tile cell j; its stencil is staged cells j .. j + 2G - 1
+    F alpha = sR[sidx(lane, j)];
+#pragma unroll
+    for (int t = 1; t < 2 * G; ++t) alpha = fmax(alpha, sR[sidx(lane, j + t)]);
+    const F ah = F(0.5) * alpha;
+#pragma unroll 1
+    for (int q = 0; q < 5; ++q) {
+      F u[2 * G], f[2 * G];
+#pragma unroll
+      for (int t = 0; t < 2 * G; ++t) {
+        u[t] = sU[q * NCS + sidx(lane, j + t)];
+        f[t] = sF[q * NCS + sidx(lane, j + t)];
+      }
+      F hp, hm;
+      if (ORDER == 7) {
+        hp = weno7<F>(fma(ah, u[0], f[0]), fma(ah, u[1], f[1]), fma(ah, u[2], f[2]), fma(ah, u[3], f[3]),
+                      fma(ah, u[4], f[4]), fma(ah, u[5], f[5]), fma(ah, u[6], f[6]), eps);
+        hm = weno7<F>(fma(-ah, u[7], f[7]), fma(-ah, u[6], f[6]), fma(-ah, u[5], f[5]), fma(-ah, u[4], f[4]),
+                      fma(-ah, u[3], f[3]), fma(-ah, u[2], f[2]), fma(-ah, u[1], f[1]), eps);
+      } else {
+        hp = weno5<F>(fma(ah, u[0], f[0]), fma(ah, u[1], f[1]), fma(ah, u[2], f[2]), fma(ah, u[3], f[3]),
+                      fma(ah, u[4], f[4]), eps);
+        hm = weno5<F>(fma(-ah, u[5], f[5]), fma(-ah, u[4], f[4]), fma(-ah, u[3], f[3]), fma(-ah, u[2], f[2]),
+                      fma(-ah, u[1], f[1]), eps);
+      }
+      sH[q * NIF + it] = hp + hm;
+    }
+  }
+  __syncthreads();
+
+  // ---------------- phase 3: flux difference, source, stage combination
+  bool jets_here = false;
+  if (FINAL) {
+    for (int jn = 0; jn < a.jets.n; ++jn) {
+      const int* cl = a.jets.cell[jn];
+      if (cl[0] < 0) continue;
+      const int jal = DIR == 0 ? cl[0] : (DIR == 1 ? cl[1] : cl[2]);
+      const int jln = DIR == 0 ? cl[1] : cl[0];
+      const int jfx = DIR == 2 ? cl[1] : cl[2];
+      if (jfx == fixed && jal >= a0 && jal < a0 + SEG && jln >= l0 && jln < l0 + LANES) jets_here = true;
+    }
+  }
+  F* __restrict__ rhs = static_cast<F*>(a.rhs);
+  const F inv_dx = (F)a.inv_dx;
+  bool bad = false;
+  for (int c = threadIdx.x; c < NC; c += kThreads) {
+    int lane, j;
+    if (DIR == 0) { lane = c / SEG; j = c - lane * SEG; }
+    else { j = c / LANES; lane = c - j * LANES; }
+    const int ga = a0 + j, gl = l0 + lane;
+    if (ga >= n_along || gl >= n_lane) continue;
+    const size_t o = offset(ga, gl);
+    const int h0 = hidx(lane, j), h1 = hidx(lane, j + 1);
+    F L[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) L[q] = -(sH[q * NIF + h1] - sH[q * NIF + h0]) * inv_dx;
+    if (!FINAL) {
+      if (DIR == 0) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) rhs[q * N + o] = L[q];
+      } else {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) rhs[q * N + o] += L[q];
+      }
+    } else {
+      double Ld[5];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) Ld[q] = (double)(rhs[q * N + o] + L[q]);
+      if (jets_here) {
+        const int gx = DIR == 0 ? ga : gl;
+        const int gy = DIR == 1 ? ga : (DIR == 0 ? gl : fixed);
+        const int gz = DIR == 2 ? ga : fixed;
+        for (int jn = 0; jn < a.jets.n; ++jn) {
+          const int* cl = a.jets.cell[jn];
+          if (cl[0] != gx || cl[1] != gy || cl[2] != gz) continue;
+          // Eq. 3 at the temperature of this cell, deposited as in Eq. 2
+          double e, vx, vy, vz;
+          int hit = 0;
+          cons_to_prim<double>((double)U[o], (double)U[N + o], (double)U[2 * N + o], (double)U[3 * N + o],
+                               a.e_floor, e, vx, vy, vz, hit);
+          const double T = temperature(e, a.src.t4coef);
+          const double S0 = (a.src.rad * T * T * T * a.jets.ell[jn] + a.src.coll * T * T) * a.src.inv_vol;
+          Ld[0] += S0;
+          Ld[1] += a.jets.dir[jn][0] * S0;
+          Ld[2] += a.jets.dir[jn][1] * S0;
+          Ld[3] += a.jets.dir[jn][2] * S0;
+          a.diag->dep[jn] += a.src.wdt_vol * S0;
+          a.diag->cell[jn][0] = gx;
+          a.diag->cell[jn][1] = gy;
+          a.diag->cell[jn][2] = gz;
+        }
+      }
+      // U0 and Uout alias at the last stage (in-place update of the step state)
+      const Store* U0 = static_cast<const Store*>(a.U0);
+      Store* Uout = static_cast<Store*>(a.Uout);
+      const Store dt = (Store)a.dt, ca = (Store)a.a, cb = (Store)a.b;
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        const Store u = U[q * N + o];
+        const Store l = (Store)Ld[q];
+        Store out = (a.a == 0.0) ? u + dt * l : ca * U0[q * N + o] + cb * (u + dt * l);
+        bad |= !isfinite(out);
+        Uout[q * N + o] = out;
+      }
+    }
+  }
+  if (FINAL && bad) atomicCAS(&a.diag->status, 0, (int)HYDRO_EUNPHYSICAL);
+}
+
+template <int PREC, int ORDER, int DIR>
+static cudaError_t launch_one(const SweepArgs& a, cudaStream_t s) {
+  using F = typename Types<PREC>::Flux;
+  constexpr int SEG = Tile<DIR>::SEG, LANES = Tile<DIR>::LANES, G = (ORDER == 7) ? 4 : 3;
+  constexpr size_t smem = sizeof(F) * (size_t)(11 * LANES * (SEG + 2 * G) + 5 * LANES * (SEG + 1));
+  dim3 grid;
+  if (DIR == 0) grid = dim3((a.nx + SEG - 1) / SEG, (a.ny + LANES - 1) / LANES, a.nz);
+  else if (DIR == 1) grid = dim3((a.nx + LANES - 1) / LANES, (a.ny + SEG - 1) / SEG, a.nz);
+  else grid = dim3((a.nx + LANES - 1) / LANES, (a.nz + SEG - 1) / SEG, a.ny);
+  auto kern = sweep_kernel<PREC, ORDER, DIR, DIR == 2>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  kern<<<grid, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int PREC, int ORDER>
+static cudaError_t launch_dir(int dir, const SweepArgs& a, cudaStream_t s) {
+  switch (dir) {
+    case 0: return launch_one<PREC, ORDER, 0>(a, s);
+    case 1: return launch_one<PREC, ORDER, 1>(a, s);
+    default: return launch_one<PREC, ORDER, 2>(a, s);
+  }
+}
+
+template <int PREC>
+static cudaError_t launch_order(int order, int dir, const SweepArgs& a, cudaStream_t s) {
+  return order == 5 ? launch_dir<PREC, 5>(dir, a, s) : launch_dir<PREC, 7>(dir, a, s);
+}
+
+cudaError_t launch_sweep(int precision, int order, int dir, const SweepArgs& a, cudaStream_t s) {
+  switch (precision) {
+    case HYDRO_FP64: return launch_order<HYDRO_FP64>(order, dir, a, s);
+    case HYDRO_FP32: return launch_order<HYDRO_FP32>(order, dir, a, s);
+    default: return launch_order<HYDRO_MIXED>(order, dir, a, s);
+  }
+}
+
+// ---------------------------------------------------------------- initial state and read-back
+
+// Eq. 1 with p = e/3: E = (e+p) gamma^2 - p, M^i = (e+p) gamma u^i, R = n gamma,
+// gamma = sqrt(1 + u.u).  Rejects e < 0 and non-finite input.
+template <class Store>
+__global__ void init_kernel(int kind, const double* __restrict__ st, Store* __restrict__ U, size_t n,
+                            DevDiag* diag) {
+  bool bad = false;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double f0 = st[i], f1 = st[n + i], f2 = st[2 * n + i], f3 = st[3 * n + i], f4 = st[4 * n + i];
+    bad |= !(isfinite(f0) && isfinite(f1) && isfinite(f2) && isfinite(f3) && isfinite(f4));
+    double E, Mx, My, Mz, R;
+    if (kind == HYDRO_PRIMITIVE) {
+      bad |= !(f0 >= 0.0);
+      const double p = f0 / 3.0, w = f0 + p;
+      const double g2 = 1.0 + (f1 * f1 + f2 * f2 + f3 * f3);
+      const double g = sqrt(g2);
+      E = w * g2 - p;
+      Mx = w * g * f1;
+      My = w * g * f2;
+      Mz = w * g * f3;
+      R = f4 * g;
+    } else {
+      E = f0; Mx = f1; My = f2; Mz = f3; R = f4;
+    }
+    U[i] = (Store)E;
+    U[n + i] = (Store)Mx;
+    U[2 * n + i] = (Store)My;
+    U[3 * n + i] = (Store)Mz;
+    U[4 * n + i] = (Store)R;
+  }
+  if (bad) atomicExch(&diag->bad_input, 1);
+}
+
+template <class Store>
+__global__ void readback_kernel(int kind, const Store* __restrict__ U, double* __restrict__ st, size_t n,
+                                double e_floor) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double E = U[i], Mx = U[n + i], My = U[2 * n + i], Mz = U[3 * n + i], R = U[4 * n + i];
+    if (kind == HYDRO_CONSERVED) {
+      st[i] = E; st[n + i] = Mx; st[2 * n + i] = My; st[3 * n + i] = Mz; st[4 * n + i] = R;
+    } else {
+      double e, vx, vy, vz;
+      int hit = 0;
+      cons_to_prim<double>(E, Mx, My, Mz, e_floor, e, vx, vy, vz, hit);
+      const double v2 = vx * vx + vy * vy + vz * vz;
+      const double ig = sqrt(1.0 - v2);   // 1/gamma
+      const double g = 1.0 / ig;
+      st[i] = e; st[n + i] = g * vx; st[2 * n + i] = g * vy; st[3 * n + i] = g * vz; st[4 * n + i] = R * ig;
+    }
+  }
+}
+
+static unsigned grid_for(size_t n) {
+  size_t b = (n + 255) / 256;
+  return (unsigned)(b < 148 * 32 ? (b > 0 ? b : 1) : 148 * 32);
+}
+
+cudaError_t launch_init(int precision, int kind, const double* staging, void* U, size_t n, DevDiag* diag,
+                        cudaStream_t s) {
+  if (precision == HYDRO_FP32)
+    init_kernel<float><<<grid_for(n), 256, 0, s>>>(kind, staging, static_cast<float*>(U), n, diag);
+  else
+    init_kernel<double><<<grid_for(n), 256, 0, s>>>(kind, staging, static_cast<double*>(U), n, diag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_readback(int precision, int kind, const void* U, double* staging, size_t n, double e_floor,
+                            cudaStream_t s) {
+  if (precision == HYDRO_FP32)
+    readback_kernel<float><<<grid_for(n), 256, 0, s>>>(kind, static_cast<const float*>(U), staging, n, e_floor);
+  else
+    readback_kernel<double><<<grid_for(n), 256, 0, s>>>(kind, static_cast<const double*>(U), staging, n, e_floor);
+  return cudaGetLastError();
+}
+
+}  // namespace hydro

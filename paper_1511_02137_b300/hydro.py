@@ -1,0 +1,204 @@
+"""Python binding of the C ABI in include/hydro.h (argument marshalling only).
+
+Every function keeps the C name.  Device memory for the field store comes from
+PyTorch's CUDA caching allocator (one workspace tensor per context) and the
+device work runs on PyTorch's current CUDA stream unless another is given; all
+arithmetic runs in the CUDA kernels of ``libhydro.so``.  There is no CPU path:
+importing this module fails if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhydro.so")
+
+HYDRO_OK, HYDRO_EINVAL, HYDRO_ENOMEM, HYDRO_ECUDA, HYDRO_EUNPHYSICAL, HYDRO_ECFL, HYDRO_ETIMEOUT, HYDRO_ESTATE = range(8)
+HYDRO_FP64, HYDRO_FP32, HYDRO_MIXED = 0, 1, 2
+HYDRO_OUTFLOW, HYDRO_PERIODIC = 0, 1
+HYDRO_PRIMITIVE, HYDRO_CONSERVED = 0, 1
+HYDRO_KERNEL_SWEEP_X, HYDRO_KERNEL_SWEEP_Y, HYDRO_KERNEL_SWEEP_Z, HYDRO_KERNEL_OTHER = 0, 1, 2, 3
+HYDRO_MAX_JETS = 16
+PRECISIONS = {"fp64": HYDRO_FP64, "fp32": HYDRO_FP32, "mixed": HYDRO_MIXED}
+
+
+class hydro_config(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("boundary", ctypes.c_int32), ("weno_order", ctypes.c_int32),
+                ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("t0", ctypes.c_double),
+                ("k_rad", ctypes.c_double), ("k_coll", ctypes.c_double), ("cr_over_cf", ctypes.c_double),
+                ("hbarc", ctypes.c_double), ("dof", ctypes.c_double), ("e_floor", ctypes.c_double),
+                ("weno_eps", ctypes.c_double), ("cfl_limit", ctypes.c_double),
+                ("cuda_stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_size_t)]
+
+
+class hydro_diag(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("steps", ctypes.c_int64), ("max_speed", ctypes.c_double),
+                ("floor_hits", ctypes.c_int64), ("dep_E", ctypes.c_double), ("dep_M", ctypes.c_double * 3),
+                ("njet", ctypes.c_int32), ("jet_cell", (ctypes.c_int32 * 3) * HYDRO_MAX_JETS),
+                ("status", ctypes.c_int32)]
+
+
+class HydroError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {_lib().hydro_status_string(status).decode()}")
+
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1511_02137_b300.build`")
+        lib = ctypes.CDLL(LIB_PATH)
+        P = ctypes.POINTER
+        vp, dp = ctypes.c_void_p, P(ctypes.c_double)
+        lib.hydro_config_default.argtypes = [P(hydro_config), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+        lib.hydro_config_default.restype = None
+        lib.hydro_workspace_size.argtypes = [P(hydro_config), P(ctypes.c_size_t)]
+        lib.hydro_create.argtypes = [P(hydro_config), P(vp)]
+        lib.hydro_set_initial.argtypes = [vp, ctypes.c_int32, vp]
+        lib.hydro_add_jet.argtypes = [vp, dp, dp, ctypes.c_double, P(ctypes.c_int32)]
+        lib.hydro_step.argtypes = [vp, ctypes.c_int32]
+        lib.hydro_read_fields.argtypes = [vp, ctypes.c_int32, vp]
+        lib.hydro_get_diag.argtypes = [vp, P(hydro_diag)]
+        lib.hydro_profile_enable.argtypes = [vp, ctypes.c_int32]
+        lib.hydro_profile_query.argtypes = [vp, ctypes.c_int32, dp, P(ctypes.c_int64)]
+        lib.hydro_destroy.argtypes = [vp]
+        lib.hydro_destroy.restype = None
+        lib.hydro_status_string.argtypes = [ctypes.c_int]
+        lib.hydro_status_string.restype = ctypes.c_char_p
+        for name in ("hydro_workspace_size", "hydro_create", "hydro_set_initial", "hydro_add_jet", "hydro_step",
+                     "hydro_read_fields", "hydro_get_diag", "hydro_profile_enable", "hydro_profile_query"):
+            getattr(lib, name).restype = ctypes.c_int
+        _LIB = lib
+    return _LIB
+
+
+def _check(status: int, where: str, allow=()):
+    if status != HYDRO_OK and status not in allow:
+        raise HydroError(status, where)
+    return status
+
+
+class Context:
+    """Opaque hydro_ctx plus the torch workspace tensor that backs it."""
+
+    def __init__(self, handle, cfg, workspace):
+        self.handle = handle
+        self.cfg = cfg
+        self.workspace = workspace
+        self.cells = cfg.nx * cfg.ny * cfg.nz
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            hydro_destroy(self)
+
+
+def hydro_config_default(nx: int, ny: int, nz: int, **overrides) -> hydro_config:
+    cfg = hydro_config()
+    _lib().hydro_config_default(ctypes.byref(cfg), nx, ny, nz)
+    for k, v in overrides.items():
+        if k == "precision" and isinstance(v, str):
+            v = PRECISIONS[v]
+        if k == "boundary" and isinstance(v, str):
+            v = {"outflow": HYDRO_OUTFLOW, "periodic": HYDRO_PERIODIC}[v]
+        setattr(cfg, k, v)
+    return cfg
+
+
+def hydro_workspace_size(cfg: hydro_config) -> int:
+    n = ctypes.c_size_t()
+    _check(_lib().hydro_workspace_size(ctypes.byref(cfg), ctypes.byref(n)), "hydro_workspace_size")
+    return n.value
+
+
+def hydro_create(cfg: hydro_config, device=None, stream=None) -> Context:
+    """Creates a context whose workspace is a torch CUDA tensor and whose stream
+    is torch's current stream on `device` (or `stream` if given)."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    nbytes = hydro_workspace_size(cfg)
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+    base = ws.data_ptr()
+    aligned = (base + 255) // 256 * 256
+    c = hydro_config.from_buffer_copy(cfg)
+    c.workspace = aligned
+    c.workspace_bytes = nbytes
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    c.cuda_stream = s.cuda_stream
+    h = ctypes.c_void_p()
+    _check(_lib().hydro_create(ctypes.byref(c), ctypes.byref(h)), "hydro_create")
+    ctx = Context(h, c, ws)
+    ctx.stream = s
+    return ctx
+
+
+def _host_ptr(buf, n: int, writable: bool):
+    if isinstance(buf, np.ndarray):
+        if buf.dtype != np.float64 or not buf.flags.c_contiguous or buf.size != n:
+            raise ValueError(f"expected a C-contiguous float64 array of {n} values")
+        if writable and not buf.flags.writeable:
+            raise ValueError("output array is read-only")
+        return buf.ctypes.data
+    import torch
+    if isinstance(buf, torch.Tensor):
+        if buf.device.type != "cpu" or buf.dtype != torch.float64 or not buf.is_contiguous() or buf.numel() != n:
+            raise ValueError(f"expected a contiguous CPU float64 tensor of {n} values")
+        return buf.data_ptr()
+    raise TypeError("host buffer must be a numpy array or a CPU torch tensor")
+
+
+def hydro_set_initial(ctx: Context, kind: int, host5) -> None:
+    _check(_lib().hydro_set_initial(ctx.handle, kind, _host_ptr(host5, 5 * ctx.cells, False)), "hydro_set_initial")
+
+
+def hydro_add_jet(ctx: Context, x0, direction, t_start: float) -> int:
+    a = (ctypes.c_double * 3)(*x0)
+    d = (ctypes.c_double * 3)(*direction)
+    jid = ctypes.c_int32()
+    _check(_lib().hydro_add_jet(ctx.handle, a, d, t_start, ctypes.byref(jid)), "hydro_add_jet")
+    return jid.value
+
+
+def hydro_step(ctx: Context, nsteps: int, allow=()) -> int:
+    return _check(_lib().hydro_step(ctx.handle, nsteps), "hydro_step", allow)
+
+
+def hydro_read_fields(ctx: Context, kind: int = HYDRO_CONSERVED, out=None):
+    if out is None:
+        out = np.empty((5, ctx.cfg.nz, ctx.cfg.ny, ctx.cfg.nx), dtype=np.float64)
+    _check(_lib().hydro_read_fields(ctx.handle, kind, _host_ptr(out, 5 * ctx.cells, True)), "hydro_read_fields")
+    return out
+
+
+def hydro_get_diag(ctx: Context) -> dict:
+    d = hydro_diag()
+    _check(_lib().hydro_get_diag(ctx.handle, ctypes.byref(d)), "hydro_get_diag")
+    return {"t": d.t, "steps": d.steps, "max_speed": d.max_speed, "floor_hits": d.floor_hits,
+            "dep_E": d.dep_E, "dep_M": tuple(d.dep_M), "njet": d.njet,
+            "jet_cells": [tuple(d.jet_cell[i]) for i in range(d.njet)], "status": d.status}
+
+
+def hydro_profile_enable(ctx: Context, on: bool = True) -> None:
+    _check(_lib().hydro_profile_enable(ctx.handle, 1 if on else 0), "hydro_profile_enable")
+
+
+def hydro_profile_query(ctx: Context, kind: int):
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(_lib().hydro_profile_query(ctx.handle, kind, ctypes.byref(ms), ctypes.byref(n)), "hydro_profile_query")
+    return ms.value, n.value
+
+
+def hydro_destroy(ctx: Context) -> None:
+    if ctx.handle:
+        _lib().hydro_destroy(ctx.handle)
+        ctx.handle = None

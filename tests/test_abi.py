@@ -1,0 +1,88 @@
+"""The C ABI library loads and exports every declared entry point (no GPU).
+
+Only calls that touch no device memory are made here: defaults, workspace
+sizing and configuration validation.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "hydro.h")
+
+
+@pytest.fixture(scope="module")
+def hy():
+    from paper_1511_02137_b300 import build
+    build.build()
+    from paper_1511_02137_b300 import hydro
+    return hydro
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hydro_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_six_calls_and_more():
+    names = _declared_functions()
+    for n in ("hydro_create", "hydro_set_initial", "hydro_add_jet", "hydro_step", "hydro_read_fields",
+              "hydro_destroy"):
+        assert n in names
+    assert "hydro_get_diag" in names
+
+
+def test_library_exports_every_declared_symbol(hy):
+    lib = ctypes.CDLL(hy.LIB_PATH)
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_defaults_are_the_paper_values(hy):
+    c = hy.hydro_config_default(256, 256, 256)
+    assert (c.dx, c.dt, c.t0) == (0.1, 0.02, 1.0)
+    assert (c.k_rad, c.k_coll, c.cr_over_cf) == (4.0, 2.5, 1.0)
+    assert (c.hbarc, c.dof) == (0.1973, 47.5)
+    assert c.weno_order == 7 and c.precision == hy.HYDRO_FP64 and c.boundary == hy.HYDRO_OUTFLOW
+
+
+def test_workspace_size_counts_three_states_and_rhs(hy):
+    n = 32 * 32 * 32
+    fp64 = hy.hydro_workspace_size(hy.hydro_config_default(32, 32, 32))
+    fp32 = hy.hydro_workspace_size(hy.hydro_config_default(32, 32, 32, precision="fp32"))
+    mixed = hy.hydro_workspace_size(hy.hydro_config_default(32, 32, 32, precision="mixed"))
+    assert 4 * 5 * n * 8 <= fp64 < 4 * 5 * n * 8 + 8192
+    assert 4 * 5 * n * 4 <= fp32 < 4 * 5 * n * 4 + 8192
+    assert 3 * 5 * n * 8 + 5 * n * 4 <= mixed < 3 * 5 * n * 8 + 5 * n * 4 + 8192
+
+
+@pytest.mark.parametrize("field,value", [("nx", 0), ("precision", 7), ("boundary", 5), ("weno_order", 6),
+                                         ("dx", 0.0), ("dt", -1.0), ("e_floor", 0.0), ("hbarc", 0.0)])
+def test_invalid_configuration_is_rejected_without_touching_the_device(hy, field, value):
+    c = hy.hydro_config_default(16, 16, 16)
+    setattr(c, field, value)
+    size = ctypes.c_size_t()
+    assert hy._lib().hydro_workspace_size(ctypes.byref(c), ctypes.byref(size)) == hy.HYDRO_EINVAL
+    h = ctypes.c_void_p(1)
+    assert hy._lib().hydro_create(ctypes.byref(c), ctypes.byref(h)) == hy.HYDRO_EINVAL
+    assert h.value is None
+
+
+def test_misaligned_workspace_is_rejected(hy):
+    c = hy.hydro_config_default(8, 8, 8)
+    c.workspace = 0x1000 + 8
+    c.workspace_bytes = 1 << 30
+    h = ctypes.c_void_p()
+    assert hy._lib().hydro_create(ctypes.byref(c), ctypes.byref(h)) == hy.HYDRO_EINVAL
+
+
+def test_null_arguments_are_rejected(hy):
+    lib = hy._lib()
+    assert lib.hydro_step(None, 1) == hy.HYDRO_EINVAL
+    assert lib.hydro_set_initial(None, 0, None) == hy.HYDRO_EINVAL
+    assert lib.hydro_read_fields(None, 0, None) == hy.HYDRO_EINVAL
+    lib.hydro_destroy(None)
+    assert lib.hydro_status_string(hy.HYDRO_ECFL).startswith(b"HYDRO_ECFL")
