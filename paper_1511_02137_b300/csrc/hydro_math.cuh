@@ -61,11 +61,11 @@ __device__ __forceinline__ P spectral_radius(P vd, P v2) {
 
 // Nonlinear weights of WENO-JS, w_k ~ d_k / (eps + beta_k)^2, returned as the
 // weighted candidate average.  Arguments are 12*q_k (candidates in twelfths),
-// 240*beta_k and 240*eps, so that sum_k w_k q_k = num / (12 den).
+// 720*beta_k and 720*eps, so that sum_k w_k q_k = num / (12 den).
 // FP64: one division, using w_k ~ d_k prod_{j != k} (eps + beta_j)^2.
 __device__ __forceinline__ double weno7_combine(double q0, double q1, double q2, double q3, double b0, double b1,
-                                                double b2, double b3, double eps240) {
-  double s0 = eps240 + b0, s1 = eps240 + b1, s2 = eps240 + b2, s3 = eps240 + b3;
+                                                double b2, double b3, double eps720) {
+  double s0 = eps720 + b0, s1 = eps720 + b1, s2 = eps720 + b2, s3 = eps720 + b3;
   s0 *= s0;
   s1 *= s1;
   s2 *= s2;
@@ -82,8 +82,8 @@ __device__ __forceinline__ double weno7_combine(double q0, double q1, double q2,
 
 // FP32: the product form could overflow, so each weight takes a fast reciprocal.
 __device__ __forceinline__ float weno7_combine(float q0, float q1, float q2, float q3, float b0, float b1, float b2,
-                                               float b3, float eps240) {
-  float s0 = eps240 + b0, s1 = eps240 + b1, s2 = eps240 + b2, s3 = eps240 + b3;
+                                               float b3, float eps720) {
+  float s0 = eps720 + b0, s1 = eps720 + b1, s2 = eps720 + b2, s3 = eps720 + b3;
   float a0 = __fdividef(1.0f, s0 * s0);
   float a1 = __fdividef(12.0f, s1 * s1);
   float a2 = __fdividef(18.0f, s2 * s2);
@@ -95,28 +95,35 @@ __device__ __forceinline__ float weno7_combine(float q0, float q1, float q2, flo
 
 // WENO7 reconstruction at x_{i+1/2} from f0..f6 = f_{i-3..i+3} (finite-difference
 // form: the values are cell averages of the function reconstructed).  Candidate
-// cubics on the four 4-cell stencils, Balsara-Shu smoothness indicators
-// 240 beta_k (integer quadratic forms), Jiang-Shu weights with linear weights
-// (1, 12, 18, 4)/35.
+// cubics on the four 4-cell stencils and Jiang-Shu weights with linear weights
+// (1, 12, 18, 4)/35.  The Balsara-Shu smoothness indicators
+// beta_k = sum_{l=1..3} int_cell (h^l p_k^(l))^2 dx / h are evaluated as the sum
+// of squares they equal, 720 beta_k = 20 A_k^2 + 780 B_k^2 + 781 C_k^2, with
+// A_k, B_k, C_k integer combinations of the first, second and third
+// differences of the stencil values (p_k = a0 + a1 x + a2 x^2 + a3 x^3 about
+// the cell centre gives beta = (a1 + a3/4)^2 + 13/3 a2^2 + 781/20 a3^2).  Being
+// a sum of squares it stays non-negative in FP32, where the expanded quadratic
+// form cancels to negative values in smooth regions.
 template <class F>
-__device__ __forceinline__ F weno7(F f0, F f1, F f2, F f3, F f4, F f5, F f6, F eps240) {
-  F q0 = F(-3) * f0 + F(13) * f1 - F(23) * f2 + F(25) * f3;
-  F q1 = f1 - F(5) * f2 + F(13) * f3 + F(3) * f4;
-  F q2 = -f2 + F(7) * f3 + F(7) * f4 - f5;
-  F q3 = F(3) * f3 + F(13) * f4 - F(5) * f5 + f6;
-  F b0 = f0 * (F(547) * f0 - F(3882) * f1 + F(4642) * f2 - F(1854) * f3) +
-         f1 * (F(7043) * f1 - F(17246) * f2 + F(7042) * f3) + f2 * (F(11003) * f2 - F(9402) * f3) +
-         F(2107) * f3 * f3;
-  F b1 = f1 * (F(267) * f1 - F(1642) * f2 + F(1602) * f3 - F(494) * f4) +
-         f2 * (F(2843) * f2 - F(5966) * f3 + F(1922) * f4) + f3 * (F(3443) * f3 - F(2522) * f4) +
-         F(547) * f4 * f4;
-  F b2 = f2 * (F(547) * f2 - F(2522) * f3 + F(1922) * f4 - F(494) * f5) +
-         f3 * (F(3443) * f3 - F(5966) * f4 + F(1602) * f5) + f4 * (F(2843) * f4 - F(1642) * f5) +
-         F(267) * f5 * f5;
-  F b3 = f3 * (F(2107) * f3 - F(9402) * f4 + F(7042) * f5 - F(1854) * f6) +
-         f4 * (F(11003) * f4 - F(17246) * f5 + F(4642) * f6) + f5 * (F(7043) * f5 - F(3882) * f6) +
-         F(547) * f6 * f6;
-  return weno7_combine(q0, q1, q2, q3, b0, b1, b2, b3, eps240);
+__device__ __forceinline__ F weno7(F f0, F f1, F f2, F f3, F f4, F f5, F f6, F eps720) {
+  const F q0 = F(-3) * f0 + F(13) * f1 - F(23) * f2 + F(25) * f3;
+  const F q1 = f1 - F(5) * f2 + F(13) * f3 + F(3) * f4;
+  const F q2 = -f2 + F(7) * f3 + F(7) * f4 - f5;
+  const F q3 = F(3) * f3 + F(13) * f4 - F(5) * f5 + f6;
+  const F d10 = f1 - f0, d11 = f2 - f1, d12 = f3 - f2, d13 = f4 - f3, d14 = f5 - f4, d15 = f6 - f5;
+  const F d20 = d11 - d10, d21 = d12 - d11, d22 = d13 - d12, d23 = d14 - d13, d24 = d15 - d14;
+  const F c0 = d21 - d20, c1 = d22 - d21, c2 = d23 - d22, c3 = d24 - d23;
+  const F bb0 = F(2) * d21 - d20, bb12 = d22, bb3 = F(2) * d23 - d24;
+  const F a0 = F(2) * d10 - F(7) * d11 + F(11) * d12;
+  const F a1 = -d11 + F(5) * d12 + F(2) * d13;
+  const F a2 = F(2) * d12 + F(5) * d13 - d14;
+  const F a3 = F(11) * d13 - F(7) * d14 + F(2) * d15;
+  const F m12 = F(780) * bb12 * bb12;
+  const F b0 = F(20) * a0 * a0 + F(780) * bb0 * bb0 + F(781) * c0 * c0;
+  const F b1 = F(20) * a1 * a1 + m12 + F(781) * c1 * c1;
+  const F b2 = F(20) * a2 * a2 + m12 + F(781) * c2 * c2;
+  const F b3 = F(20) * a3 * a3 + F(780) * bb3 * bb3 + F(781) * c3 * c3;
+  return weno7_combine(q0, q1, q2, q3, b0, b1, b2, b3, eps720);
 }
 
 // WENO5 weights (linear weights (1, 6, 3)/10); candidates in sixths.

@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a) {
   __syncthreads();
 
   // ---------------- phase 2: numerical flux at every interface of the tile
-  const F eps = (ORDER == 7) ? (F)(240.0 * a.eps) : (F)a.eps;
+  const F eps = (ORDER == 7) ? (F)(720.0 * a.eps) : (F)a.eps;
   for (int it = threadIdx.x; it < NIF; it += kThreads) {
     int lane, j;
     if (DIR == 0) { lane = it / (SEG + 1); j = it - lane * (SEG + 1); }

@@ -219,3 +219,22 @@ def test_error_statuses(hy, W):
     with pytest.raises(hy.HydroError) as e:
         hy.hydro_add_jet(ctx2, (0, 0, 0), (0, 0, 0), 1.0)
     assert e.value.status == hy.HYDRO_EINVAL
+
+
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_full_size_reduced_precision_stays_finite_and_close(hy, W, precision):
+    """256^3 with the jet: FP32 and mixed runs stay finite and within 1e-4
+    (norm-relative, per field) of the FP64 path after 10 steps."""
+    w = W.ELLIPSOIDAL_256
+    res = {}
+    for prec in ("fp64", precision):
+        ctx = gpu_context(hy, w, prec)
+        hy.hydro_step(ctx, 10)
+        res[prec] = hy.hydro_read_fields(ctx, hy.HYDRO_CONSERVED)
+        d = hy.hydro_get_diag(ctx)
+        assert d["status"] == 0 and d["floor_hits"] == 0
+        hy.hydro_destroy(ctx)
+    assert np.isfinite(res[precision]).all()
+    err = norm_rel_err(res[precision], res["fp64"])
+    print(precision, "256^3, 10 steps, error vs FP64 path per field:", err)
+    assert np.all(err <= 1e-4), err
