@@ -156,6 +156,43 @@ enum {
 hydro_status hydro_profile_enable(hydro_ctx* ctx, int32_t on);
 hydro_status hydro_profile_query(hydro_ctx* ctx, int32_t kind, double* total_ms, int64_t* launches);
 
+/* Largest grid (nx*ny*nz cells) that hydro_step_noalloc accepts. */
+#define HYDRO_NOALLOC_MAX_CELLS 65536
+
+/* Allocation-free stepping, for callers that cannot allocate device memory
+ * (code that runs inside a memory pool or arena it does not own, plugins
+ * whose host forbids cudaMalloc after start-up, real-time loops where an
+ * allocation's latency or failure is not acceptable).  The paper has no
+ * counterpart: this is a library-side convenience around the same step.
+ *
+ * Advances the conserved state in d_state by nsteps SSP-RK3 steps exactly as
+ * hydro_step does (same kernels, same arithmetic), starting at step index
+ * step0 (time t0 + step0*dt).  d_state is caller-owned device memory holding
+ * 5*nx*ny*nz values (E, M^x, M^y, M^z, R; x fastest) in the storage type of
+ * cfg->precision (double for HYDRO_FP64 and HYDRO_MIXED, float for
+ * HYDRO_FP32); it is read and overwritten in place.  jets (host memory, may be
+ * NULL when njet = 0) holds njet rows of 7 doubles: x0[3], dir[3], t_start,
+ * with dir normalised inside as in hydro_add_jet.  diag_out (may be NULL)
+ * receives the diagnostics of this call only.  cfg->workspace is ignored; all
+ * work runs on cfg->cuda_stream and the call synchronises it before returning.
+ *
+ * The two intermediate stages, the right-hand-side accumulator and the
+ * diagnostics live in one fixed device array inside the library (about
+ * 7.9 MB), which every GPU that loads the library holds until the process
+ * exits.  The first call on a device, made with that device current, looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call
+ * before capturing a stream on the device.  Every call uses the same array, so
+ * calls that may overlap on the GPU (other streams or threads on the same
+ * device) race on it and must be serialised by the caller.  The call clears
+ * what must start at zero; it calls no cudaMalloc or cudaFree.
+ *
+ * Returns HYDRO_ENOMEM when nx*ny*nz > HYDRO_NOALLOC_MAX_CELLS (the fixed
+ * array is too small), HYDRO_EINVAL for an invalid configuration, NULL or
+ * misaligned d_state, bad jets, step0 < 0 or nsteps < 0, and otherwise the
+ * statuses of hydro_step (HYDRO_EUNPHYSICAL, HYDRO_ECFL, HYDRO_ECUDA). */
+hydro_status hydro_step_noalloc(const hydro_config* cfg, void* d_state, int64_t step0, int32_t nsteps,
+                                const double* jets, int32_t njet, hydro_diag* diag_out);
+
 /* Releases the context and any memory the library allocated.  NULL is a no-op. */
 void hydro_destroy(hydro_ctx* ctx);
 

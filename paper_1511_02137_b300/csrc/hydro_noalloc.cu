@@ -1,0 +1,199 @@
+// hydro_step_noalloc: RK3 steps on a caller-owned device state without any
+// device allocation.
+//
+// Who needs this: callers that cannot call cudaMalloc -- code running inside
+// a memory pool or arena it does not own, a plugin whose host forbids device
+// allocation after start-up, or a real-time loop where an allocation's
+// latency (or its failure) is not acceptable.  hydro_create needs a workspace
+// (three state copies and a right-hand-side accumulator); this entry point
+// instead keeps the two intermediate RK3 stages, the accumulator and the
+// diagnostics block in one fixed array compiled into the library.
+//
+// Cost of that choice: every GPU that loads the library holds the array
+// (kScratchBytes, about 7.9 MB) until the process exits, the grid is limited
+// to kNoAllocMaxCells cells, and all calls share the array, so calls whose
+// work overlaps on the GPU (different streams or threads sharing the device)
+// race on it and must be serialised by the caller.
+//
+// The array's name is only a host-side stand-in for the symbol: the device
+// address is looked up with cudaGetSymbolAddress once per device (on the
+// first call made with that device current) and passed to the kernels.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "hydro.h"
+#include "hydro_internal.h"
+
+namespace {
+
+using hydro::DevDiag;
+using hydro::SweepArgs;
+
+constexpr size_t kNoAllocMaxCells = HYDRO_NOALLOC_MAX_CELLS;
+constexpr size_t kAlign = 256;
+constexpr size_t kStateBytesMax = ((5 * kNoAllocMaxCells * sizeof(double) + kAlign - 1) / kAlign) * kAlign;
+constexpr size_t kDiagBytes = ((sizeof(DevDiag) + kAlign - 1) / kAlign) * kAlign;
+// two stage states and the accumulator at FP64 width, then the diagnostics block
+constexpr size_t kScratchBytes = 3 * kStateBytesMax + kDiagBytes;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mutex;
+void* g_scratch_dev[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device (looked up once).
+hydro_status scratch_address(void** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HYDRO_ECUDA;
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
+  if (!g_scratch_dev[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
+      cudaGetLastError();
+      return HYDRO_ECUDA;
+    }
+    g_scratch_dev[dev] = p;
+  }
+  *out = g_scratch_dev[dev];
+  return HYDRO_OK;
+}
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+bool config_ok(const hydro_config* c) {
+  if (!c) return false;
+  if (c->nx < 1 || c->ny < 1 || c->nz < 1) return false;
+  if (c->precision < HYDRO_FP64 || c->precision > HYDRO_MIXED) return false;
+  if (c->boundary != HYDRO_OUTFLOW && c->boundary != HYDRO_PERIODIC) return false;
+  if (c->weno_order != 7 && c->weno_order != 5) return false;
+  if (!(c->dx > 0.0) || !(c->dt > 0.0) || !std::isfinite(c->t0)) return false;
+  if (!(c->hbarc > 0.0) || !(c->dof > 0.0) || !(c->e_floor > 0.0) || !(c->weno_eps > 0.0)) return false;
+  if (!std::isfinite(c->k_rad) || !std::isfinite(c->k_coll) || !std::isfinite(c->cr_over_cf)) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" hydro_status hydro_step_noalloc(const hydro_config* cfg, void* d_state, int64_t step0, int32_t nsteps,
+                                           const double* jets, int32_t njet, hydro_diag* diag_out) {
+  if (!config_ok(cfg) || !d_state || nsteps < 0 || step0 < 0) return HYDRO_EINVAL;
+  if (njet < 0 || njet > HYDRO_MAX_JETS || (njet > 0 && !jets)) return HYDRO_EINVAL;
+  const size_t n = (size_t)cfg->nx * (size_t)cfg->ny * (size_t)cfg->nz;
+  if (n > kNoAllocMaxCells) return HYDRO_ENOMEM;   // the fixed scratch array is too small for this grid
+  const size_t store = cfg->precision == HYDRO_FP32 ? sizeof(float) : sizeof(double);
+  if ((uintptr_t)d_state % store != 0) return HYDRO_EINVAL;
+
+  // jets: x0[3], dir[3], t_start per jet; the direction is normalised as in hydro_add_jet
+  double jx0[HYDRO_MAX_JETS][3], jn[HYDRO_MAX_JETS][3], jt[HYDRO_MAX_JETS];
+  for (int j = 0; j < njet; ++j) {
+    const double* r = jets + 7 * j;
+    for (int a = 0; a < 7; ++a)
+      if (!std::isfinite(r[a])) return HYDRO_EINVAL;
+    const double len = std::sqrt(r[3] * r[3] + r[4] * r[4] + r[5] * r[5]);
+    if (!(len > 0.0)) return HYDRO_EINVAL;
+    for (int a = 0; a < 3; ++a) {
+      jx0[j][a] = r[a];
+      jn[j][a] = r[3 + a] / len;
+    }
+    jt[j] = r[6];
+  }
+
+  void* base = nullptr;
+  hydro_status st = scratch_address(&base);
+  if (st != HYDRO_OK) return st;
+  char* b = static_cast<char*>(base);
+  void* U1 = b;
+  void* U2 = b + align_up(5 * n * store);
+  void* rhs = b + 2 * align_up(5 * n * store);
+  DevDiag* diag = reinterpret_cast<DevDiag*>(b + 3 * kStateBytesMax);
+  cudaStream_t stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+
+  // the diagnostics block keeps the previous call's contents: start from zero
+  cudaError_t err = cudaMemsetAsync(diag, 0, sizeof(DevDiag), stream);
+
+  static const double kStageC[3] = {0.0, 1.0, 0.5};
+  static const double kStageW[3] = {1.0 / 6.0, 1.0 / 6.0, 4.0 / 6.0};
+  static const double kA[3] = {0.0, 0.75, 1.0 / 3.0};
+  static const double kB[3] = {1.0, 0.25, 2.0 / 3.0};
+  void* U[3] = {d_state, U1, U2};
+  SweepArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.U0 = d_state;
+  a.rhs = rhs;
+  a.diag = diag;
+  a.nx = cfg->nx;
+  a.ny = cfg->ny;
+  a.nz = cfg->nz;
+  a.periodic = cfg->boundary == HYDRO_PERIODIC;
+  a.inv_dx = 1.0 / cfg->dx;
+  a.dt = cfg->dt;
+  a.e_floor = cfg->e_floor;
+  a.eps = cfg->weno_eps;
+  a.src.rad = cfg->k_rad * cfg->cr_over_cf / (cfg->hbarc * cfg->hbarc);
+  a.src.coll = cfg->k_coll * cfg->cr_over_cf / cfg->hbarc;
+  a.src.t4coef = cfg->hbarc * cfg->hbarc * cfg->hbarc / (M_PI * M_PI / 30.0 * cfg->dof);
+  const double vol = cfg->dx * cfg->dx * cfg->dx;
+  a.src.inv_vol = 1.0 / vol;
+  const int N[3] = {cfg->nx, cfg->ny, cfg->nz};
+  for (int32_t s = 0; s < nsteps && err == cudaSuccess; ++s) {
+    const int64_t step = step0 + s;
+    err = cudaMemsetAsync(&diag->vmax_bits, 0, sizeof(unsigned long long), stream);
+    for (int k = 0; k < 3 && err == cudaSuccess; ++k) {
+      const double t = cfg->t0 + ((double)step + kStageC[k]) * cfg->dt;
+      a.jets.n = njet;
+      for (int j = 0; j < njet; ++j) {
+        // cell floor(x/dx + N/2) of x = x0 + n (t - t_start), FP64 without contraction
+        const double l = t - jt[j];
+        a.jets.ell[j] = l;
+        bool inside = (l >= 0.0);
+        for (int ax = 0; ax < 3; ++ax) {
+          const double x = jx0[j][ax] + jn[j][ax] * l;
+          const double fl = std::floor(x / cfg->dx + 0.5 * (double)N[ax]);
+          if (!(fl >= 0.0 && fl < (double)N[ax])) inside = false;
+          a.jets.cell[j][ax] = (fl >= 0.0 && fl < (double)N[ax]) ? (int)fl : -1;
+          a.jets.dir[j][ax] = jn[j][ax];
+        }
+        if (!inside) a.jets.cell[j][0] = a.jets.cell[j][1] = a.jets.cell[j][2] = -1;
+      }
+      a.src.wdt_vol = cfg->dt * kStageW[k] * vol;
+      a.U = U[k];
+      a.Uout = (k == 2) ? U[0] : U[k + 1];
+      a.a = kA[k];
+      a.b = kB[k];
+      a.reduce_speed = (k == 0);
+      for (int dir = 0; dir < 3 && err == cudaSuccess; ++dir) {
+        a.count_floors = (dir == 0);
+        err = hydro::launch_sweep(cfg->precision, cfg->weno_order, dir, a, stream);
+      }
+    }
+  }
+  if (err != cudaSuccess) return HYDRO_ECUDA;
+  DevDiag d;
+  err = cudaMemcpyAsync(&d, diag, sizeof(d), cudaMemcpyDeviceToHost, stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(stream);
+  if (err != cudaSuccess) return HYDRO_ECUDA;
+  if (diag_out) {
+    std::memset(diag_out, 0, sizeof(*diag_out));
+    diag_out->t = cfg->t0 + (double)(step0 + nsteps) * cfg->dt;
+    diag_out->steps = step0 + nsteps;
+    std::memcpy(&diag_out->max_speed, &d.vmax_bits, sizeof(double));
+    diag_out->floor_hits = (int64_t)d.floor_hits;
+    diag_out->njet = njet;
+    for (int j = 0; j < HYDRO_MAX_JETS; ++j)
+      for (int ax = 0; ax < 3; ++ax) diag_out->jet_cell[j][ax] = j < njet ? d.cell[j][ax] : -1;
+    for (int j = 0; j < njet; ++j) {
+      diag_out->dep_E += d.dep[j];
+      for (int ax = 0; ax < 3; ++ax) diag_out->dep_M[ax] += jn[j][ax] * d.dep[j];
+    }
+    diag_out->status = d.status;
+  }
+  if (d.status != 0) return (hydro_status)d.status;
+  if (cfg->cfl_limit > 0.0 && nsteps > 0) {
+    double vmax;
+    std::memcpy(&vmax, &d.vmax_bits, sizeof(vmax));
+    if (vmax * cfg->dt / cfg->dx > cfg->cfl_limit) return HYDRO_ECFL;
+  }
+  return HYDRO_OK;
+}
