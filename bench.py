@@ -37,11 +37,13 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-updates/s per RK3 step at 256^3 (FP64 vs FP32); % of HBM roofline"
 UNIT = "cell-updates/s"
 
-# Algorithmic work per cell for one directional sweep of one RK3 stage (design
-# notes, "Roofline"): FLOPs with FMA = 2 and division / square root = 1.
-FLOP_PER_CELL_SWEEP = 1645          # x and y sweeps
-FLOP_PER_CELL_SWEEP_FINAL = 1665    # z sweep: + source check and stage combination
-FLOP_PER_CELL_STEP = 3 * (2 * FLOP_PER_CELL_SWEEP + FLOP_PER_CELL_SWEEP_FINAL)
+# Algorithmic work per cell of one directional sweep of one RK3 stage (FLOPs
+# with FMA = 2, division and square root = 1; breakdown in the design notes):
+# one interface (LLF split 141 + 10 WENO7 reconstructions x 122 + 5) = 1366,
+# the flux difference, and the per-cell terms the sweep carries (x: primitive
+# recovery, |v|^2, rho_x and F_x; y, z: rho_d and F_d; z: stage combination).
+FLOP_PER_CELL = {"sweep_x": 1428, "sweep_y": 1405, "sweep_z": 1425}
+FLOP_PER_CELL_STEP = 3 * sum(FLOP_PER_CELL.values())
 # Algorithmic HBM bytes per cell per step: 40 field accesses (stage 1 reads 5 and
 # writes 5; stages 2 and 3 read 10 and write 5) in storage precision.
 FIELD_ACCESSES_PER_CELL_STEP = 40
@@ -209,7 +211,7 @@ def _roofline(prof, cells, precision):
     dom = max(prof, key=lambda k: prof[k]["ms"])
     p = prof[dom]
     avg_s = p["ms"] / 1e3 / max(p["launches"], 1)
-    flop = cells * (FLOP_PER_CELL_SWEEP_FINAL if dom == "sweep_z" else FLOP_PER_CELL_SWEEP)
+    flop = cells * FLOP_PER_CELL[dom]
     achieved = flop / avg_s / 1e12
     peak = PEAK_FP64_TFLOPS if precision == "fp64" else PEAK_FP32_TFLOPS
     total_ms = sum(v["ms"] for v in prof.values())
