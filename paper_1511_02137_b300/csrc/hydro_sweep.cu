@@ -30,17 +30,20 @@
 
 namespace hydro {
 
+// Storage type of the state, arithmetic type of the fluxes, and the math
+// policy of the flux arithmetic.  Mixed: FP64 storage and RK3 accumulation,
+// FP64 for the cancelling part of the primitive recovery, FP32 for the rest.
 template <int PREC> struct Types;
-template <> struct Types<HYDRO_FP64> { using Store = double; using Prim = double; using Flux = double; };
-template <> struct Types<HYDRO_FP32> { using Store = float; using Prim = float; using Flux = float; };
-template <> struct Types<HYDRO_MIXED> { using Store = double; using Prim = double; using Flux = float; };
+template <> struct Types<HYDRO_FP64> { using Store = double; using Flux = double; using Math = MathD; };
+template <> struct Types<HYDRO_FP32> { using Store = float; using Flux = float; using Math = MathF; };
+template <> struct Types<HYDRO_MIXED> { using Store = double; using Flux = float; using Math = MathF; };
 
 // Tile shape per sweep axis: SEG cells along the sweep axis, LANES lines.  The
 // lines of the y and z sweeps run along x so that loads stay coalesced.
 template <int DIR> struct Tile;
 template <> struct Tile<0> { static constexpr int SEG = 64, LANES = 4; };
-template <> struct Tile<1> { static constexpr int SEG = 16, LANES = 16; };
-template <> struct Tile<2> { static constexpr int SEG = 16, LANES = 16; };
+template <> struct Tile<1> { static constexpr int SEG = 32, LANES = 8; };
+template <> struct Tile<2> { static constexpr int SEG = 32, LANES = 8; };
 
 constexpr int kThreads = 256;
 
@@ -84,8 +87,8 @@ __device__ __forceinline__ void publish_block(double vmax, unsigned hits, DevDia
 template <int PREC, int ORDER, int DIR, bool FINAL>
 __global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a) {
   using Store = typename Types<PREC>::Store;
-  using Prim = typename Types<PREC>::Prim;
   using F = typename Types<PREC>::Flux;
+  using Math = typename Types<PREC>::Math;
   constexpr int SEG = Tile<DIR>::SEG;
   constexpr int LANES = Tile<DIR>::LANES;
   constexpr int G = (ORDER == 7) ? 4 : 3;   // halo width = half the interface stencil
@@ -122,8 +125,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a) {
 
   // ---------------- phase 1: stage cells, primitives, half fluxes, rho
   const Store* __restrict__ U = static_cast<const Store*>(a.U);
-  const Prim e_floor = (Prim)a.e_floor;
-  double vmax = 0.0;
+  F vmax = F(0);
   unsigned hits = 0;
   for (int c = threadIdx.x; c < NCS; c += kThreads) {
     int lane, s;
@@ -132,36 +134,40 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a) {
     const int ga = a0 - G + s;
     const int gl = l0 + lane;
     const size_t o = offset(map_along(ga, n_along, a.periodic), gl < n_lane ? gl : n_lane - 1);
-    const Prim E = (Prim)U[o], Mx = (Prim)U[N + o], My = (Prim)U[2 * N + o], Mz = (Prim)U[3 * N + o];
-    const Prim R = (Prim)U[4 * N + o];
-    Prim e, vx, vy, vz;
+    const Store Es = U[o], Mxs = U[N + o], Mys = U[2 * N + o], Mzs = U[3 * N + o], Rs = U[4 * N + o];
+    F e, vx, vy, vz;
     int hit = 0;
-    cons_to_prim(E, Mx, My, Mz, e_floor, e, vx, vy, vz, hit);
-    const Prim p = e * Prim(1.0 / 3.0);
-    const Prim vd = DIR == 0 ? vx : (DIR == 1 ? vy : vz);
-    const Prim rho = spectral_radius(vd, vx * vx + vy * vy + vz * vz);
-    const Prim Md = DIR == 0 ? Mx : (DIR == 1 ? My : Mz);
-    sU[0 * NCS + c] = (F)E;
-    sU[1 * NCS + c] = (F)Mx;
-    sU[2 * NCS + c] = (F)My;
-    sU[3 * NCS + c] = (F)Mz;
-    sU[4 * NCS + c] = (F)R;
-    sF[0 * NCS + c] = (F)(Prim(0.5) * Md);
-    sF[1 * NCS + c] = (F)(Prim(0.5) * (Mx * vd + (DIR == 0 ? p : Prim(0))));
-    sF[2 * NCS + c] = (F)(Prim(0.5) * (My * vd + (DIR == 1 ? p : Prim(0))));
-    sF[3 * NCS + c] = (F)(Prim(0.5) * (Mz * vd + (DIR == 2 ? p : Prim(0))));
-    sF[4 * NCS + c] = (F)(Prim(0.5) * (R * vd));
-    sR[c] = (F)rho;
+    if constexpr (PREC == HYDRO_MIXED) {
+      cons_to_prim_mixed(Es, Mxs, Mys, Mzs, a.e_floor, e, vx, vy, vz, hit);
+    } else {
+      cons_to_prim<Math>(Es, Mxs, Mys, Mzs, (F)a.e_floor, e, vx, vy, vz, hit);
+    }
+    const F E = (F)Es, Mx = (F)Mxs, My = (F)Mys, Mz = (F)Mzs, R = (F)Rs;
+    const F p = e * F(1.0 / 3.0);
+    const F vd = DIR == 0 ? vx : (DIR == 1 ? vy : vz);
+    const F rho = spectral_radius<Math>(vd, vx * vx + vy * vy + vz * vz);
+    const F Md = DIR == 0 ? Mx : (DIR == 1 ? My : Mz);
+    sU[0 * NCS + c] = E;
+    sU[1 * NCS + c] = Mx;
+    sU[2 * NCS + c] = My;
+    sU[3 * NCS + c] = Mz;
+    sU[4 * NCS + c] = R;
+    sF[0 * NCS + c] = F(0.5) * Md;
+    sF[1 * NCS + c] = F(0.5) * (Mx * vd + (DIR == 0 ? p : F(0)));
+    sF[2 * NCS + c] = F(0.5) * (My * vd + (DIR == 1 ? p : F(0)));
+    sF[3 * NCS + c] = F(0.5) * (Mz * vd + (DIR == 2 ? p : F(0)));
+    sF[4 * NCS + c] = F(0.5) * (R * vd);
+    sR[c] = rho;
     if (s >= G && s < G + SEG && ga < n_along && gl < n_lane) {
-      vmax = fmax(vmax, (double)rho);
+      vmax = fmax(vmax, rho);
       hits += (unsigned)hit;
     }
   }
-  if (a.reduce_speed || a.count_floors) publish_block(vmax, hits, a.diag, a.reduce_speed, a.count_floors);
+  if (a.reduce_speed || a.count_floors) publish_block((double)vmax, hits, a.diag, a.reduce_speed, a.count_floors);
   __syncthreads();
 
   // ---------------- phase 2: numerical flux at every interface of the tile
-  const F eps = (ORDER == 7) ? (F)(720.0 * a.eps) : (F)a.eps;
+  const F eps = (ORDER == 7) ? (F)(kW7EpsScale * a.eps) : (F)(kW5EpsScale * a.eps);
   for (int it = threadIdx.x; it < NIF; it += kThreads) {
     int lane, j;
     if (DIR == 0) { lane = it / (SEG + 1); j = it - lane * (SEG + 1); }
@@ -244,7 +250,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a) {
           // Eq. 3 at the temperature of this cell, deposited as in Eq. 2
           double e, vx, vy, vz;
           int hit = 0;
-          cons_to_prim<double>((double)U[o], (double)U[N + o], (double)U[2 * N + o], (double)U[3 * N + o],
+          cons_to_prim<MathD>((double)U[o], (double)U[N + o], (double)U[2 * N + o], (double)U[3 * N + o],
                                a.e_floor, e, vx, vy, vz, hit);
           const double T = temperature(e, a.src.t4coef);
           const double S0 = (a.src.rad * T * T * T * a.jets.ell[jn] + a.src.coll * T * T) * a.src.inv_vol;
@@ -357,7 +363,7 @@ __global__ void readback_kernel(int kind, const Store* __restrict__ U, double* _
     } else {
       double e, vx, vy, vz;
       int hit = 0;
-      cons_to_prim<double>(E, Mx, My, Mz, e_floor, e, vx, vy, vz, hit);
+      cons_to_prim<MathD>(E, Mx, My, Mz, e_floor, e, vx, vy, vz, hit);
       const double v2 = vx * vx + vy * vy + vz * vz;
       const double ig = sqrt(1.0 - v2);   // 1/gamma
       const double g = 1.0 / ig;
