@@ -156,6 +156,60 @@ enum {
 hydro_status hydro_profile_enable(hydro_ctx* ctx, int32_t on);
 hydro_status hydro_profile_query(hydro_ctx* ctx, int32_t kind, double* total_ms, int64_t* launches);
 
+/* ---------------------------------------------------------------------------
+ * Batched ensembles: nevents grids of uneven sizes advanced together (the
+ * ensemble form of the same step; BASELINE's batched configuration).  All
+ * grids share the configuration (precision, boundary, dx, dt, t0, Eq. 3
+ * constants, WENO7 only); nx/ny/nz of cfg are ignored, dims[3*e .. 3*e+2] give
+ * grid e.  Each sweep of each RK3 stage is one persistent launch over the tiles
+ * of all grids, and hydro_batch_step records up to 64 steps into one CUDA graph
+ * that it replays.  Device work runs on a stream the batch creates; calls
+ * synchronise cfg->cuda_stream first and their own stream before returning.
+ * Results are identical to advancing each grid with hydro_step.
+ * ------------------------------------------------------------------------- */
+typedef struct hydro_batch hydro_batch;
+
+/* Device bytes a batch needs (states, accumulator, diagnostics, tile and jet
+ * tables).  HYDRO_EINVAL for a bad configuration, nevents < 1, a zero
+ * dimension, or weno_order other than 7. */
+hydro_status hydro_batch_workspace_size(const hydro_config* cfg, int32_t nevents, const int32_t* dims,
+                                        size_t* bytes);
+
+/* Creates a batch; the workspace comes from cfg->workspace (>= the size above,
+ * 256-byte aligned, caller-owned) or from cudaMalloc.  Errors as hydro_create. */
+hydro_status hydro_batch_create(const hydro_config* cfg, int32_t nevents, const int32_t* dims, hydro_batch** out);
+
+/* Initial state of grid `event` (as hydro_set_initial); resets the batch's
+ * step counter.  Every grid needs one before stepping (else HYDRO_ESTATE). */
+hydro_status hydro_batch_set_initial(hydro_batch* b, int32_t event, int32_t kind, const double* host5);
+
+/* Adds a jet to grid `event` (as hydro_add_jet, up to HYDRO_MAX_JETS per grid). */
+hydro_status hydro_batch_add_jet(hydro_batch* b, int32_t event, const double x0[3], const double dir[3],
+                                 double t_start, int32_t* jet_id);
+
+/* Selects the tile shape of each sweep axis (0..2 per axis; see
+ * hydro_batch_autotune).  HYDRO_EINVAL for an unknown shape. */
+hydro_status hydro_batch_set_tiles(hydro_batch* b, const int32_t variant[3]);
+
+/* Times every compiled tile shape of each sweep axis on this ensemble (three
+ * first-stage launches each, writing only scratch) and keeps the fastest.
+ * variant_out (may be NULL) receives the choice per axis, ms_out (may be NULL)
+ * the 9 times in ms, axis-major.  Needs every grid initialised. */
+hydro_status hydro_batch_autotune(hydro_batch* b, int32_t variant_out[3], double ms_out[9]);
+
+/* Advances every grid by nsteps SSP-RK3 steps; statuses as hydro_step (the
+ * first error over the grids). */
+hydro_status hydro_batch_step(hydro_batch* b, int32_t nsteps);
+
+/* Fields of grid `event` (as hydro_read_fields). */
+hydro_status hydro_batch_read_fields(hydro_batch* b, int32_t event, int32_t kind, double* host5);
+
+/* Diagnostics of grid `event` (as hydro_get_diag). */
+hydro_status hydro_batch_get_diag(hydro_batch* b, int32_t event, hydro_diag* out);
+
+/* Releases a batch; NULL is a no-op. */
+void hydro_batch_destroy(hydro_batch* b);
+
 /* Largest grid (nx*ny*nz cells) that hydro_step_noalloc accepts. */
 #define HYDRO_NOALLOC_MAX_CELLS 65536
 

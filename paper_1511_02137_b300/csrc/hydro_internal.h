@@ -38,7 +38,8 @@ struct SourceCoef {
   double wdt_vol; // dt * RK3 weight of the stage * dx^3 (deposit diagnostic)
 };
 
-struct SweepArgs {
+// Everything a sweep tile needs except the jet list.
+struct GridArgs {
   const void* U;    // state the right-hand side is evaluated on
   const void* U0;   // state at the start of the step (stage combination)
   void* Uout;       // combined stage result (z sweep only)
@@ -53,9 +54,52 @@ struct SweepArgs {
   double eps;       // WENO epsilon
   int reduce_speed; // 1: fold spectral radii into diag->vmax_bits
   int count_floors; // 1: count floor hits (x sweep of each stage)
-  JetStage jets;
   SourceCoef src;
 };
+
+// Arguments of a single-grid sweep launch.
+struct SweepArgs : GridArgs {
+  JetStage jets;
+};
+
+// One grid of a batched ensemble: its size and where its fields start.
+struct BatchEvent {
+  int nx, ny, nz;
+  int pad;
+  size_t off;       // element offset of the grid's 5 fields in every state array
+};
+
+// Arguments of a batched (persistent) sweep launch: one launch covers every
+// tile of every grid; tiles are (event, a0, l0, fixed).
+struct BatchArgs {
+  const BatchEvent* events;
+  const int4* tiles;
+  int ntiles;
+  int periodic;
+  const void* U;    // base of the concatenated state arrays
+  const void* U0;
+  void* Uout;
+  void* rhs;
+  DevDiag* diags;   // one per event
+  const JetStage* jets;   // one per event, for this stage
+  double inv_dx, dt, a, b, e_floor, eps;
+  int reduce_speed, count_floors;
+  SourceCoef src;
+};
+
+// Tile shapes the batched sweeps can use (index = autotuner choice):
+// x sweep (SEG along x, LANES rows), y and z sweeps (SEG along the axis, LANES x-lanes).
+constexpr int kBatchVariants = 3;
+constexpr int kTileSegX[kBatchVariants] = {64, 32, 128};
+constexpr int kTileLanesX[kBatchVariants] = {4, 8, 2};
+constexpr int kTileSegYZ[kBatchVariants] = {32, 16, 64};
+constexpr int kTileLanesYZ[kBatchVariants] = {8, 16, 4};
+
+cudaError_t launch_batch_sweep(int precision, int dir, int variant, const BatchArgs& a, int grid, cudaStream_t s);
+// Blocks per SM the batched sweep kernel reaches (0 on error).
+int batch_sweep_blocks_per_sm(int precision, int dir, int variant);
+// Zeroes the per-step maximum signal speed of n diagnostics blocks.
+cudaError_t launch_reset_vmax(DevDiag* diags, int n, cudaStream_t s);
 
 // Launches one directional sweep (dir 0/1/2) for the given precision
 // (0 FP64, 1 FP32, 2 mixed) and WENO order (7 or 5).

@@ -39,7 +39,7 @@ struct MathF {
 
 // Closed-form conserved -> primitive recovery for p = e/3.
 // With m = |M|/E the EOS gives m = 4v/(3+v^2), so v = 3m/(2 + sqrt(4-3m^2)),
-// e = E (1 - m v), p = e/3 and v^i = v M^i/|M| = 3 M^i / (E (2 + sqrt(4-3m^2))).
+// e = E (1 - m v), p = e/3 and v^i = v M^i/|M| = 3 (m/|M|) M^i / (2 + sqrt(4-3m^2)).
 // E below e_floor is raised to e_floor and m is capped below 1; either floor
 // sets hit.  The stored state is never modified.
 template <class M>
@@ -55,14 +55,16 @@ __device__ __forceinline__ void cons_to_prim(typename M::T E, typename M::T Mx, 
   }
   const P invE = M::rcp(Ee);
   P m = Mabs * invE;
+  P m_over_M = invE;   // m / |M|, so that v / |M| = 3 r m / |M| stays finite for M = 0
   if (!(m <= M::m_max)) {
     m = M::m_max;
+    m_over_M = m / Mabs;
     hit = 1;
   }
   const P r = M::rcp(P(2) + M::sqrt(P(4) - P(3) * m * m));
   const P v = P(3) * m * r;
   e = Ee * (P(1) - m * v);
-  const P vs = P(3) * invE * r;   // v / |M|, finite for M = 0
+  const P vs = P(3) * m_over_M * r;   // v / |M|
   vx = Mx * vs;
   vy = My * vs;
   vz = Mz * vs;
@@ -85,8 +87,10 @@ __device__ __forceinline__ void cons_to_prim_mixed(double E, double Mx, double M
   const float invE = rcp_approx(Ef);
   float om = (float)(Ee - Mabs) * invE;
   const float om_min = (float)(1.0 - MathD::m_max);
+  float m_over_M = invE;   // m / |M|
   if (!(om >= om_min)) {
     om = om_min;
+    m_over_M = (1.0f - om) / (float)Mabs;
     hit = 1;
   }
   const float s = sqrt_approx(1.0f + 3.0f * om * (2.0f - om));
@@ -94,7 +98,7 @@ __device__ __forceinline__ void cons_to_prim_mixed(double E, double Mx, double M
   const float omv = 3.0f * om * (1.0f + (2.0f - om) * rcp_approx(s + 1.0f)) * r;   // 1 - v
   const float v = 1.0f - omv;
   e = Ef * (omv + v * om);
-  const float vs = 3.0f * invE * r;
+  const float vs = 3.0f * m_over_M * r;   // v / |M|
   vx = (float)Mx * vs;
   vy = (float)My * vs;
   vz = (float)Mz * vs;

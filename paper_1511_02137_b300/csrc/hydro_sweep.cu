@@ -84,20 +84,22 @@ __device__ __forceinline__ void publish_block(double vmax, unsigned hits, DevDia
   }
 }
 
-template <int PREC, int ORDER, int DIR, bool FINAL>
-__global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a) {
+// One tile of a sweep: SEG cells along the sweep axis starting at a0, LANES
+// lines starting at l0, in plane `fixed` (z for the x and y sweeps, y for the z
+// sweep).  Must be reached by every thread of the block; shared memory is free
+// again when it returns.
+template <int PREC, int ORDER, int DIR, bool FINAL, int SEG, int LANES>
+__device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& jets, int a0, int l0, int fixed,
+                                           unsigned char* smem_raw) {
   using Store = typename Types<PREC>::Store;
   using F = typename Types<PREC>::Flux;
   using Math = typename Types<PREC>::Math;
-  constexpr int SEG = Tile<DIR>::SEG;
-  constexpr int LANES = Tile<DIR>::LANES;
   constexpr int G = (ORDER == 7) ? 4 : 3;   // halo width = half the interface stencil
   constexpr int W = SEG + 2 * G;            // staged cells per line
   constexpr int NCS = LANES * W;            // staged cells
   constexpr int NIF = LANES * (SEG + 1);    // interfaces
   constexpr int NC = LANES * SEG;           // updated cells
 
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   F* sU = reinterpret_cast<F*>(smem_raw);   // [5][NCS] conserved
   F* sF = sU + 5 * NCS;                     // [5][NCS] F_d / 2
   F* sR = sF + 5 * NCS;                     // [NCS]    rho_d
@@ -105,14 +107,8 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a) {
 
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const size_t N = (size_t)nx * ny * nz;
-  int a0, l0, fixed, n_along, n_lane;
-  if (DIR == 0) {
-    a0 = blockIdx.x * SEG; l0 = blockIdx.y * LANES; fixed = blockIdx.z; n_along = nx; n_lane = ny;
-  } else if (DIR == 1) {
-    l0 = blockIdx.x * LANES; a0 = blockIdx.y * SEG; fixed = blockIdx.z; n_along = ny; n_lane = nx;
-  } else {
-    l0 = blockIdx.x * LANES; a0 = blockIdx.y * SEG; fixed = blockIdx.z; n_along = nz; n_lane = nx;
-  }
+  const int n_along = DIR == 0 ? nx : (DIR == 1 ? ny : nz);
+  const int n_lane = DIR == 0 ? ny : nx;
   auto offset = [&](int along, int lane) -> size_t {
     if (DIR == 0) return ((size_t)fixed * ny + lane) * nx + along;
     if (DIR == 1) return ((size_t)fixed * ny + along) * nx + lane;
@@ -205,8 +201,8 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a) {
   // ---------------- phase 3: flux difference, source, stage combination
   bool jets_here = false;
   if (FINAL) {
-    for (int jn = 0; jn < a.jets.n; ++jn) {
-      const int* cl = a.jets.cell[jn];
+    for (int jn = 0; jn < jets.n; ++jn) {
+      const int* cl = jets.cell[jn];
       if (cl[0] < 0) continue;
       const int jal = DIR == 0 ? cl[0] : (DIR == 1 ? cl[1] : cl[2]);
       const int jln = DIR == 0 ? cl[1] : cl[0];
@@ -244,8 +240,8 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a) {
         const int gx = DIR == 0 ? ga : gl;
         const int gy = DIR == 1 ? ga : (DIR == 0 ? gl : fixed);
         const int gz = DIR == 2 ? ga : fixed;
-        for (int jn = 0; jn < a.jets.n; ++jn) {
-          const int* cl = a.jets.cell[jn];
+        for (int jn = 0; jn < jets.n; ++jn) {
+          const int* cl = jets.cell[jn];
           if (cl[0] != gx || cl[1] != gy || cl[2] != gz) continue;
           // Eq. 3 at the temperature of this cell, deposited as in Eq. 2
           double e, vx, vy, vz;
@@ -253,11 +249,11 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a) {
           cons_to_prim<MathD>((double)U[o], (double)U[N + o], (double)U[2 * N + o], (double)U[3 * N + o],
                                a.e_floor, e, vx, vy, vz, hit);
           const double T = temperature(e, a.src.t4coef);
-          const double S0 = (a.src.rad * T * T * T * a.jets.ell[jn] + a.src.coll * T * T) * a.src.inv_vol;
+          const double S0 = (a.src.rad * T * T * T * jets.ell[jn] + a.src.coll * T * T) * a.src.inv_vol;
           Ld[0] += S0;
-          Ld[1] += a.jets.dir[jn][0] * S0;
-          Ld[2] += a.jets.dir[jn][1] * S0;
-          Ld[3] += a.jets.dir[jn][2] * S0;
+          Ld[1] += jets.dir[jn][0] * S0;
+          Ld[2] += jets.dir[jn][1] * S0;
+          Ld[3] += jets.dir[jn][2] * S0;
           a.diag->dep[jn] += a.src.wdt_vol * S0;
           a.diag->cell[jn][0] = gx;
           a.diag->cell[jn][1] = gy;
@@ -279,6 +275,58 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a) {
     }
   }
   if (FINAL && bad) atomicCAS(&a.diag->status, 0, (int)HYDRO_EUNPHYSICAL);
+}
+
+template <int PREC, int ORDER, int DIR, bool FINAL>
+__global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int SEG = Tile<DIR>::SEG, LANES = Tile<DIR>::LANES;
+  int a0, l0;
+  if (DIR == 0) {
+    a0 = blockIdx.x * SEG; l0 = blockIdx.y * LANES;
+  } else {
+    l0 = blockIdx.x * LANES; a0 = blockIdx.y * SEG;
+  }
+  sweep_tile<PREC, ORDER, DIR, FINAL, SEG, LANES>(a, a.jets, a0, l0, blockIdx.z, smem_raw);
+}
+
+// Batched sweep: a persistent grid walks the tile list of all grids of the
+// ensemble; each tile finds its grid's size and field offset in the event table.
+template <int PREC, int DIR, bool FINAL, int SEG, int LANES>
+__global__ void __launch_bounds__(kThreads) batch_sweep_kernel(const BatchArgs b) {
+  using Store = typename Types<PREC>::Store;
+  using F = typename Types<PREC>::Flux;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
+    const int4 td = b.tiles[t];
+    const BatchEvent ev = b.events[td.x];
+    GridArgs g;
+    g.U = static_cast<const Store*>(b.U) + ev.off;
+    g.U0 = static_cast<const Store*>(b.U0) + ev.off;
+    g.Uout = static_cast<Store*>(b.Uout) + ev.off;
+    g.rhs = static_cast<F*>(b.rhs) + ev.off;
+    g.diag = b.diags + td.x;
+    g.nx = ev.nx;
+    g.ny = ev.ny;
+    g.nz = ev.nz;
+    g.periodic = b.periodic;
+    g.inv_dx = b.inv_dx;
+    g.dt = b.dt;
+    g.a = b.a;
+    g.b = b.b;
+    g.e_floor = b.e_floor;
+    g.eps = b.eps;
+    g.reduce_speed = b.reduce_speed;
+    g.count_floors = b.count_floors;
+    g.src = b.src;
+    sweep_tile<PREC, 7, DIR, FINAL, SEG, LANES>(g, b.jets[td.x], td.y, td.z, td.w, smem_raw);
+    __syncthreads();   // the next tile overwrites shared memory
+  }
+}
+
+__global__ void reset_vmax_kernel(DevDiag* d, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d[i].vmax_bits = 0ull;
 }
 
 template <int PREC, int ORDER, int DIR>
@@ -317,6 +365,102 @@ cudaError_t launch_sweep(int precision, int order, int dir, const SweepArgs& a, 
     case HYDRO_FP32: return launch_order<HYDRO_FP32>(order, dir, a, s);
     default: return launch_order<HYDRO_MIXED>(order, dir, a, s);
   }
+}
+
+// ---------------------------------------------------------------- batched launches
+
+template <int PREC, int DIR, int SEG, int LANES>
+static constexpr size_t batch_smem() {
+  using F = typename Types<PREC>::Flux;
+  return sizeof(F) * (size_t)(11 * LANES * (SEG + 8) + 5 * LANES * (SEG + 1));
+}
+
+template <int PREC, int DIR, int SEG, int LANES>
+static auto batch_kernel_ptr() {
+  return batch_sweep_kernel<PREC, DIR, DIR == 2, SEG, LANES>;
+}
+
+template <int PREC, int DIR, int V>
+static cudaError_t batch_launch_v(const BatchArgs& a, int grid, cudaStream_t s) {
+  constexpr int SEG = DIR == 0 ? kTileSegX[V] : kTileSegYZ[V];
+  constexpr int LANES = DIR == 0 ? kTileLanesX[V] : kTileLanesYZ[V];
+  constexpr size_t smem = batch_smem<PREC, DIR, SEG, LANES>();
+  auto kern = batch_kernel_ptr<PREC, DIR, SEG, LANES>();
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  kern<<<grid, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int PREC, int DIR, int V>
+static int batch_occupancy_v() {
+  constexpr int SEG = DIR == 0 ? kTileSegX[V] : kTileSegYZ[V];
+  constexpr int LANES = DIR == 0 ? kTileLanesX[V] : kTileLanesYZ[V];
+  constexpr size_t smem = batch_smem<PREC, DIR, SEG, LANES>();
+  auto kern = batch_kernel_ptr<PREC, DIR, SEG, LANES>();
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kThreads, smem) != cudaSuccess) return 0;
+  return n;
+}
+
+template <int PREC, int DIR>
+static cudaError_t batch_launch_dir(int variant, const BatchArgs& a, int grid, cudaStream_t s) {
+  switch (variant) {
+    case 0: return batch_launch_v<PREC, DIR, 0>(a, grid, s);
+    case 1: return batch_launch_v<PREC, DIR, 1>(a, grid, s);
+    default: return batch_launch_v<PREC, DIR, 2>(a, grid, s);
+  }
+}
+
+template <int PREC, int DIR>
+static int batch_occupancy_dir(int variant) {
+  switch (variant) {
+    case 0: return batch_occupancy_v<PREC, DIR, 0>();
+    case 1: return batch_occupancy_v<PREC, DIR, 1>();
+    default: return batch_occupancy_v<PREC, DIR, 2>();
+  }
+}
+
+template <int PREC>
+static cudaError_t batch_launch_prec(int dir, int variant, const BatchArgs& a, int grid, cudaStream_t s) {
+  switch (dir) {
+    case 0: return batch_launch_dir<PREC, 0>(variant, a, grid, s);
+    case 1: return batch_launch_dir<PREC, 1>(variant, a, grid, s);
+    default: return batch_launch_dir<PREC, 2>(variant, a, grid, s);
+  }
+}
+
+template <int PREC>
+static int batch_occupancy_prec(int dir, int variant) {
+  switch (dir) {
+    case 0: return batch_occupancy_dir<PREC, 0>(variant);
+    case 1: return batch_occupancy_dir<PREC, 1>(variant);
+    default: return batch_occupancy_dir<PREC, 2>(variant);
+  }
+}
+
+cudaError_t launch_batch_sweep(int precision, int dir, int variant, const BatchArgs& a, int grid, cudaStream_t s) {
+  if (grid <= 0 || a.ntiles <= 0) return cudaSuccess;
+  switch (precision) {
+    case HYDRO_FP64: return batch_launch_prec<HYDRO_FP64>(dir, variant, a, grid, s);
+    case HYDRO_FP32: return batch_launch_prec<HYDRO_FP32>(dir, variant, a, grid, s);
+    default: return batch_launch_prec<HYDRO_MIXED>(dir, variant, a, grid, s);
+  }
+}
+
+int batch_sweep_blocks_per_sm(int precision, int dir, int variant) {
+  switch (precision) {
+    case HYDRO_FP64: return batch_occupancy_prec<HYDRO_FP64>(dir, variant);
+    case HYDRO_FP32: return batch_occupancy_prec<HYDRO_FP32>(dir, variant);
+    default: return batch_occupancy_prec<HYDRO_MIXED>(dir, variant);
+  }
+}
+
+cudaError_t launch_reset_vmax(DevDiag* diags, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  reset_vmax_kernel<<<(n + 127) / 128, 128, 0, s>>>(diags, n);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- initial state and read-back

@@ -75,8 +75,23 @@ def _lib():
         lib.hydro_destroy.restype = None
         lib.hydro_status_string.argtypes = [ctypes.c_int]
         lib.hydro_status_string.restype = ctypes.c_char_p
+        i32p = P(ctypes.c_int32)
+        lib.hydro_batch_workspace_size.argtypes = [P(hydro_config), ctypes.c_int32, i32p, P(ctypes.c_size_t)]
+        lib.hydro_batch_create.argtypes = [P(hydro_config), ctypes.c_int32, i32p, P(vp)]
+        lib.hydro_batch_set_initial.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, vp]
+        lib.hydro_batch_add_jet.argtypes = [vp, ctypes.c_int32, dp, dp, ctypes.c_double, i32p]
+        lib.hydro_batch_set_tiles.argtypes = [vp, i32p]
+        lib.hydro_batch_autotune.argtypes = [vp, i32p, dp]
+        lib.hydro_batch_step.argtypes = [vp, ctypes.c_int32]
+        lib.hydro_batch_read_fields.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, vp]
+        lib.hydro_batch_get_diag.argtypes = [vp, ctypes.c_int32, P(hydro_diag)]
+        lib.hydro_batch_destroy.argtypes = [vp]
+        lib.hydro_batch_destroy.restype = None
         for name in ("hydro_workspace_size", "hydro_create", "hydro_set_initial", "hydro_add_jet", "hydro_step",
-                     "hydro_read_fields", "hydro_get_diag", "hydro_profile_enable", "hydro_profile_query"):
+                     "hydro_read_fields", "hydro_get_diag", "hydro_profile_enable", "hydro_profile_query",
+                     "hydro_batch_workspace_size", "hydro_batch_create", "hydro_batch_set_initial",
+                     "hydro_batch_add_jet", "hydro_batch_set_tiles", "hydro_batch_autotune", "hydro_batch_step",
+                     "hydro_batch_read_fields", "hydro_batch_get_diag"):
             getattr(lib, name).restype = ctypes.c_int
         _LIB = lib
     return _LIB
@@ -202,3 +217,106 @@ def hydro_destroy(ctx: Context) -> None:
     if ctx.handle:
         _lib().hydro_destroy(ctx.handle)
         ctx.handle = None
+
+
+# ---------------------------------------------------------------- batched ensembles
+
+
+class Batch:
+    """Opaque hydro_batch plus the torch workspace tensor that backs it."""
+
+    def __init__(self, handle, cfg, dims, workspace):
+        self.handle = handle
+        self.cfg = cfg
+        self.dims = [tuple(int(v) for v in d) for d in dims]
+        self.workspace = workspace
+        self.cells = [d[0] * d[1] * d[2] for d in self.dims]
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            hydro_batch_destroy(self)
+
+
+def _dims_array(dims):
+    flat = [int(v) for d in dims for v in d]
+    return (ctypes.c_int32 * len(flat))(*flat), len(dims)
+
+
+def hydro_batch_workspace_size(cfg: hydro_config, dims) -> int:
+    arr, n = _dims_array(dims)
+    size = ctypes.c_size_t()
+    _check(_lib().hydro_batch_workspace_size(ctypes.byref(cfg), n, arr, ctypes.byref(size)),
+           "hydro_batch_workspace_size")
+    return size.value
+
+
+def hydro_batch_create(cfg: hydro_config, dims, device=None, stream=None) -> Batch:
+    """Creates a batch over grids `dims` [(nx, ny, nz), ...] with a torch CUDA
+    workspace; `stream` (default: torch's current stream) is the one the calls
+    order themselves after."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    nbytes = hydro_batch_workspace_size(cfg, dims)
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+    c = hydro_config.from_buffer_copy(cfg)
+    c.workspace = (ws.data_ptr() + 255) // 256 * 256
+    c.workspace_bytes = nbytes
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    c.cuda_stream = s.cuda_stream
+    arr, n = _dims_array(dims)
+    h = ctypes.c_void_p()
+    _check(_lib().hydro_batch_create(ctypes.byref(c), n, arr, ctypes.byref(h)), "hydro_batch_create")
+    return Batch(h, c, dims, ws)
+
+
+def hydro_batch_set_initial(b: Batch, event: int, kind: int, host5) -> None:
+    _check(_lib().hydro_batch_set_initial(b.handle, event, kind, _host_ptr(host5, 5 * b.cells[event], False)),
+           "hydro_batch_set_initial")
+
+
+def hydro_batch_add_jet(b: Batch, event: int, x0, direction, t_start: float) -> int:
+    a = (ctypes.c_double * 3)(*x0)
+    d = (ctypes.c_double * 3)(*direction)
+    jid = ctypes.c_int32()
+    _check(_lib().hydro_batch_add_jet(b.handle, event, a, d, t_start, ctypes.byref(jid)), "hydro_batch_add_jet")
+    return jid.value
+
+
+def hydro_batch_set_tiles(b: Batch, variants) -> None:
+    v = (ctypes.c_int32 * 3)(*variants)
+    _check(_lib().hydro_batch_set_tiles(b.handle, v), "hydro_batch_set_tiles")
+
+
+def hydro_batch_autotune(b: Batch):
+    """Returns (chosen tile shape per axis, 3x3 launch times in ms [axis][shape])."""
+    v = (ctypes.c_int32 * 3)()
+    ms = (ctypes.c_double * 9)()
+    _check(_lib().hydro_batch_autotune(b.handle, v, ms), "hydro_batch_autotune")
+    return tuple(v), [[ms[3 * d + k] for k in range(3)] for d in range(3)]
+
+
+def hydro_batch_step(b: Batch, nsteps: int, allow=()) -> int:
+    return _check(_lib().hydro_batch_step(b.handle, nsteps), "hydro_batch_step", allow)
+
+
+def hydro_batch_read_fields(b: Batch, event: int, kind: int = HYDRO_CONSERVED, out=None):
+    nx, ny, nz = b.dims[event]
+    if out is None:
+        out = np.empty((5, nz, ny, nx), dtype=np.float64)
+    _check(_lib().hydro_batch_read_fields(b.handle, event, kind, _host_ptr(out, 5 * b.cells[event], True)),
+           "hydro_batch_read_fields")
+    return out
+
+
+def hydro_batch_get_diag(b: Batch, event: int) -> dict:
+    d = hydro_diag()
+    _check(_lib().hydro_batch_get_diag(b.handle, event, ctypes.byref(d)), "hydro_batch_get_diag")
+    return {"t": d.t, "steps": d.steps, "max_speed": d.max_speed, "floor_hits": d.floor_hits,
+            "dep_E": d.dep_E, "dep_M": tuple(d.dep_M), "njet": d.njet,
+            "jet_cells": [tuple(d.jet_cell[i]) for i in range(d.njet)], "status": d.status}
+
+
+def hydro_batch_destroy(b: Batch) -> None:
+    if b.handle:
+        _lib().hydro_batch_destroy(b.handle)
+        b.handle = None

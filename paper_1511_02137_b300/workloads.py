@@ -126,3 +126,40 @@ def scaled(w: Workload, n: int, steps: int | None = None) -> Workload:
     """Same profile on an n^3 grid with the same dx (a sub-volume of the full run)."""
     return replace(w, n=(n, n, n), steps=w.steps if steps is None else steps,
                    name=f"{w.name} [sub-grid {n}^3]")
+
+
+@dataclass(frozen=True)
+class Ensemble:
+    name: str
+    events: tuple
+    steps: int
+
+    @property
+    def cells(self) -> int:
+        return sum(w.cells for w in self.events)
+
+
+def seeded_ensemble(seed: int, count: int, edges=(64, 96, 128, 160), e0=(10.0, 50.0), sigma=(2.0, 6.0),
+                    jets=(1, 4), steps: int = 50) -> Ensemble:
+    """Events of uneven cube grids (edge drawn from `edges`), e0 and the three
+    sigmas drawn uniformly from their ranges, 1-4 jets each starting uniformly
+    in the ball of radius 0.4 x the half-width of the grid with isotropic
+    directions, t_start = t0."""
+    rng = SplitMix64(seed)
+    events = []
+    for k in range(count):
+        edge = edges[min(int(rng.uniform() * len(edges)), len(edges) - 1)]
+        e0k = e0[0] + (e0[1] - e0[0]) * rng.uniform()
+        sig = tuple(sigma[0] + (sigma[1] - sigma[0]) * rng.uniform() for _ in range(3))
+        nj = jets[0] + min(int(rng.uniform() * (jets[1] - jets[0] + 1)), jets[1] - jets[0])
+        radius = 0.4 * 0.5 * edge * 0.1
+        js = seeded_jets(rng.next_u64(), nj, radius, 1.0)
+        events.append(Workload(name=f"event {k}: {edge}^3", n=(edge, edge, edge), steps=steps, e0=e0k, sigma=sig,
+                               jets=js))
+    return Ensemble(name=f"{count}-event ensemble, edges {edges}, {steps} RK3 steps", events=tuple(events),
+                    steps=steps)
+
+
+# Batched ensemble: 64 events, cube edges from {64, 96, 128, 160}, e0 in [10, 50] GeV/fm^3,
+# sigmas in [2, 6] fm, 1-4 jets each, 50 steps.
+ENSEMBLE_64 = seeded_ensemble(15114, 64)

@@ -86,3 +86,33 @@ def test_null_arguments_are_rejected(hy):
     assert lib.hydro_read_fields(None, 0, None) == hy.HYDRO_EINVAL
     lib.hydro_destroy(None)
     assert lib.hydro_status_string(hy.HYDRO_ECFL).startswith(b"HYDRO_ECFL")
+
+
+def test_batch_workspace_size_and_validation(hy):
+    dims = [(64, 64, 64), (96, 80, 72)]
+    c = hy.hydro_config_default(1, 1, 1, precision="fp32")
+    cells = 64 ** 3 + 96 * 80 * 72
+    size = hy.hydro_batch_workspace_size(c, dims)
+    assert 4 * 5 * cells * 4 <= size < 4 * 5 * cells * 4 + (64 << 20)
+    c5 = hy.hydro_config_default(1, 1, 1, weno_order=5)
+    arr, n = hy._dims_array(dims)
+    out = ctypes.c_size_t()
+    assert hy._lib().hydro_batch_workspace_size(ctypes.byref(c5), n, arr, ctypes.byref(out)) == hy.HYDRO_EINVAL
+    bad, n = hy._dims_array([(4, 0, 4)])
+    assert hy._lib().hydro_batch_workspace_size(ctypes.byref(c), n, bad, ctypes.byref(out)) == hy.HYDRO_EINVAL
+    assert hy._lib().hydro_batch_step(None, 1) == hy.HYDRO_EINVAL
+    hy._lib().hydro_batch_destroy(None)
+
+
+def test_ensemble_recipe():
+    from paper_1511_02137_b300 import workloads as W
+    E = W.ENSEMBLE_64
+    assert len(E.events) == 64 and E.steps == 50
+    for w in E.events:
+        assert w.n[0] == w.n[1] == w.n[2] and w.n[0] in (64, 96, 128, 160)
+        assert 10.0 <= w.e0 <= 50.0 and all(2.0 <= s <= 6.0 for s in w.sigma)
+        assert 1 <= len(w.jets) <= 4
+        half = 0.5 * w.n[0] * w.dx
+        for j in w.jets:
+            assert sum(x * x for x in j.x0) ** 0.5 < 0.4 * half + 1e-12
+    assert {w.n[0] for w in E.events} == {64, 96, 128, 160}

@@ -238,3 +238,23 @@ def test_full_size_reduced_precision_stays_finite_and_close(hy, W, precision):
     err = norm_rel_err(res[precision], res["fp64"])
     print(precision, "256^3, 10 steps, error vs FP64 path per field:", err)
     assert np.all(err <= 1e-4), err
+
+
+def test_fp64_parity_when_floors_act(hy, orc, W):
+    """Cells with |M| > E (unphysical) hit the |M|/E cap: the recovered
+    velocity is v M/|M| with v from the capped ratio, on both sides."""
+    w = replace(W.ELLIPSOIDAL_32, n=(20, 18, 16), jets=())
+    U = orc.prim_to_cons(W.ellipsoidal_primitives(w))
+    U[1, 8, 9, 10] = 1.001 * U[0, 8, 9, 10]                     # |M| > E
+    U[1, 3, 4, 5], U[2, 3, 4, 5] = 0.8 * U[0, 3, 4, 5], -0.7 * U[0, 3, 4, 5]
+    cfg = hy.hydro_config_default(*w.n, precision="fp64")
+    ctx = hy.hydro_create(cfg)
+    hy.hydro_set_initial(ctx, hy.HYDRO_CONSERVED, U.ravel())
+    hy.hydro_step(ctx, 1)
+    G = hy.hydro_read_fields(ctx, hy.HYDRO_CONSERVED)
+    gd = hy.hydro_get_diag(ctx)
+    O, od = orc.run(oracle_config(orc, w), U, 1)
+    assert od.floor_hits > 0 and gd["floor_hits"] == od.floor_hits
+    assert gd["max_speed"] <= 1.0
+    err = norm_rel_err(G, O)
+    assert np.all(err <= 1e-10), err
