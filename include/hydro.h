@@ -210,6 +210,46 @@ hydro_status hydro_batch_get_diag(hydro_batch* b, int32_t event, hydro_diag* out
 /* Releases a batch; NULL is a no-op. */
 void hydro_batch_destroy(hydro_batch* b);
 
+/* ---------------------------------------------------------------------------
+ * Adjoint: gradients of a final-time observable, the energy J = sum E dx^3 in a
+ * cone (apex, axis, half angle, radius rmax) after nsteps RK3 steps, with
+ * respect to k_rad and k_coll of Eq. 3 and the initial energy density field.
+ * Reverse mode of the FP64 step written by hand (vector-Jacobian products of
+ * the WENO7 fluxes, the LLF split, the primitive recovery and the jet source),
+ * states checkpointed every `checkpoint_every` steps and recomputed segment by
+ * segment in reverse.  FP64, outflow, WENO7 only.  The derivative of the LLF
+ * alpha = max over the stencil is split equally among tying cells.
+ * ------------------------------------------------------------------------- */
+typedef struct hydro_adjoint hydro_adjoint;
+
+/* Sets up an adjoint run (allocates checkpoint, segment and adjoint buffers
+ * with cudaMalloc).  HYDRO_EINVAL unless precision = HYDRO_FP64, boundary =
+ * HYDRO_OUTFLOW and weno_order = 7, or for non-positive sizes or cone. */
+hydro_status hydro_adjoint_create(const hydro_config* cfg, int32_t nsteps, int32_t checkpoint_every,
+                                  const double apex[3], const double axis[3], double half_angle_deg, double rmax,
+                                  hydro_adjoint** out);
+
+/* Adds a jet (as hydro_add_jet). */
+hydro_status hydro_adjoint_add_jet(hydro_adjoint* a, const double x0[3], const double dir[3], double t_start);
+
+/* Changes k_rad and k_coll of Eq. 3 for the next forward run. */
+hydro_status hydro_adjoint_set_params(hydro_adjoint* a, double k_rad, double k_coll);
+
+/* Runs the forward steps from the primitive fields in device memory d_prim5
+ * (5 x nx*ny*nz doubles: e, u^x, u^y, u^z, n), keeping checkpoints, and
+ * returns the observable in *J (host). */
+hydro_status hydro_adjoint_forward(hydro_adjoint* a, const double* d_prim5, double* J);
+
+/* Reverse sweep for an upstream derivative dJ (1 for the plain gradient):
+ * writes dJ/dk_rad and dJ/dk_coll to the host doubles (may be NULL) and
+ * dJ/de(x) at fixed u^i and n to d_grad_e (device, nx*ny*nz doubles).
+ * HYDRO_ESTATE before hydro_adjoint_forward. */
+hydro_status hydro_adjoint_backward(hydro_adjoint* a, double dJ, double* grad_k_rad, double* grad_k_coll,
+                                    double* d_grad_e);
+
+/* Releases an adjoint run; NULL is a no-op. */
+void hydro_adjoint_destroy(hydro_adjoint* a);
+
 /* Largest grid (nx*ny*nz cells) that hydro_step_noalloc accepts. */
 #define HYDRO_NOALLOC_MAX_CELLS 65536
 

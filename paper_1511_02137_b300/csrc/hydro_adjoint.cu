@@ -1,0 +1,689 @@
+// Adjoint (reverse mode) of the FP64 RK3-WENO7 step with jet sources, and a
+// cone-energy observable with gradients with respect to k_rad, k_coll and the
+// initial energy density (checkpointed every k steps, recomputed in reverse).
+//
+// The vector-Jacobian product of the right-hand side L(U) = -div F + S runs as
+// three sweeps (x, y, z), like the forward.  A tile gathers, for each of its
+// cells, every contribution of the interfaces whose stencils contain the cell
+// (so the result is deterministic and needs no atomics): it recomputes alpha,
+// the split fluxes and both WENO7 reconstructions of the SEG + 8 interfaces that
+// touch its SEG cells, differentiates them in reverse (hydro_adjoint_math.cuh),
+// and chains the per-cell adjoints through the half flux F_d/2, the spectral
+// radius and the primitive recovery.  The derivative of alpha = max rho is
+// split equally among the stencil cells that tie for the maximum (to 1e-12
+// relative), the symmetric subgradient.  The z sweep adds the adjoint of the jet
+// source of Eqs. 2-3 and accumulates dJ/dk_rad and dJ/dk_coll.  Outflow
+// boundaries only: a clamped ghost hands its adjoint to the edge cell.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "hydro.h"
+#include "hydro_adjoint_math.cuh"
+#include "hydro_internal.h"
+#include "hydro_math.cuh"
+
+namespace hydro {
+
+namespace {
+
+constexpr int kAdjThreads = 256;
+constexpr int kAdjSeg = 32;     // cells per line along the sweep axis
+constexpr int kAdjLanes = 8;    // lines per tile
+constexpr int kAdjW = kAdjSeg + 16;              // staged positions per line: a0-8 .. a0+SEG+7
+constexpr int kAdjNCS = kAdjLanes * kAdjW;
+constexpr int kAdjNI = kAdjSeg + 8;              // interfaces i = a0-4 .. a0+SEG+3
+constexpr int kAdjNIF = kAdjLanes * kAdjNI;
+constexpr int kAdjNC = kAdjLanes * kAdjSeg;
+constexpr size_t kAdjSmem = sizeof(double) * (size_t)(16 * kAdjNCS + 16 * kAdjNIF + 2 * kAdjNIF + 10 * kAdjNC) +
+                            sizeof(unsigned) * kAdjNIF;
+
+struct VjpArgs {
+  const double* U;      // stage state the right-hand side was evaluated on
+  const double* lam;    // adjoint of the stage result; a = ascale * lam is the adjoint of L
+  double* r;            // output J_L^T a (x sweep writes, y and z add)
+  double* kbar;         // [2]: dJ/dk_rad, dJ/dk_coll accumulators
+  double ascale;
+  int nx, ny, nz;
+  double inv_dx, e_floor, eps_s;
+  double rad_per_k, coll_per_k, k_rad, k_coll, t4coef, inv_vol;
+  JetStage jets;
+};
+
+__device__ __forceinline__ int clampi(int i, int n) { return i < 0 ? 0 : (i >= n ? n - 1 : i); }
+
+template <int DIR>
+__global__ void __launch_bounds__(kAdjThreads) vjp_kernel(const VjpArgs p) {
+  constexpr int SEG = kAdjSeg, LANES = kAdjLanes, W = kAdjW, NCS = kAdjNCS, NI = kAdjNI, NIF = kAdjNIF,
+                NC = kAdjNC;
+  constexpr bool FINAL = DIR == 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sU = reinterpret_cast<double*>(smem_raw);   // [5][NCS]
+  double* sF = sU + 5 * NCS;                          // [5][NCS] F_d/2
+  double* sA = sF + 5 * NCS;                          // [5][NCS] adjoint of L (0 outside the grid)
+  double* sR = sA + 5 * NCS;                          // [NCS] rho_d
+  double* cF = sR + NCS;                              // [NIF][8] adjoint of F_d/2 per stencil slot
+  double* cU = cF + 8 * NIF;                          // [NIF][8] direct adjoint of U per stencil slot
+  double* sAl = cU + 8 * NIF;                         // [NIF] alpha
+  double* sAhb = sAl + NIF;                           // [NIF] adjoint of alpha/2
+  double* sFb = sAhb + NIF;                           // [5][NC] gathered adjoint of F_d/2
+  double* sUb = sFb + 5 * NC;                         // [5][NC] gathered direct adjoint of U
+  unsigned* sTie = reinterpret_cast<unsigned*>(sUb + 5 * NC);   // [NIF] slots attaining max rho
+
+  const int nx = p.nx, ny = p.ny, nz = p.nz;
+  const size_t N = (size_t)nx * ny * nz;
+  const int n_along = DIR == 0 ? nx : (DIR == 1 ? ny : nz);
+  const int n_lane = DIR == 0 ? ny : nx;
+  int a0, l0;
+  if (DIR == 0) { a0 = blockIdx.x * SEG; l0 = blockIdx.y * LANES; }
+  else { l0 = blockIdx.x * LANES; a0 = blockIdx.y * SEG; }
+  const int fixed = blockIdx.z;
+  auto offset = [&](int along, int lane) -> size_t {
+    if (DIR == 0) return ((size_t)fixed * ny + lane) * nx + along;
+    if (DIR == 1) return ((size_t)fixed * ny + along) * nx + lane;
+    return ((size_t)along * ny + fixed) * nx + lane;
+  };
+  auto sidx = [&](int lane, int s) { return DIR == 0 ? lane * W + s : s * LANES + lane; };
+  auto iidx = [&](int lane, int ii) { return DIR == 0 ? lane * NI + ii : ii * LANES + lane; };
+  auto cidx = [&](int lane, int j) { return DIR == 0 ? lane * SEG + j : j * LANES + lane; };
+
+  // ---- stage: U, F_d/2, rho_d at positions a0-8 .. a0+SEG+7 (clamped), adjoint a (zero outside)
+  for (int c = threadIdx.x; c < NCS; c += kAdjThreads) {
+    int lane, s;
+    if (DIR == 0) { lane = c / W; s = c - lane * W; }
+    else { s = c / LANES; lane = c - s * LANES; }
+    const int ga = a0 - 8 + s;
+    const int gl = l0 + lane;
+    const size_t o = offset(clampi(ga, n_along), gl < n_lane ? gl : n_lane - 1);
+    const double E = p.U[o], Mx = p.U[N + o], My = p.U[2 * N + o], Mz = p.U[3 * N + o], R = p.U[4 * N + o];
+    double e, vx, vy, vz;
+    int hit = 0;
+    cons_to_prim<MathD>(E, Mx, My, Mz, p.e_floor, e, vx, vy, vz, hit);
+    const double pr = e * (1.0 / 3.0);
+    const double vd = DIR == 0 ? vx : (DIR == 1 ? vy : vz);
+    sU[c] = E; sU[NCS + c] = Mx; sU[2 * NCS + c] = My; sU[3 * NCS + c] = Mz; sU[4 * NCS + c] = R;
+    sF[c] = 0.5 * (DIR == 0 ? Mx : (DIR == 1 ? My : Mz));
+    sF[NCS + c] = 0.5 * (Mx * vd + (DIR == 0 ? pr : 0.0));
+    sF[2 * NCS + c] = 0.5 * (My * vd + (DIR == 1 ? pr : 0.0));
+    sF[3 * NCS + c] = 0.5 * (Mz * vd + (DIR == 2 ? pr : 0.0));
+    sF[4 * NCS + c] = 0.5 * (R * vd);
+    sR[c] = spectral_radius<MathD>(vd, vx * vx + vy * vy + vz * vz);
+    const bool inside = ga >= 0 && ga < n_along && gl < n_lane;
+    const size_t oa = offset(inside ? ga : 0, gl < n_lane ? gl : 0);
+    for (int q = 0; q < 5; ++q) sA[q * NCS + c] = inside ? p.ascale * p.lam[q * N + oa] : 0.0;
+  }
+  __syncthreads();
+
+  // ---- alpha and the slots that attain it, per interface i = a0-4+ii (valid for -1 <= i <= n-1)
+  for (int it = threadIdx.x; it < NIF; it += kAdjThreads) {
+    int lane, ii;
+    if (DIR == 0) { lane = it / NI; ii = it - lane * NI; }
+    else { ii = it / LANES; lane = it - ii * LANES; }
+    const int i = a0 - 4 + ii;
+    const bool valid = i >= -1 && i <= n_along - 1 && l0 + lane < n_lane;
+    double al = 0.0;
+    for (int t = 0; t < 8; ++t) al = fmax(al, sR[sidx(lane, ii + 1 + t)]);
+    unsigned mask = 0;
+    if (valid)
+      for (int t = 0; t < 8; ++t)
+        if (sR[sidx(lane, ii + 1 + t)] >= al * (1.0 - 1e-12)) mask |= 1u << t;
+    sAl[iidx(lane, ii)] = al;
+    sTie[iidx(lane, ii)] = mask;
+    sAhb[iidx(lane, ii)] = 0.0;
+  }
+  __syncthreads();
+
+  // ---- per component: reverse WENO at every interface, then gather per cell
+  for (int q = 0; q < 5; ++q) {
+    for (int it = threadIdx.x; it < NIF; it += kAdjThreads) {
+      int lane, ii;
+      if (DIR == 0) { lane = it / NI; ii = it - lane * NI; }
+      else { ii = it / LANES; lane = it - ii * LANES; }
+      const int x = iidx(lane, ii);
+      double* cf = cF + 8 * x;
+      double* cu = cU + 8 * x;
+      if (sTie[x] == 0u) {
+        for (int t = 0; t < 8; ++t) { cf[t] = 0.0; cu[t] = 0.0; }
+        continue;
+      }
+      const double ah = 0.5 * sAl[x];
+      double u[8], fh[8];
+      for (int t = 0; t < 8; ++t) {
+        u[t] = sU[q * NCS + sidx(lane, ii + 1 + t)];
+        fh[t] = sF[q * NCS + sidx(lane, ii + 1 + t)];
+      }
+      // adjoint of Fhat_{i+1/2}: L_i holds -Fhat inv_dx, L_{i+1} holds +Fhat inv_dx
+      const double g = (sA[q * NCS + sidx(lane, ii + 5)] - sA[q * NCS + sidx(lane, ii + 4)]) * p.inv_dx;
+      double fp[7], fm[7], gp[7], gm[7];
+      for (int t = 0; t < 7; ++t) {
+        fp[t] = fh[t] + ah * u[t];
+        fm[t] = fh[7 - t] - ah * u[7 - t];   // mirrored: cells i+4 .. i-2
+      }
+      weno7_vjp(fp, p.eps_s, g, gp);
+      weno7_vjp(fm, p.eps_s, g, gm);
+      double ahb = 0.0;
+      for (int t = 0; t < 8; ++t) {
+        const double bp = t <= 6 ? gp[t] : 0.0;
+        const double bm = t >= 1 ? gm[7 - t] : 0.0;
+        cf[t] = bp + bm;
+        cu[t] = ah * (bp - bm);
+        ahb += u[t] * (bp - bm);
+      }
+      sAhb[x] += ahb;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < NC; c += kAdjThreads) {
+      int lane, j;
+      if (DIR == 0) { lane = c / SEG; j = c - lane * SEG; }
+      else { j = c / LANES; lane = c - j * LANES; }
+      const int gcell = a0 + j;
+      double fb = 0.0, ub = 0.0;
+      if (gcell < n_along) {
+        const bool interior = gcell >= 4 && gcell <= n_along - 5;
+        for (int ii = j; ii <= j + 7; ++ii) {
+          const int x = iidx(lane, ii);
+          if (interior) {
+            const int t = j + 7 - ii;   // stencil slot holding cell gcell
+            fb += cF[8 * x + t];
+            ub += cU[8 * x + t];
+          } else {
+            const int i = a0 - 4 + ii;
+            for (int t = 0; t < 8; ++t)
+              if (clampi(i - 3 + t, n_along) == gcell) {
+                fb += cF[8 * x + t];
+                ub += cU[8 * x + t];
+              }
+          }
+        }
+      }
+      sFb[q * NC + cidx(lane, j)] = fb;
+      sUb[q * NC + cidx(lane, j)] = ub;
+    }
+    __syncthreads();
+  }
+
+  // ---- per cell: adjoint of rho from the interfaces whose max it attains, then the chain rule
+  for (int c = threadIdx.x; c < NC; c += kAdjThreads) {
+    int lane, j;
+    if (DIR == 0) { lane = c / SEG; j = c - lane * SEG; }
+    else { j = c / LANES; lane = c - j * LANES; }
+    const int gcell = a0 + j, gl = l0 + lane;
+    if (gcell >= n_along || gl >= n_lane) continue;
+    double rhob = 0.0;
+    for (int ii = j; ii <= j + 7; ++ii) {
+      const int x = iidx(lane, ii);
+      const unsigned mask = sTie[x];
+      if (!mask) continue;
+      const double albar = 0.5 * sAhb[x] / (double)__popc(mask);
+      const int i = a0 - 4 + ii;
+      for (int t = 0; t < 8; ++t)
+        if ((mask >> t) & 1u)
+          if (clampi(i - 3 + t, n_along) == gcell) rhob += albar;
+    }
+    const int sc = sidx(lane, j + 8);
+    const double E = sU[sc], Mx = sU[NCS + sc], My = sU[2 * NCS + sc], Mz = sU[3 * NCS + sc], R = sU[4 * NCS + sc];
+    double e, vx, vy, vz;
+    int hit = 0;
+    cons_to_prim<MathD>(E, Mx, My, Mz, p.e_floor, e, vx, vy, vz, hit);
+    const double v[3] = {vx, vy, vz};
+    const double vd = v[DIR];
+    const int ci = cidx(lane, j);
+    // F/2 adjoint -> F adjoint
+    double Fb[5];
+    for (int k = 0; k < 5; ++k) Fb[k] = 0.5 * sFb[k * NC + ci];
+    double Mb[3] = {0.0, 0.0, 0.0}, vb[3] = {0.0, 0.0, 0.0}, Rb = 0.0, pb = 0.0;
+    const double M[3] = {Mx, My, Mz};
+    Mb[DIR] += Fb[0];
+    for (int k = 0; k < 3; ++k) {
+      Mb[k] += Fb[1 + k] * vd;
+      vb[DIR] += Fb[1 + k] * M[k];
+    }
+    pb += Fb[1 + DIR];
+    Rb += Fb[4] * vd;
+    vb[DIR] += Fb[4] * R;
+    double d_vd, d_v2;
+    spectral_radius_grad(vd, vx * vx + vy * vy + vz * vz, d_vd, d_v2);
+    vb[DIR] += rhob * d_vd;
+    for (int k = 0; k < 3; ++k) vb[k] += rhob * d_v2 * 2.0 * v[k];
+    double Eb = sUb[ci];
+    double Mbx = sUb[NC + ci] + Mb[0], Mby = sUb[2 * NC + ci] + Mb[1], Mbz = sUb[3 * NC + ci] + Mb[2];
+    Rb += sUb[4 * NC + ci];
+    cons_to_prim_vjp(E, Mx, My, Mz, p.e_floor, pb * (1.0 / 3.0), vb[0], vb[1], vb[2], Eb, Mbx, Mby, Mbz);
+    if (FINAL) {
+      const int gx = DIR == 0 ? gcell : gl;
+      const int gy = DIR == 1 ? gcell : (DIR == 0 ? gl : fixed);
+      const int gz = DIR == 2 ? gcell : fixed;
+      for (int jn = 0; jn < p.jets.n; ++jn) {
+        const int* cl = p.jets.cell[jn];
+        if (cl[0] != gx || cl[1] != gy || cl[2] != gz) continue;
+        // S0 = inv_vol (k_rad C T^3 l / hc^2 + k_coll C T^2 / hc), T = (e t4)^(1/4): S = (S0, n S0, 0)
+        const double aE = sA[sc], aMx = sA[NCS + sc], aMy = sA[2 * NCS + sc], aMz = sA[3 * NCS + sc];
+        const double Sb = aE + p.jets.dir[jn][0] * aMx + p.jets.dir[jn][1] * aMy + p.jets.dir[jn][2] * aMz;
+        const double T = temperature(e, p.t4coef);
+        const double l = p.jets.ell[jn];
+        p.kbar[0] += Sb * p.rad_per_k * T * T * T * l * p.inv_vol;
+        p.kbar[1] += Sb * p.coll_per_k * T * T * p.inv_vol;
+        if (e > 0.0 && T > 0.0) {
+          const double dS_dT = (3.0 * p.k_rad * p.rad_per_k * T * T * l + 2.0 * p.k_coll * p.coll_per_k * T) * p.inv_vol;
+          const double dT_de = T / (4.0 * e);
+          cons_to_prim_vjp(E, Mx, My, Mz, p.e_floor, Sb * dS_dT * dT_de, 0.0, 0.0, 0.0, Eb, Mbx, Mby, Mbz);
+        }
+      }
+    }
+    const size_t o = offset(gcell, gl);
+    const double out[5] = {Eb, Mbx, Mby, Mbz, Rb};
+    if (DIR == 0) {
+      for (int k = 0; k < 5; ++k) p.r[k * N + o] = out[k];
+    } else {
+      for (int k = 0; k < 5; ++k) p.r[k * N + o] += out[k];
+    }
+  }
+}
+
+template <int DIR>
+cudaError_t launch_vjp(const VjpArgs& p, cudaStream_t s) {
+  dim3 grid;
+  if (DIR == 0) grid = dim3((p.nx + kAdjSeg - 1) / kAdjSeg, (p.ny + kAdjLanes - 1) / kAdjLanes, p.nz);
+  else if (DIR == 1) grid = dim3((p.nx + kAdjLanes - 1) / kAdjLanes, (p.ny + kAdjSeg - 1) / kAdjSeg, p.nz);
+  else grid = dim3((p.nx + kAdjLanes - 1) / kAdjLanes, (p.nz + kAdjSeg - 1) / kAdjSeg, p.ny);
+  cudaError_t err = cudaFuncSetAttribute(vjp_kernel<DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjSmem);
+  if (err != cudaSuccess) return err;
+  vjp_kernel<DIR><<<grid, kAdjThreads, kAdjSmem, s>>>(p);
+  return cudaGetLastError();
+}
+
+// Reverse of one stage combination Uout = ca U0 + cb (Uk + dt L(Uk)).
+// mode 0 (stage 3): lamB = cb lamA + r;  lam0 = ca lamA
+// mode 1 (stage 2): lamA = cb lamB + r;  lam0 += ca lamB
+// mode 2 (stage 1): lam0 += lamA + r
+__global__ void adj_combine_kernel(int mode, double ca, double cb, double* lamA, double* lamB, double* lam0,
+                                   const double* r, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    if (mode == 0) {
+      const double la = lamA[i];
+      lamB[i] = cb * la + r[i];
+      lam0[i] = ca * la;
+    } else if (mode == 1) {
+      const double lb = lamB[i];
+      lamA[i] = cb * lb + r[i];
+      lam0[i] += ca * lb;
+    } else {
+      lam0[i] += lamA[i] + r[i];
+    }
+  }
+}
+
+struct ConeArgs {
+  double apex[3], axis[3], cos_half, rmax2, dx, vol;
+  int nx, ny, nz;
+};
+
+__device__ __forceinline__ bool in_cone(const ConeArgs& c, int i, int j, int k) {
+  const double x = (i + 0.5 - 0.5 * c.nx) * c.dx - c.apex[0];
+  const double y = (j + 0.5 - 0.5 * c.ny) * c.dx - c.apex[1];
+  const double z = (k + 0.5 - 0.5 * c.nz) * c.dx - c.apex[2];
+  const double r2 = x * x + y * y + z * z;
+  if (!(r2 < c.rmax2)) return false;
+  return x * c.axis[0] + y * c.axis[1] + z * c.axis[2] >= c.cos_half * sqrt(r2);
+}
+
+// Partial sums of E dx^3 over the cone, one per block (summed on the host in order).
+__global__ void cone_energy_kernel(const double* U, ConeArgs c, double* partial) {
+  __shared__ double red[256];
+  const size_t n = (size_t)c.nx * c.ny * c.nz;
+  double acc = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int ix = (int)(i % c.nx), iy = (int)((i / c.nx) % c.ny), iz = (int)(i / ((size_t)c.nx * c.ny));
+    if (in_cone(c, ix, iy, iz)) acc += U[i] * c.vol;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+// Seed of the reverse sweep: dJ/dU = g dx^3 on E inside the cone.
+__global__ void cone_seed_kernel(double* lam, ConeArgs c, double g) {
+  const size_t n = (size_t)c.nx * c.ny * c.nz;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int ix = (int)(i % c.nx), iy = (int)((i / c.nx) % c.ny), iz = (int)(i / ((size_t)c.nx * c.ny));
+    lam[i] = in_cone(c, ix, iy, iz) ? g * c.vol : 0.0;
+    for (int q = 1; q < 5; ++q) lam[q * n + i] = 0.0;
+  }
+}
+
+// dJ/de of the initial state at fixed u^i and n: E = (4/3) e gamma^2 - e/3,
+// M^i = (4/3) e gamma u^i, R = n gamma.
+__global__ void grad_e_kernel(const double* prim, const double* lam, double* grad, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double ux = prim[n + i], uy = prim[2 * n + i], uz = prim[3 * n + i];
+    const double g2 = 1.0 + (ux * ux + uy * uy + uz * uz);
+    const double g = sqrt(g2);
+    grad[i] = lam[i] * (4.0 / 3.0 * g2 - 1.0 / 3.0) +
+              (4.0 / 3.0) * g * (lam[n + i] * ux + lam[2 * n + i] * uy + lam[3 * n + i] * uz);
+  }
+}
+
+unsigned grid_1d(size_t n) {
+  size_t b = (n + 255) / 256;
+  return (unsigned)(b < 148 * 16 ? (b > 0 ? b : 1) : 148 * 16);
+}
+
+}  // namespace
+}  // namespace hydro
+
+using namespace hydro;
+
+struct hydro_adjoint {
+  hydro_config cfg;
+  size_t n = 0;
+  int nsteps = 0, every = 0, nckpt = 0;
+  cudaStream_t stream = nullptr;
+  char* ws = nullptr;
+  std::vector<double*> ckpt;     // states at steps 0, every, 2 every, ...
+  std::vector<double*> seg;      // (every + 1) step states for the recomputed segment
+  double* rhs = nullptr;
+  std::vector<double*> stages;   // every x 2 stage states (U1, U2) of the segment
+  double *lamA = nullptr, *lamB = nullptr, *lam0 = nullptr, *r = nullptr, *prim = nullptr;
+  double* kbar = nullptr;        // [2]
+  double* partial = nullptr;     // cone partial sums
+  DevDiag* diag = nullptr;
+  int njet = 0;
+  double jx0[kMaxJets][3], jn[kMaxJets][3], jt[kMaxJets];
+  ConeArgs cone;
+  bool forward_done = false;
+  double J = 0.0;
+};
+
+namespace {
+
+const double kStageC[3] = {0.0, 1.0, 0.5};
+const double kStageW[3] = {1.0 / 6.0, 1.0 / 6.0, 4.0 / 6.0};
+const double kA[3] = {0.0, 0.75, 1.0 / 3.0};
+const double kB[3] = {1.0, 0.25, 2.0 / 3.0};
+constexpr unsigned kConeBlocks = 512;
+
+void jet_stage(const hydro_adjoint* a, double t, JetStage& js) {
+  std::memset(&js, 0, sizeof(js));
+  const int N[3] = {a->cfg.nx, a->cfg.ny, a->cfg.nz};
+  js.n = a->njet;
+  for (int j = 0; j < a->njet; ++j) {
+    const double l = t - a->jt[j];
+    js.ell[j] = l;
+    bool inside = (l >= 0.0);
+    for (int ax = 0; ax < 3; ++ax) {
+      const double x = a->jx0[j][ax] + a->jn[j][ax] * l;
+      const double fl = std::floor(x / a->cfg.dx + 0.5 * (double)N[ax]);
+      if (!(fl >= 0.0 && fl < (double)N[ax])) inside = false;
+      js.cell[j][ax] = (fl >= 0.0 && fl < (double)N[ax]) ? (int)fl : -1;
+      js.dir[j][ax] = a->jn[j][ax];
+    }
+    if (!inside) js.cell[j][0] = js.cell[j][1] = js.cell[j][2] = -1;
+  }
+}
+
+SweepArgs sweep_base(const hydro_adjoint* a) {
+  SweepArgs s;
+  std::memset(&s, 0, sizeof(s));
+  const hydro_config& g = a->cfg;
+  s.rhs = a->rhs;
+  s.diag = a->diag;
+  s.nx = g.nx;
+  s.ny = g.ny;
+  s.nz = g.nz;
+  s.periodic = 0;
+  s.inv_dx = 1.0 / g.dx;
+  s.dt = g.dt;
+  s.e_floor = g.e_floor;
+  s.eps = g.weno_eps;
+  s.src.rad = g.k_rad * g.cr_over_cf / (g.hbarc * g.hbarc);
+  s.src.coll = g.k_coll * g.cr_over_cf / g.hbarc;
+  s.src.t4coef = g.hbarc * g.hbarc * g.hbarc / (M_PI * M_PI / 30.0 * g.dof);
+  s.src.inv_vol = 1.0 / (g.dx * g.dx * g.dx);
+  return s;
+}
+
+// One forward step from `in` (step index n) to `out`; the two intermediate stage
+// states go to s1, s2.
+cudaError_t forward_step(hydro_adjoint* a, int64_t n, const double* in, double* s1, double* s2, double* out) {
+  SweepArgs s = sweep_base(a);
+  s.U0 = in;
+  const double vol = a->cfg.dx * a->cfg.dx * a->cfg.dx;
+  const double* Us[3] = {in, s1, s2};
+  double* Uo[3] = {s1, s2, out};
+  cudaError_t err = cudaSuccess;
+  for (int st = 0; st < 3 && err == cudaSuccess; ++st) {
+    jet_stage(a, a->cfg.t0 + ((double)n + kStageC[st]) * a->cfg.dt, s.jets);
+    s.src.wdt_vol = a->cfg.dt * kStageW[st] * vol;
+    s.U = Us[st];
+    s.Uout = Uo[st];
+    s.a = kA[st];
+    s.b = kB[st];
+    for (int d = 0; d < 3 && err == cudaSuccess; ++d) err = launch_sweep(HYDRO_FP64, 7, d, s, a->stream);
+  }
+  return err;
+}
+
+cudaError_t vjp(hydro_adjoint* a, int64_t n, int st, const double* Uk, const double* lam, double ascale) {
+  VjpArgs p;
+  std::memset(&p, 0, sizeof(p));
+  const hydro_config& g = a->cfg;
+  p.U = Uk;
+  p.lam = lam;
+  p.r = a->r;
+  p.kbar = a->kbar;
+  p.ascale = ascale;
+  p.nx = g.nx;
+  p.ny = g.ny;
+  p.nz = g.nz;
+  p.inv_dx = 1.0 / g.dx;
+  p.e_floor = g.e_floor;
+  p.eps_s = kW7EpsScale * g.weno_eps;
+  p.rad_per_k = g.cr_over_cf / (g.hbarc * g.hbarc);
+  p.coll_per_k = g.cr_over_cf / g.hbarc;
+  p.k_rad = g.k_rad;
+  p.k_coll = g.k_coll;
+  p.t4coef = g.hbarc * g.hbarc * g.hbarc / (M_PI * M_PI / 30.0 * g.dof);
+  p.inv_vol = 1.0 / (g.dx * g.dx * g.dx);
+  jet_stage(a, g.t0 + ((double)n + kStageC[st]) * g.dt, p.jets);
+  cudaError_t err = launch_vjp<0>(p, a->stream);
+  if (err == cudaSuccess) err = launch_vjp<1>(p, a->stream);
+  if (err == cudaSuccess) err = launch_vjp<2>(p, a->stream);
+  return err;
+}
+
+}  // namespace
+
+extern "C" {
+
+hydro_status hydro_adjoint_create(const hydro_config* cfg, int32_t nsteps, int32_t checkpoint_every,
+                                  const double apex[3], const double axis[3], double half_angle_deg, double rmax,
+                                  hydro_adjoint** out) {
+  if (!out) return HYDRO_EINVAL;
+  *out = nullptr;
+  if (!cfg || cfg->precision != HYDRO_FP64 || cfg->boundary != HYDRO_OUTFLOW || cfg->weno_order != 7)
+    return HYDRO_EINVAL;
+  if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1 || nsteps < 1 || checkpoint_every < 1 || !apex || !axis)
+    return HYDRO_EINVAL;
+  if (!(cfg->dx > 0.0) || !(cfg->dt > 0.0) || !(cfg->e_floor > 0.0) || !(cfg->weno_eps > 0.0)) return HYDRO_EINVAL;
+  const double al = std::sqrt(axis[0] * axis[0] + axis[1] * axis[1] + axis[2] * axis[2]);
+  if (!(al > 0.0) || !(rmax > 0.0) || !(half_angle_deg > 0.0 && half_angle_deg < 180.0)) return HYDRO_EINVAL;
+  hydro_adjoint* a = new (std::nothrow) hydro_adjoint;
+  if (!a) return HYDRO_ENOMEM;
+  a->cfg = *cfg;
+  a->n = (size_t)cfg->nx * cfg->ny * cfg->nz;
+  a->nsteps = nsteps;
+  a->every = checkpoint_every < nsteps ? checkpoint_every : nsteps;
+  a->nckpt = (nsteps + a->every - 1) / a->every;
+  a->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+  for (int k = 0; k < 3; ++k) {
+    a->cone.apex[k] = apex[k];
+    a->cone.axis[k] = axis[k] / al;
+  }
+  a->cone.cos_half = std::cos(half_angle_deg * M_PI / 180.0);
+  a->cone.rmax2 = rmax * rmax;
+  a->cone.dx = cfg->dx;
+  a->cone.vol = cfg->dx * cfg->dx * cfg->dx;
+  a->cone.nx = cfg->nx;
+  a->cone.ny = cfg->ny;
+  a->cone.nz = cfg->nz;
+  // buffers: checkpoints, the segment's step states and stage states, adjoints, scratch
+  const size_t f5 = 5 * a->n * sizeof(double);
+  const size_t nbuf = (size_t)a->nckpt + (size_t)(a->every + 1) + 2 * (size_t)a->every + 1 + 4 + 1;
+  const size_t bytes = nbuf * f5 + a->n * sizeof(double) + 64 + kConeBlocks * sizeof(double) + sizeof(DevDiag) + 4096;
+  if (cudaMalloc(&a->ws, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete a;
+    return HYDRO_ENOMEM;
+  }
+  char* p = a->ws;
+  auto take = [&](size_t b) {
+    char* q = p;
+    p += (b + 255) / 256 * 256;
+    return q;
+  };
+  for (int k = 0; k < a->nckpt; ++k) a->ckpt.push_back(reinterpret_cast<double*>(take(f5)));
+  for (int k = 0; k <= a->every; ++k) a->seg.push_back(reinterpret_cast<double*>(take(f5)));
+  for (int k = 0; k < 2 * a->every; ++k) a->stages.push_back(reinterpret_cast<double*>(take(f5)));
+  a->rhs = reinterpret_cast<double*>(take(f5));
+  a->lamA = reinterpret_cast<double*>(take(f5));
+  a->lamB = reinterpret_cast<double*>(take(f5));
+  a->lam0 = reinterpret_cast<double*>(take(f5));
+  a->r = reinterpret_cast<double*>(take(f5));
+  a->prim = reinterpret_cast<double*>(take(f5));
+  a->kbar = reinterpret_cast<double*>(take(64));
+  a->partial = reinterpret_cast<double*>(take(kConeBlocks * sizeof(double)));
+  a->diag = reinterpret_cast<DevDiag*>(take(sizeof(DevDiag)));
+  *out = a;
+  return HYDRO_OK;
+}
+
+hydro_status hydro_adjoint_add_jet(hydro_adjoint* a, const double x0[3], const double dir[3], double t_start) {
+  if (!a || !x0 || !dir || a->njet >= kMaxJets || !std::isfinite(t_start)) return HYDRO_EINVAL;
+  const double len = std::sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+  if (!(len > 0.0) || !std::isfinite(len)) return HYDRO_EINVAL;
+  for (int k = 0; k < 3; ++k) {
+    a->jx0[a->njet][k] = x0[k];
+    a->jn[a->njet][k] = dir[k] / len;
+  }
+  a->jt[a->njet] = t_start;
+  a->njet += 1;
+  return HYDRO_OK;
+}
+
+hydro_status hydro_adjoint_set_params(hydro_adjoint* a, double k_rad, double k_coll) {
+  if (!a || !std::isfinite(k_rad) || !std::isfinite(k_coll)) return HYDRO_EINVAL;
+  a->cfg.k_rad = k_rad;
+  a->cfg.k_coll = k_coll;
+  a->forward_done = false;
+  return HYDRO_OK;
+}
+
+hydro_status hydro_adjoint_forward(hydro_adjoint* a, const double* d_prim5, double* J) {
+  if (!a || !d_prim5 || !J) return HYDRO_EINVAL;
+  const size_t f5 = 5 * a->n * sizeof(double);
+  cudaError_t err = cudaMemcpyAsync(a->prim, d_prim5, f5, cudaMemcpyDeviceToDevice, a->stream);
+  if (err == cudaSuccess) err = cudaMemsetAsync(a->diag, 0, sizeof(DevDiag), a->stream);
+  if (err == cudaSuccess) err = launch_init(HYDRO_FP64, HYDRO_PRIMITIVE, a->prim, a->ckpt[0], a->n, a->diag, a->stream);
+  // march, keeping a checkpoint every `every` steps; other states ping-pong in seg[0], seg[1]
+  const double* cur = a->ckpt[0];
+  int pp = 0;
+  for (int s = 0; s < a->nsteps && err == cudaSuccess; ++s) {
+    const int k = (s + 1) / a->every;
+    double* next;
+    if ((s + 1) % a->every == 0 && k < a->nckpt) {
+      next = a->ckpt[k];
+    } else {
+      next = a->seg[pp];
+      pp ^= 1;
+    }
+    err = forward_step(a, s, cur, a->stages[0], a->stages[1], next);
+    cur = next;
+  }
+  if (err == cudaSuccess) cone_energy_kernel<<<kConeBlocks, 256, 0, a->stream>>>(cur, a->cone, a->partial);
+  std::vector<double> part(kConeBlocks);
+  DevDiag d;
+  if (err == cudaSuccess) err = cudaGetLastError();
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(part.data(), a->partial, kConeBlocks * sizeof(double), cudaMemcpyDeviceToHost, a->stream);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(&d, a->diag, sizeof(d), cudaMemcpyDeviceToHost, a->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(a->stream);
+  if (err != cudaSuccess) return HYDRO_ECUDA;
+  if (d.bad_input) return HYDRO_EINVAL;
+  if (d.status) return (hydro_status)d.status;
+  double sum = 0.0;
+  for (double v : part) sum += v;
+  a->J = sum;
+  *J = sum;
+  a->forward_done = true;
+  return HYDRO_OK;
+}
+
+hydro_status hydro_adjoint_backward(hydro_adjoint* a, double dJ, double* grad_k_rad, double* grad_k_coll,
+                                    double* d_grad_e) {
+  if (!a || !d_grad_e) return HYDRO_EINVAL;
+  if (!a->forward_done) return HYDRO_ESTATE;
+  cudaError_t err = cudaMemsetAsync(a->kbar, 0, 2 * sizeof(double), a->stream);
+  const unsigned g1 = grid_1d(5 * a->n);
+  if (err == cudaSuccess) {
+    cone_seed_kernel<<<grid_1d(a->n), 256, 0, a->stream>>>(a->lamA, a->cone, dJ);
+    err = cudaGetLastError();
+  }
+  // segments in reverse: recompute the step states of the segment from its
+  // checkpoint, then walk its steps backwards
+  for (int k = a->nckpt - 1; k >= 0 && err == cudaSuccess; --k) {
+    const int s0 = k * a->every;
+    const int s1 = std::min(a->nsteps, s0 + a->every);
+    const int len = s1 - s0;
+    err = cudaMemcpyAsync(a->seg[0], a->ckpt[k], 5 * a->n * sizeof(double), cudaMemcpyDeviceToDevice, a->stream);
+    for (int s = 0; s < len && err == cudaSuccess; ++s)
+      err = forward_step(a, s0 + s, a->seg[s], a->stages[2 * s], a->stages[2 * s + 1], a->seg[s + 1]);
+    for (int s = len - 1; s >= 0 && err == cudaSuccess; --s) {
+      const int64_t n = s0 + s;
+      const double* Us[3] = {a->seg[s], a->stages[2 * s], a->stages[2 * s + 1]};
+      // stage 3: U = 1/3 U0 + 2/3 (U2 + dt L(U2))
+      err = vjp(a, n, 2, Us[2], a->lamA, kB[2] * a->cfg.dt);
+      if (err == cudaSuccess) {
+        adj_combine_kernel<<<g1, 256, 0, a->stream>>>(0, kA[2], kB[2], a->lamA, a->lamB, a->lam0, a->r, 5 * a->n);
+        err = cudaGetLastError();
+      }
+      // stage 2: U2 = 3/4 U0 + 1/4 (U1 + dt L(U1))
+      if (err == cudaSuccess) err = vjp(a, n, 1, Us[1], a->lamB, kB[1] * a->cfg.dt);
+      if (err == cudaSuccess) {
+        adj_combine_kernel<<<g1, 256, 0, a->stream>>>(1, kA[1], kB[1], a->lamA, a->lamB, a->lam0, a->r, 5 * a->n);
+        err = cudaGetLastError();
+      }
+      // stage 1: U1 = U0 + dt L(U0)
+      if (err == cudaSuccess) err = vjp(a, n, 0, Us[0], a->lamA, kB[0] * a->cfg.dt);
+      if (err == cudaSuccess) {
+        adj_combine_kernel<<<g1, 256, 0, a->stream>>>(2, kA[0], kB[0], a->lamA, a->lamB, a->lam0, a->r, 5 * a->n);
+        err = cudaGetLastError();
+      }
+      std::swap(a->lamA, a->lam0);   // adjoint of the step's input becomes the next output adjoint
+    }
+  }
+  if (err == cudaSuccess) {
+    grad_e_kernel<<<grid_1d(a->n), 256, 0, a->stream>>>(a->prim, a->lamA, d_grad_e, a->n);
+    err = cudaGetLastError();
+  }
+  double kb[2] = {0.0, 0.0};
+  if (err == cudaSuccess) err = cudaMemcpyAsync(kb, a->kbar, sizeof(kb), cudaMemcpyDeviceToHost, a->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(a->stream);
+  if (err != cudaSuccess) return HYDRO_ECUDA;
+  if (grad_k_rad) *grad_k_rad = kb[0];
+  if (grad_k_coll) *grad_k_coll = kb[1];
+  return HYDRO_OK;
+}
+
+void hydro_adjoint_destroy(hydro_adjoint* a) {
+  if (!a) return;
+  if (a->stream || a->ws) cudaStreamSynchronize(a->stream);
+  if (a->ws) cudaFree(a->ws);
+  delete a;
+}
+
+}  // extern "C"

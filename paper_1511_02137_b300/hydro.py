@@ -87,6 +87,17 @@ def _lib():
         lib.hydro_batch_get_diag.argtypes = [vp, ctypes.c_int32, P(hydro_diag)]
         lib.hydro_batch_destroy.argtypes = [vp]
         lib.hydro_batch_destroy.restype = None
+        lib.hydro_adjoint_create.argtypes = [P(hydro_config), ctypes.c_int32, ctypes.c_int32, dp, dp, ctypes.c_double,
+                                             ctypes.c_double, P(vp)]
+        lib.hydro_adjoint_add_jet.argtypes = [vp, dp, dp, ctypes.c_double]
+        lib.hydro_adjoint_set_params.argtypes = [vp, ctypes.c_double, ctypes.c_double]
+        lib.hydro_adjoint_forward.argtypes = [vp, vp, dp]
+        lib.hydro_adjoint_backward.argtypes = [vp, ctypes.c_double, dp, dp, vp]
+        lib.hydro_adjoint_destroy.argtypes = [vp]
+        lib.hydro_adjoint_destroy.restype = None
+        for name in ("hydro_adjoint_create", "hydro_adjoint_add_jet", "hydro_adjoint_set_params",
+                     "hydro_adjoint_forward", "hydro_adjoint_backward"):
+            getattr(lib, name).restype = ctypes.c_int
         for name in ("hydro_workspace_size", "hydro_create", "hydro_set_initial", "hydro_add_jet", "hydro_step",
                      "hydro_read_fields", "hydro_get_diag", "hydro_profile_enable", "hydro_profile_query",
                      "hydro_batch_workspace_size", "hydro_batch_create", "hydro_batch_set_initial",
@@ -320,3 +331,70 @@ def hydro_batch_destroy(b: Batch) -> None:
     if b.handle:
         _lib().hydro_batch_destroy(b.handle)
         b.handle = None
+
+
+# ---------------------------------------------------------------- adjoint
+
+
+class Adjoint:
+    """Opaque hydro_adjoint handle."""
+
+    def __init__(self, handle, cfg, nsteps, every):
+        self.handle = handle
+        self.cfg = cfg
+        self.nsteps = nsteps
+        self.every = every
+        self.cells = cfg.nx * cfg.ny * cfg.nz
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            hydro_adjoint_destroy(self)
+
+
+def hydro_adjoint_create(cfg: hydro_config, nsteps: int, checkpoint_every: int, apex, axis,
+                         half_angle_deg: float, rmax: float, stream=None) -> Adjoint:
+    import torch
+    c = hydro_config.from_buffer_copy(cfg)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    c.cuda_stream = s.cuda_stream
+    h = ctypes.c_void_p()
+    _check(_lib().hydro_adjoint_create(ctypes.byref(c), nsteps, checkpoint_every, (ctypes.c_double * 3)(*apex),
+                                       (ctypes.c_double * 3)(*axis), half_angle_deg, rmax, ctypes.byref(h)),
+           "hydro_adjoint_create")
+    return Adjoint(h, c, nsteps, checkpoint_every)
+
+
+def hydro_adjoint_add_jet(a: Adjoint, x0, direction, t_start: float) -> None:
+    _check(_lib().hydro_adjoint_add_jet(a.handle, (ctypes.c_double * 3)(*x0), (ctypes.c_double * 3)(*direction),
+                                        t_start), "hydro_adjoint_add_jet")
+
+
+def hydro_adjoint_set_params(a: Adjoint, k_rad: float, k_coll: float) -> None:
+    _check(_lib().hydro_adjoint_set_params(a.handle, k_rad, k_coll), "hydro_adjoint_set_params")
+
+
+def hydro_adjoint_forward(a: Adjoint, prim_dev) -> float:
+    """prim_dev: contiguous float64 CUDA tensor of 5*cells values (e, u^x, u^y, u^z, n)."""
+    if prim_dev.dtype.itemsize != 8 or not prim_dev.is_cuda or not prim_dev.is_contiguous() \
+            or prim_dev.numel() != 5 * a.cells:
+        raise ValueError("expected a contiguous float64 CUDA tensor of 5*cells values")
+    J = ctypes.c_double()
+    _check(_lib().hydro_adjoint_forward(a.handle, prim_dev.data_ptr(), ctypes.byref(J)), "hydro_adjoint_forward")
+    return J.value
+
+
+def hydro_adjoint_backward(a: Adjoint, dJ: float, grad_e_dev):
+    """Returns (dJ/dk_rad, dJ/dk_coll); writes dJ/de into grad_e_dev (float64 CUDA, cells values)."""
+    if not grad_e_dev.is_cuda or not grad_e_dev.is_contiguous() or grad_e_dev.numel() != a.cells:
+        raise ValueError("expected a contiguous float64 CUDA tensor of cells values")
+    gr = ctypes.c_double()
+    gc = ctypes.c_double()
+    _check(_lib().hydro_adjoint_backward(a.handle, dJ, ctypes.byref(gr), ctypes.byref(gc), grad_e_dev.data_ptr()),
+           "hydro_adjoint_backward")
+    return gr.value, gc.value
+
+
+def hydro_adjoint_destroy(a: Adjoint) -> None:
+    if a.handle:
+        _lib().hydro_adjoint_destroy(a.handle)
+        a.handle = None
