@@ -307,6 +307,42 @@ def _batched(hy, steps, warmup):
             "timing": "wall clock around hydro_batch_step (CUDA graph replay, includes host jet tables and sync)"}
 
 
+def _adjoint(hy):
+    """The adjoint configuration: 128^3, 50 steps, checkpoint every 10, one jet
+    from (-4, 0, 0) fm along +x, energy in a 30-degree cone of radius 3 fm around
+    the jet axis; gradient with respect to k_rad, k_coll and e(x).  Times one
+    forward and one forward + backward through torch.autograd (wall clock, synced)."""
+    import torch
+    from paper_1511_02137_b300 import adjoint as A
+    from paper_1511_02137_b300 import workloads as W
+    jet = W.JetSpec((-4.0, 0.0, 0.0), (1.0, 0.0, 0.0), 1.0)
+    w = W.Workload(name="ellipsoidal-flow 128^3, 50 RK3 steps, 1 jet (adjoint)", n=(128, 128, 128), steps=50,
+                   sigma=(4.0, 5.0, 6.0), jets=(jet,))
+    prim = W.ellipsoidal_primitives(w)
+    run = A.ConeEnergyRun(hy.hydro_config_default(*w.n), w.steps, 10, w.jets,
+                          torch.from_numpy(prim[1:].copy()).cuda(), apex=jet.x0, axis=jet.direction)
+    e = torch.from_numpy(prim[0].copy()).cuda()
+    kr = torch.tensor(4.0, dtype=torch.float64, requires_grad=True)
+    kc = torch.tensor(2.5, dtype=torch.float64, requires_grad=True)
+    A.cone_energy(e, kr.detach(), kc.detach(), run)            # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    A.cone_energy(e, kr.detach(), kc.detach(), run)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    ev = e.clone().requires_grad_(True)
+    t0 = time.perf_counter()
+    J = A.cone_energy(ev, kr, kc, run)
+    J.backward()
+    torch.cuda.synchronize()
+    t_all = time.perf_counter() - t0
+    return {"workload": w.name, "precision": "fp64", "checkpoint_every": 10, "J_GeV": J.item(),
+            "dJ_dk_rad": kr.grad.item(), "dJ_dk_coll": kc.grad.item(),
+            "forward_s": round(t_fwd, 3), "backward_s": round(t_all - t_fwd, 3),
+            "backward_over_forward": round((t_all - t_fwd) / t_fwd, 3),
+            "forward_cell_updates_per_s": w.cells * w.steps / t_fwd}
+
+
 def run_cuda(args, rank, ws):
     import numpy as np
     import torch
@@ -370,6 +406,8 @@ def run_cuda(args, rank, ws):
     out["variants"] = variants
     if not args.no_batched:
         out["batched"] = _batched(hy, args.steps, args.warmup)
+    if not args.no_adjoint:
+        out["adjoint"] = _adjoint(hy)
     if not args.no_e2e:
         sec, sb, db = _e2e(hy, w, prim_pinned, out_pinned, args.steps)
         sec = _max_over_ranks(sec, ws)
@@ -426,6 +464,7 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-event batched ensemble measurement")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the 128^3 adjoint timing")
     ap.add_argument("--grid", type=int, default=256,
                     help="cube edge; 256 is the paper's run, smaller edges are centre sub-grids for profiling")
     args = ap.parse_args(argv)

@@ -29,8 +29,8 @@ namespace hydro {
 namespace {
 
 constexpr int kAdjThreads = 256;
-constexpr int kAdjSeg = 32;     // cells per line along the sweep axis
-constexpr int kAdjLanes = 8;    // lines per tile
+constexpr int kAdjSeg = 64;     // cells per line along the sweep axis
+constexpr int kAdjLanes = 4;    // lines per tile
 constexpr int kAdjW = kAdjSeg + 16;              // staged positions per line: a0-8 .. a0+SEG+7
 constexpr int kAdjNCS = kAdjLanes * kAdjW;
 constexpr int kAdjNI = kAdjSeg + 8;              // interfaces i = a0-4 .. a0+SEG+3

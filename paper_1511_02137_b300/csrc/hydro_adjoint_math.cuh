@@ -112,10 +112,11 @@ __device__ __forceinline__ double weno7_vjp(const double f[7], double eps_s, dou
   const double dk[4] = {1.0, 12.0, 18.0, 4.0};
   const double num = t[0] * Q0 + t[1] * Q1 + t[2] * Q2 + t[3] * Q3;
   const double den = t[0] + 12.0 * t[1] + 18.0 * t[2] + 4.0 * t[3];
-  const double W = num / den;
+  const double rden = 1.0 / den;
+  const double W = num * rden;
   // reverse
-  const double numb = gbar / den;
-  const double denb = -gbar * W / den;
+  const double numb = gbar * rden;
+  const double denb = -numb * W;
   double tb[4], Qb[4];
   for (int k = 0; k < 4; ++k) {
     tb[k] = numb * Q[k] + denb * dk[k];
