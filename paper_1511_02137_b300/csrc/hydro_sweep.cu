@@ -233,9 +233,10 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
         for (int q = 0; q < 5; ++q) rhs[q * N + o] += L[q];
       }
     } else {
-      double Ld[5];
+      // accumulate in storage precision (FP64 for FP64 and mixed, FP32 for FP32)
+      Store Ld[5];
 #pragma unroll
-      for (int q = 0; q < 5; ++q) Ld[q] = (double)(rhs[q * N + o] + L[q]);
+      for (int q = 0; q < 5; ++q) Ld[q] = (Store)(rhs[q * N + o] + L[q]);
       if (jets_here) {
         const int gx = DIR == 0 ? ga : gl;
         const int gy = DIR == 1 ? ga : (DIR == 0 ? gl : fixed);
@@ -250,10 +251,10 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
                                a.e_floor, e, vx, vy, vz, hit);
           const double T = temperature(e, a.src.t4coef);
           const double S0 = (a.src.rad * T * T * T * jets.ell[jn] + a.src.coll * T * T) * a.src.inv_vol;
-          Ld[0] += S0;
-          Ld[1] += jets.dir[jn][0] * S0;
-          Ld[2] += jets.dir[jn][1] * S0;
-          Ld[3] += jets.dir[jn][2] * S0;
+          Ld[0] += (Store)S0;
+          Ld[1] += (Store)(jets.dir[jn][0] * S0);
+          Ld[2] += (Store)(jets.dir[jn][1] * S0);
+          Ld[3] += (Store)(jets.dir[jn][2] * S0);
           a.diag->dep[jn] += a.src.wdt_vol * S0;
           a.diag->cell[jn][0] = gx;
           a.diag->cell[jn][1] = gy;
@@ -266,8 +267,9 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
       const Store dt = (Store)a.dt, ca = (Store)a.a, cb = (Store)a.b;
 #pragma unroll
       for (int q = 0; q < 5; ++q) {
-        const Store u = U[q * N + o];
-        const Store l = (Store)Ld[q];
+        // the cell's own state is staged already unless storage and flux types differ (mixed)
+        const Store u = (PREC == HYDRO_MIXED) ? U[q * N + o] : (Store)sU[q * NCS + sidx(lane, j + G)];
+        const Store l = Ld[q];
         Store out = (a.a == 0.0) ? u + dt * l : ca * U0[q * N + o] + cb * (u + dt * l);
         bad |= !isfinite(out);
         Uout[q * N + o] = out;

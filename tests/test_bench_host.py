@@ -1,0 +1,73 @@
+"""Host-side logic of bench.py without a GPU: multi-rank timing reduction over
+gloo (world size 2), clock-sample parsing and the roofline arithmetic."""
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank_main(rank, world, port, q):
+    os.environ.update({"RANK": str(rank), "WORLD_SIZE": str(world), "LOCAL_RANK": str(rank),
+                       "MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
+    sys.path.insert(0, ROOT)
+    import bench
+    r, ws, local = bench._dist()
+    bench._barrier(ws)
+    t = bench._max_over_ranks(1.5 + rank, ws)     # rank 1 is the slow one
+    q.put((r, ws, t))
+    import torch.distributed as dist
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_with_two_gloo_ranks():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert out == [(0, 2, 2.5), (1, 2, 2.5)]
+
+
+def test_clock_summary_parsing():
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.ClockSampler(None)
+    c.lines = ["1980, 2032, 800.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "2010, 2032, 900.5, 0x4, Not Active, Not Active, Not Active, Active",
+               "1995, 2032, 950.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "garbage line"]
+    s = c.summary()
+    assert s["sm_mhz"] == 1995 and s["sm_max_mhz"] == 2032 and s["reasons"] == ["sw_power_cap"]
+    assert s["samples"] == 3
+
+
+def test_roofline_arithmetic():
+    sys.path.insert(0, ROOT)
+    import bench
+    cells = 256 ** 3
+    prof = {"sweep_x": {"ms": 100.0, "launches": 10}, "sweep_y": {"ms": 110.0, "launches": 10},
+            "sweep_z": {"ms": 120.0, "launches": 10}}
+    r = bench._roofline(prof, cells, "fp64")
+    assert r["kernel"] == "sweep_z" and r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    want = cells * bench.FLOP_PER_CELL["sweep_z"] / 12e-3 / 1e12
+    assert abs(r["achieved"] - round(want, 4)) < 1e-9
+    assert abs(r["frac"] - round(want / bench.PEAK_FP64_TFLOPS, 4)) < 1e-9
+    assert abs(sum(r["share"].values()) - 1.0) < 1e-3
+    assert abs(bench.PEAK_FP32_TFLOPS - 76.98815) < 1e-3

@@ -258,3 +258,22 @@ def test_fp64_parity_when_floors_act(hy, orc, W):
     assert gd["max_speed"] <= 1.0
     err = norm_rel_err(G, O)
     assert np.all(err <= 1e-10), err
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp32"])
+def test_three_jet_run_error_per_field_after_70_steps(hy, W, precision):
+    """The mixed-precision configuration: 256^3, 70 steps, 3 seeded jets; error
+    per field against the FP64 path (which matches the FP64 oracle to 1e-10)."""
+    w = W.ELLIPSOIDAL_256_3JETS
+    res = {}
+    for prec in ("fp64", precision):
+        ctx = gpu_context(hy, w, prec)
+        hy.hydro_step(ctx, w.steps)
+        res[prec] = hy.hydro_read_fields(ctx, hy.HYDRO_CONSERVED)
+        d = hy.hydro_get_diag(ctx)
+        assert d["status"] == 0
+        hy.hydro_destroy(ctx)
+    err = norm_rel_err(res[precision], res["fp64"])
+    print(precision, "256^3, 3 jets, 70 steps, error vs FP64 per field (E, Mx, My, Mz, R):", err)
+    assert np.isfinite(res[precision]).all()
+    assert np.all(err <= 1e-4), err
