@@ -117,8 +117,8 @@ __device__ __forceinline__ typename M::T spectral_radius(typename M::T vd, typen
   return (fabs(vd) * (P(2) * third) + M::sqrt(disc * third)) * M::rcp(P(1) - v2 * third);
 }
 
-// Jiang-Shu weights w_k ~ d_k / (eps + beta_k)^2 applied to candidates that
-// already carry the factor d_k (Q_k = d_k q_k), so the reconstruction is
+// Jiang-Shu weights w_k ~ d_k / (eps + beta_k)^2 applied to values that
+// already carry the factor d_k (Q_k = d_k q_k), giving
 // sum_k Q_k t_k / sum_k d_k t_k with t_k = 1/(eps + beta_k)^2.
 // FP64: one division, t_k ~ prod_{j != k} (eps + beta_j)^2.
 __device__ __forceinline__ double weno7_combine(double Q0, double Q1, double Q2, double Q3, double b0, double b1,
@@ -167,12 +167,13 @@ constexpr double kW7B = 0.999359590072005;     // sqrt(780/781)
 // eps_s is (720/781) eps.
 template <class F>
 __device__ __forceinline__ F weno7(F f0, F f1, F f2, F f3, F f4, F f5, F f6, F eps_s) {
-  // candidates times their linear weight d_k = 1, 12, 18, 4, over 12
-  const F Q0 = F(-3.0 / 12.0) * f0 + F(13.0 / 12.0) * f1 + F(-23.0 / 12.0) * f2 + F(25.0 / 12.0) * f3;
-  const F Q1 = f1 - F(5) * f2 + F(13) * f3 + F(3) * f4;
-  const F Q2 = F(-1.5) * f2 + F(10.5) * f3 + F(10.5) * f4 + F(-1.5) * f5;
-  const F Q3 = f3 + F(13.0 / 3.0) * f4 + F(-5.0 / 3.0) * f5 + F(1.0 / 3.0) * f6;
   const F d10 = f1 - f0, d11 = f2 - f1, d12 = f3 - f2, d13 = f4 - f3, d14 = f5 - f4, d15 = f6 - f5;
+  // candidates q_k = f_i + (difference part); the differences times d_k/12 are R_k, so the
+  // reconstruction is f_i + sum_k t_k R_k / sum_k d_k t_k (the f_i part has weights summing to 1)
+  const F R0 = F(3.0 / 12.0) * d10 + F(-10.0 / 12.0) * d11 + F(13.0 / 12.0) * d12;
+  const F R1 = -d11 + F(4) * d12 + F(3) * d13;
+  const F R2 = F(1.5) * d12 + F(9) * d13 + F(-1.5) * d14;
+  const F R3 = F(3) * d13 + F(-4.0 / 3.0) * d14 + F(1.0 / 3.0) * d15;
   const F d20 = d11 - d10, d21 = d12 - d11, d22 = d13 - d12, d23 = d14 - d13, d24 = d15 - d14;
   const F c0 = d21 - d20, c1 = d22 - d21, c2 = d23 - d22, c3 = d24 - d23;
   const F B = F(kW7B);
@@ -188,7 +189,7 @@ __device__ __forceinline__ F weno7(F f0, F f1, F f2, F f3, F f4, F f5, F f6, F e
   const F b1 = a1 * a1 + (c1 * c1 + m12);
   const F b2 = a2 * a2 + (c2 * c2 + m12);
   const F b3 = a3 * a3 + (bb3 * bb3 + c3 * c3);
-  return weno7_combine(Q0, Q1, Q2, Q3, b0, b1, b2, b3, eps_s);
+  return f3 + weno7_combine(R0, R1, R2, R3, b0, b1, b2, b3, eps_s);
 }
 
 // WENO5 weights (linear weights (1, 6, 3)/10), candidates carrying d_k.

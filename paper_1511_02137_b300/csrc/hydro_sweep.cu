@@ -40,10 +40,11 @@ template <> struct Types<HYDRO_MIXED> { using Store = double; using Flux = float
 
 // Tile shape per sweep axis: SEG cells along the sweep axis, LANES lines.  The
 // lines of the y and z sweeps run along x so that loads stay coalesced.
-template <int DIR> struct Tile;
-template <> struct Tile<0> { static constexpr int SEG = 64, LANES = 4; };
-template <> struct Tile<1> { static constexpr int SEG = 32, LANES = 8; };
-template <> struct Tile<2> { static constexpr int SEG = 32, LANES = 8; };
+// FP64 keeps the longer x tile (fewer recomputed halo cells per FP64-bound
+// interface); FP32 and mixed run the x sweep on 32 x 8 tiles, faster when
+// instruction issue bounds the kernel.
+template <int PREC, int DIR> struct Tile { static constexpr int SEG = 32, LANES = 8; };
+template <> struct Tile<HYDRO_FP64, 0> { static constexpr int SEG = 64, LANES = 4; };
 
 constexpr int kThreads = 256;
 
@@ -57,8 +58,9 @@ __device__ __forceinline__ int map_along(int i, int n, int periodic) {
 
 // Block-wide max of the spectral radius and sum of floor hits, published with
 // one atomic each.  Must be reached by every thread of the block.
-__device__ __forceinline__ void publish_block(double vmax, unsigned hits, DevDiag* d, bool speed, bool floors) {
-  __shared__ double wmax[kThreads / 32];
+template <class T>
+__device__ __forceinline__ void publish_block(T vmax, unsigned hits, DevDiag* d, bool speed, bool floors) {
+  __shared__ T wmax[kThreads / 32];
   __shared__ unsigned whits[kThreads / 32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -72,12 +74,13 @@ __device__ __forceinline__ void publish_block(double vmax, unsigned hits, DevDia
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double m = 0.0;
+    T mt = T(0);
     unsigned long long h = 0;
     for (int i = 0; i < kThreads / 32; ++i) {
-      m = fmax(m, wmax[i]);
+      mt = fmax(mt, wmax[i]);
       h += whits[i];
     }
+    const double m = (double)mt;
     // non-negative doubles order like their bit patterns
     if (speed) atomicMax(&d->vmax_bits, (unsigned long long)__double_as_longlong(m));
     if (floors && h) atomicAdd(&d->floor_hits, h);
@@ -159,7 +162,7 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
       hits += (unsigned)hit;
     }
   }
-  if (a.reduce_speed || a.count_floors) publish_block((double)vmax, hits, a.diag, a.reduce_speed, a.count_floors);
+  if (a.reduce_speed || a.count_floors) publish_block(vmax, hits, a.diag, a.reduce_speed, a.count_floors);
   __syncthreads();
 
   // ---------------- phase 2: numerical flux at every interface of the tile
@@ -282,7 +285,7 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
 template <int PREC, int ORDER, int DIR, bool FINAL>
 __global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int SEG = Tile<DIR>::SEG, LANES = Tile<DIR>::LANES;
+  constexpr int SEG = Tile<PREC, DIR>::SEG, LANES = Tile<PREC, DIR>::LANES;
   int a0, l0;
   if (DIR == 0) {
     a0 = blockIdx.x * SEG; l0 = blockIdx.y * LANES;
@@ -334,7 +337,7 @@ __global__ void reset_vmax_kernel(DevDiag* d, int n) {
 template <int PREC, int ORDER, int DIR>
 static cudaError_t launch_one(const SweepArgs& a, cudaStream_t s) {
   using F = typename Types<PREC>::Flux;
-  constexpr int SEG = Tile<DIR>::SEG, LANES = Tile<DIR>::LANES, G = (ORDER == 7) ? 4 : 3;
+  constexpr int SEG = Tile<PREC, DIR>::SEG, LANES = Tile<PREC, DIR>::LANES, G = (ORDER == 7) ? 4 : 3;
   constexpr size_t smem = sizeof(F) * (size_t)(11 * LANES * (SEG + 2 * G) + 5 * LANES * (SEG + 1));
   dim3 grid;
   if (DIR == 0) grid = dim3((a.nx + SEG - 1) / SEG, (a.ny + LANES - 1) / LANES, a.nz);
