@@ -77,6 +77,8 @@ struct hydro_ctx {
   double jt[kMaxJets];
   bool profiling = false;
   Prof prof;
+  CUtensorMap tmaps[3][3];   // [state buffer][sweep axis], valid when tma
+  bool tma = false;
   void* U(size_t off) { return ws + off; }
   DevDiag* diag() { return reinterpret_cast<DevDiag*>(ws + lay.diag); }
   double* staging() { return reinterpret_cast<double*>(ws + lay.u1); }
@@ -201,6 +203,8 @@ hydro_status hydro_create(const hydro_config* cfg, hydro_ctx** out) {
     hydro_destroy(c);
     return HYDRO_ECUDA;
   }
+  void* bufs[3] = {c->U(c->lay.u0), c->U(c->lay.u1), c->U(c->lay.u2)};
+  c->tma = encode_sweep_tmaps(cfg->precision, cfg->weno_order, bufs, cfg->nx, cfg->ny, cfg->nz, c->tmaps);
   *out = c;
   return HYDRO_OK;
 }
@@ -296,7 +300,7 @@ hydro_status hydro_step(hydro_ctx* c, int32_t nsteps) {
       for (int dir = 0; dir < 3 && err == cudaSuccess; ++dir) {
         a.count_floors = (dir == 0);
         prof_mark(c, HYDRO_KERNEL_SWEEP_X + dir);
-        err = launch_sweep(g.precision, g.weno_order, dir, a, c->stream);
+        err = launch_sweep(g.precision, g.weno_order, dir, a, c->stream, c->tma ? &c->tmaps[st][dir] : nullptr);
         prof_mark(c, HYDRO_KERNEL_SWEEP_X + dir);
       }
     }

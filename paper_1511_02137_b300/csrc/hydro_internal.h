@@ -4,6 +4,7 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace hydro {
@@ -103,7 +104,17 @@ cudaError_t launch_reset_vmax(DevDiag* diags, int n, cudaStream_t s);
 
 // Launches one directional sweep (dir 0/1/2) for the given precision
 // (0 FP64, 1 FP32, 2 mixed) and WENO order (7 or 5).
-cudaError_t launch_sweep(int precision, int order, int dir, const SweepArgs& a, cudaStream_t s);
+// tmap (may be NULL): tensor map of a.U for this sweep axis from encode_sweep_tmaps;
+// with it, tiles that need no ghost cells are staged by TMA.
+cudaError_t launch_sweep(int precision, int order, int dir, const SweepArgs& a, cudaStream_t s,
+                         const CUtensorMap* tmap = nullptr);
+
+// Tensor maps of the three state buffers for the three sweep axes (maps[buffer][axis]),
+// for FP64 and FP32 storage with WENO7.  Returns false (and leaves maps unusable) when the
+// grid does not meet the TMA layout rules (row pitch a multiple of 16 bytes) or the
+// driver entry point is missing; callers then stage with plain loads.
+bool encode_sweep_tmaps(int precision, int order, void* const bufs[3], int nx, int ny, int nz,
+                        CUtensorMap maps[3][3]);
 
 // Initial state: staging (5N FP64, prim or cons) -> conserved state in storage precision.
 cudaError_t launch_init(int precision, int kind, const double* staging, void* U, size_t n, DevDiag* diag,

@@ -23,6 +23,7 @@
 // its spectral radii into the step's maximum signal speed with a warp-shuffle
 // reduction and one atomic per block.
 #include <cstdint>
+#include <cstring>
 
 #include "hydro.h"
 #include "hydro_internal.h"
@@ -54,6 +55,46 @@ __device__ __forceinline__ int map_along(int i, int n, int periodic) {
     return i < 0 ? i + n : i;
   }
   return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+// ---- TMA staging (cp.async.bulk.tensor) with an mbarrier, bounded wait
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned phase) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+// 4-D tiled copy (x, y, z, field) of one box into shared memory, completing on bar.
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Spins on the barrier phase with an iteration limit; false when it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned phase) {
+  for (long it = 0; it < (1L << 24); ++it)
+    if (mbar_try_wait(bar, phase)) return true;
+  return false;
 }
 
 // Block-wide max of the spectral radius and sum of floor hits, published with
@@ -91,9 +132,10 @@ __device__ __forceinline__ void publish_block(T vmax, unsigned hits, DevDiag* d,
 // lines starting at l0, in plane `fixed` (z for the x and y sweeps, y for the z
 // sweep).  Must be reached by every thread of the block; shared memory is free
 // again when it returns.
-template <int PREC, int ORDER, int DIR, bool FINAL, int SEG, int LANES>
+template <int PREC, int ORDER, int DIR, bool FINAL, int SEG, int LANES, bool TMA = false>
 __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& jets, int a0, int l0, int fixed,
-                                           unsigned char* smem_raw) {
+                                           unsigned char* smem_raw, const CUtensorMap* tmap = nullptr,
+                                           uint64_t* bar = nullptr) {
   using Store = typename Types<PREC>::Store;
   using F = typename Types<PREC>::Flux;
   using Math = typename Types<PREC>::Math;
@@ -124,6 +166,23 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
 
   // ---------------- phase 1: stage cells, primitives, half fluxes, rho
   const Store* __restrict__ U = static_cast<const Store*>(a.U);
+  // a tile whose halo lies inside the grid needs no ghost cells: one TMA box of all 5 fields
+  bool staged = false;
+  if constexpr (TMA) {
+    static_assert(sizeof(Store) == sizeof(F), "TMA staging writes the stored type into the flux-type tile");
+    if (a0 - G >= 0 && a0 + SEG + G <= n_along && l0 + LANES <= n_lane) {
+      if (threadIdx.x == 0) mbar_init(bar, 1);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        mbar_expect_tx(bar, (unsigned)(5 * NCS * sizeof(Store)));
+        if (DIR == 0) tma_load_4d(sU, tmap, a0 - G, l0, fixed, 0, bar);
+        else if (DIR == 1) tma_load_4d(sU, tmap, l0, a0 - G, fixed, 0, bar);
+        else tma_load_4d(sU, tmap, l0, fixed, a0 - G, 0, bar);
+      }
+      if (!mbar_wait_bounded(bar, 0)) atomicCAS(&a.diag->status, 0, (int)HYDRO_ETIMEOUT);
+      staged = true;
+    }
+  }
   F vmax = F(0);
   unsigned hits = 0;
   for (int c = threadIdx.x; c < NCS; c += kThreads) {
@@ -132,8 +191,14 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
     else { s = c / LANES; lane = c - s * LANES; }
     const int ga = a0 - G + s;
     const int gl = l0 + lane;
-    const size_t o = offset(map_along(ga, n_along, a.periodic), gl < n_lane ? gl : n_lane - 1);
-    const Store Es = U[o], Mxs = U[N + o], Mys = U[2 * N + o], Mzs = U[3 * N + o], Rs = U[4 * N + o];
+    Store Es, Mxs, Mys, Mzs, Rs;
+    if (staged) {
+      Es = (Store)sU[c]; Mxs = (Store)sU[NCS + c]; Mys = (Store)sU[2 * NCS + c];
+      Mzs = (Store)sU[3 * NCS + c]; Rs = (Store)sU[4 * NCS + c];
+    } else {
+      const size_t o = offset(map_along(ga, n_along, a.periodic), gl < n_lane ? gl : n_lane - 1);
+      Es = U[o]; Mxs = U[N + o]; Mys = U[2 * N + o]; Mzs = U[3 * N + o]; Rs = U[4 * N + o];
+    }
     F e, vx, vy, vz;
     int hit = 0;
     if constexpr (PREC == HYDRO_MIXED) {
@@ -146,11 +211,13 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
     const F vd = DIR == 0 ? vx : (DIR == 1 ? vy : vz);
     const F rho = spectral_radius<Math>(vd, vx * vx + vy * vy + vz * vz);
     const F Md = DIR == 0 ? Mx : (DIR == 1 ? My : Mz);
-    sU[0 * NCS + c] = E;
-    sU[1 * NCS + c] = Mx;
-    sU[2 * NCS + c] = My;
-    sU[3 * NCS + c] = Mz;
-    sU[4 * NCS + c] = R;
+    if (!staged) {
+      sU[0 * NCS + c] = E;
+      sU[1 * NCS + c] = Mx;
+      sU[2 * NCS + c] = My;
+      sU[3 * NCS + c] = Mz;
+      sU[4 * NCS + c] = R;
+    }
     sF[0 * NCS + c] = F(0.5) * Md;
     sF[1 * NCS + c] = F(0.5) * (Mx * vd + (DIR == 0 ? p : F(0)));
     sF[2 * NCS + c] = F(0.5) * (My * vd + (DIR == 1 ? p : F(0)));
@@ -282,9 +349,10 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   if (FINAL && bad) atomicCAS(&a.diag->status, 0, (int)HYDRO_EUNPHYSICAL);
 }
 
-template <int PREC, int ORDER, int DIR, bool FINAL>
-__global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+template <int PREC, int ORDER, int DIR, bool FINAL, bool TMA>
+__global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a, const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
   constexpr int SEG = Tile<PREC, DIR>::SEG, LANES = Tile<PREC, DIR>::LANES;
   int a0, l0;
   if (DIR == 0) {
@@ -292,7 +360,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a) {
   } else {
     l0 = blockIdx.x * LANES; a0 = blockIdx.y * SEG;
   }
-  sweep_tile<PREC, ORDER, DIR, FINAL, SEG, LANES>(a, a.jets, a0, l0, blockIdx.z, smem_raw);
+  sweep_tile<PREC, ORDER, DIR, FINAL, SEG, LANES, TMA>(a, a.jets, a0, l0, blockIdx.z, smem_raw, &tmap, &bar);
 }
 
 // Batched sweep: a persistent grid walks the tile list of all grids of the
@@ -301,7 +369,7 @@ template <int PREC, int DIR, bool FINAL, int SEG, int LANES>
 __global__ void __launch_bounds__(kThreads) batch_sweep_kernel(const BatchArgs b) {
   using Store = typename Types<PREC>::Store;
   using F = typename Types<PREC>::Flux;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
     const int4 td = b.tiles[t];
     const BatchEvent ev = b.events[td.x];
@@ -335,7 +403,7 @@ __global__ void reset_vmax_kernel(DevDiag* d, int n) {
 }
 
 template <int PREC, int ORDER, int DIR>
-static cudaError_t launch_one(const SweepArgs& a, cudaStream_t s) {
+static cudaError_t launch_one(const SweepArgs& a, cudaStream_t s, const CUtensorMap* tmap) {
   using F = typename Types<PREC>::Flux;
   constexpr int SEG = Tile<PREC, DIR>::SEG, LANES = Tile<PREC, DIR>::LANES, G = (ORDER == 7) ? 4 : 3;
   constexpr size_t smem = sizeof(F) * (size_t)(11 * LANES * (SEG + 2 * G) + 5 * LANES * (SEG + 1));
@@ -343,33 +411,94 @@ static cudaError_t launch_one(const SweepArgs& a, cudaStream_t s) {
   if (DIR == 0) grid = dim3((a.nx + SEG - 1) / SEG, (a.ny + LANES - 1) / LANES, a.nz);
   else if (DIR == 1) grid = dim3((a.nx + LANES - 1) / LANES, (a.ny + SEG - 1) / SEG, a.nz);
   else grid = dim3((a.nx + LANES - 1) / LANES, (a.nz + SEG - 1) / SEG, a.ny);
-  auto kern = sweep_kernel<PREC, ORDER, DIR, DIR == 2>;
+  constexpr bool kTmaCapable = PREC != HYDRO_MIXED && ORDER == 7;
+  if (kTmaCapable && tmap) {
+    auto kern = sweep_kernel<PREC, ORDER, DIR, DIR == 2, kTmaCapable>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    kern<<<grid, kThreads, smem, s>>>(a, *tmap);
+    return cudaGetLastError();
+  }
+  auto kern = sweep_kernel<PREC, ORDER, DIR, DIR == 2, false>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  kern<<<grid, kThreads, smem, s>>>(a);
+  CUtensorMap none;
+  memset(&none, 0, sizeof(none));
+  kern<<<grid, kThreads, smem, s>>>(a, none);
   return cudaGetLastError();
 }
 
 template <int PREC, int ORDER>
-static cudaError_t launch_dir(int dir, const SweepArgs& a, cudaStream_t s) {
+static cudaError_t launch_dir(int dir, const SweepArgs& a, cudaStream_t s, const CUtensorMap* t) {
   switch (dir) {
-    case 0: return launch_one<PREC, ORDER, 0>(a, s);
-    case 1: return launch_one<PREC, ORDER, 1>(a, s);
-    default: return launch_one<PREC, ORDER, 2>(a, s);
+    case 0: return launch_one<PREC, ORDER, 0>(a, s, t);
+    case 1: return launch_one<PREC, ORDER, 1>(a, s, t);
+    default: return launch_one<PREC, ORDER, 2>(a, s, t);
   }
 }
 
 template <int PREC>
-static cudaError_t launch_order(int order, int dir, const SweepArgs& a, cudaStream_t s) {
-  return order == 5 ? launch_dir<PREC, 5>(dir, a, s) : launch_dir<PREC, 7>(dir, a, s);
+static cudaError_t launch_order(int order, int dir, const SweepArgs& a, cudaStream_t s, const CUtensorMap* t) {
+  return order == 5 ? launch_dir<PREC, 5>(dir, a, s, t) : launch_dir<PREC, 7>(dir, a, s, t);
 }
 
-cudaError_t launch_sweep(int precision, int order, int dir, const SweepArgs& a, cudaStream_t s) {
+cudaError_t launch_sweep(int precision, int order, int dir, const SweepArgs& a, cudaStream_t s,
+                         const CUtensorMap* tmap) {
   switch (precision) {
-    case HYDRO_FP64: return launch_order<HYDRO_FP64>(order, dir, a, s);
-    case HYDRO_FP32: return launch_order<HYDRO_FP32>(order, dir, a, s);
-    default: return launch_order<HYDRO_MIXED>(order, dir, a, s);
+    case HYDRO_FP64: return launch_order<HYDRO_FP64>(order, dir, a, s, tmap);
+    case HYDRO_FP32: return launch_order<HYDRO_FP32>(order, dir, a, s, tmap);
+    default: return launch_order<HYDRO_MIXED>(order, dir, a, s, tmap);
   }
+}
+
+// ---------------------------------------------------------------- tensor maps
+
+template <int PREC, int DIR>
+static void tma_box(cuuint32_t box[4]) {
+  constexpr int SEG = Tile<PREC, DIR>::SEG, LANES = Tile<PREC, DIR>::LANES, W = SEG + 8;
+  box[3] = 5;
+  if (DIR == 0) { box[0] = W; box[1] = LANES; box[2] = 1; }
+  else if (DIR == 1) { box[0] = LANES; box[1] = W; box[2] = 1; }
+  else { box[0] = LANES; box[1] = 1; box[2] = W; }
+}
+
+bool encode_sweep_tmaps(int precision, int order, void* const bufs[3], int nx, int ny, int nz,
+                        CUtensorMap maps[3][3]) {
+  if (precision == HYDRO_MIXED || order != 7) return false;
+  const size_t es = precision == HYDRO_FP32 ? 4 : 8;
+  const cuuint64_t dim[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, 5};
+  const cuuint64_t stride[3] = {(cuuint64_t)nx * es, (cuuint64_t)nx * ny * es, (cuuint64_t)nx * ny * nz * es};
+  for (int k = 0; k < 3; ++k)
+    if (stride[k] % 16 != 0) return false;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn) {
+    cudaGetLastError();
+    return false;
+  }
+  using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  Encode encode = reinterpret_cast<Encode>(fn);
+  const CUtensorMapDataType dt = precision == HYDRO_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                         : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  for (int b = 0; b < 3; ++b)
+    for (int d = 0; d < 3; ++d) {
+      cuuint32_t box[4];
+      if (precision == HYDRO_FP32) {
+        if (d == 0) tma_box<HYDRO_FP32, 0>(box); else if (d == 1) tma_box<HYDRO_FP32, 1>(box); else tma_box<HYDRO_FP32, 2>(box);
+      } else {
+        if (d == 0) tma_box<HYDRO_FP64, 0>(box); else if (d == 1) tma_box<HYDRO_FP64, 1>(box); else tma_box<HYDRO_FP64, 2>(box);
+      }
+      if ((box[0] * es) % 16 != 0) return false;
+      if (encode(&maps[b][d], dt, 4, bufs[b], dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                 CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    }
+  return true;
 }
 
 // ---------------------------------------------------------------- batched launches
