@@ -70,27 +70,29 @@ __device__ __forceinline__ void cons_to_prim(typename M::T E, typename M::T Mx, 
   vz = Mz * vs;
 }
 
-// Mixed-precision recovery: only the cancelling difference E - |M| (tiny as
-// v -> 1) is formed in FP64; everything after it is well conditioned in terms
-// of om = 1 - m = (E - |M|)/E and runs in FP32:
+// Mixed-precision recovery: only the cancelling combination E^2 - |M|^2 (tiny
+// as v -> 1) is formed in FP64; everything after it is well conditioned in
+// terms of om = 1 - m = (E^2 - |M|^2) / (E (E + |M|)), where E + |M| needs only
+// FP32 accuracy, and runs in FP32:
 //   4 - 3m^2 = 1 + 3 om (2 - om),  1 - v = 3 om (1 + (2 - om)/(s + 1)) / (2 + s),
 //   1 - m v = (1 - v) + v om,  with s = sqrt(4 - 3m^2).
 __device__ __forceinline__ void cons_to_prim_mixed(double E, double Mx, double My, double Mz, double e_floor,
                                                    float& e, float& vx, float& vy, float& vz, int& hit) {
-  const double Mabs = ::sqrt(Mx * Mx + My * My + Mz * Mz);
   double Ee = E;
   if (!(Ee >= e_floor)) {
     Ee = e_floor;
     hit = 1;
   }
-  const float Ef = (float)Ee;
+  const double D = Ee * Ee - (Mx * Mx + My * My + Mz * Mz);
+  const float Ef = (float)Ee, mx = (float)Mx, my = (float)My, mz = (float)Mz;
+  const float Mabs = sqrt_approx(mx * mx + my * my + mz * mz);
   const float invE = rcp_approx(Ef);
-  float om = (float)(Ee - Mabs) * invE;
+  float om = (float)D * rcp_approx(Ef * (Ef + Mabs));
   const float om_min = (float)(1.0 - MathD::m_max);
   float m_over_M = invE;   // m / |M|
   if (!(om >= om_min)) {
     om = om_min;
-    m_over_M = (1.0f - om) / (float)Mabs;
+    m_over_M = (1.0f - om) / Mabs;
     hit = 1;
   }
   const float s = sqrt_approx(1.0f + 3.0f * om * (2.0f - om));
@@ -99,9 +101,9 @@ __device__ __forceinline__ void cons_to_prim_mixed(double E, double Mx, double M
   const float v = 1.0f - omv;
   e = Ef * (omv + v * om);
   const float vs = 3.0f * m_over_M * r;   // v / |M|
-  vx = (float)Mx * vs;
-  vy = (float)My * vs;
-  vz = (float)Mz * vs;
+  vx = mx * vs;
+  vy = my * vs;
+  vz = mz * vs;
 }
 
 // Spectral radius of the flux Jacobian along an axis: max |lambda_pm| with
@@ -190,6 +192,55 @@ __device__ __forceinline__ F weno7(F f0, F f1, F f2, F f3, F f4, F f5, F f6, F e
   const F b2 = a2 * a2 + (c2 * c2 + m12);
   const F b3 = a3 * a3 + (bb3 * bb3 + c3 * c3);
   return f3 + weno7_combine(R0, R1, R2, R3, b0, b1, b2, b3, eps_s);
+}
+
+// ---- FP32 pair form: the left-biased f+ and the mirrored f- reconstruction of
+// one interface run the same operation sequence, so they are evaluated together
+// in the two lanes of Blackwell's packed FP32x2 instructions (FFMA2, FADD2,
+// FMUL2), halving the issue slots of the reconstruction.
+
+__device__ __forceinline__ float2 bc2(float c) { return make_float2(c, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(rcp_approx(a.x), rcp_approx(a.y)); }
+
+// Same arithmetic as weno7<float> per lane (f_i plus the weighted difference
+// correction, scaled sum-of-squares indicators, one reciprocal per weight).
+__device__ __forceinline__ float2 weno7_pair(float2 f0, float2 f1, float2 f2, float2 f3, float2 f4, float2 f5,
+                                             float2 f6, float eps_s) {
+  const float2 d10 = sub2(f1, f0), d11 = sub2(f2, f1), d12 = sub2(f3, f2), d13 = sub2(f4, f3), d14 = sub2(f5, f4),
+               d15 = sub2(f6, f5);
+  const float2 d20 = sub2(d11, d10), d21 = sub2(d12, d11), d22 = sub2(d13, d12), d23 = sub2(d14, d13),
+               d24 = sub2(d15, d14);
+  const float2 c0 = sub2(d21, d20), c1 = sub2(d22, d21), c2 = sub2(d23, d22), c3 = sub2(d24, d23);
+  const float2 R0 = fma2(bc2(3.0f / 12.0f), d10, fma2(bc2(-10.0f / 12.0f), d11, mul2(bc2(13.0f / 12.0f), d12)));
+  const float2 R1 = fma2(bc2(4.0f), d12, fma2(bc2(3.0f), d13, mul2(bc2(-1.0f), d11)));
+  const float2 R2 = fma2(bc2(1.5f), d12, fma2(bc2(9.0f), d13, mul2(bc2(-1.5f), d14)));
+  const float2 R3 = fma2(bc2(3.0f), d13, fma2(bc2(-4.0f / 3.0f), d14, mul2(bc2(1.0f / 3.0f), d15)));
+  const float kA = (float)kW7A, kB = (float)kW7B;
+  const float2 a0 = fma2(bc2(2 * kA), d10, fma2(bc2(-7 * kA), d11, mul2(bc2(11 * kA), d12)));
+  const float2 a1 = fma2(bc2(-kA), d11, fma2(bc2(5 * kA), d12, mul2(bc2(2 * kA), d13)));
+  const float2 a2 = fma2(bc2(2 * kA), d12, fma2(bc2(5 * kA), d13, mul2(bc2(-kA), d14)));
+  const float2 a3 = fma2(bc2(11 * kA), d13, fma2(bc2(-7 * kA), d14, mul2(bc2(2 * kA), d15)));
+  const float2 bb0 = fma2(bc2(2 * kB), d21, mul2(bc2(-kB), d20));
+  const float2 bb12 = mul2(bc2(kB), d22);
+  const float2 bb3 = fma2(bc2(2 * kB), d23, mul2(bc2(-kB), d24));
+  const float2 m12 = mul2(bb12, bb12);
+  const float2 b0 = fma2(a0, a0, fma2(bb0, bb0, mul2(c0, c0)));
+  const float2 b1 = fma2(a1, a1, fma2(c1, c1, m12));
+  const float2 b2 = fma2(a2, a2, fma2(c2, c2, m12));
+  const float2 b3 = fma2(a3, a3, fma2(bb3, bb3, mul2(c3, c3)));
+  const float2 e = bc2(eps_s);
+  float2 t0 = rcp2(add2(e, b0)), t1 = rcp2(add2(e, b1)), t2 = rcp2(add2(e, b2)), t3 = rcp2(add2(e, b3));
+  t0 = mul2(t0, t0);
+  t1 = mul2(t1, t1);
+  t2 = mul2(t2, t2);
+  t3 = mul2(t3, t3);
+  const float2 num = fma2(t0, R0, fma2(t1, R1, fma2(t2, R2, mul2(t3, R3))));
+  const float2 den = fma2(bc2(12.0f), t1, fma2(bc2(18.0f), t2, fma2(bc2(4.0f), t3, t0)));
+  return fma2(num, rcp2(den), f3);
 }
 
 // WENO5 weights (linear weights (1, 6, 3)/10), candidates carrying d_k.

@@ -234,17 +234,15 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
 
   // ---------------- phase 2: numerical flux at every interface of the tile
   const F eps = (ORDER == 7) ? (F)(kW7EpsScale * a.eps) : (F)(kW5EpsScale * a.eps);
-  for (int it = threadIdx.x; it < NIF; it += kThreads) {
-    int lane, j;
-    if (DIR == 0) { lane = it / (SEG + 1); j = it - lane * (SEG + 1); }
-    else { j = it / LANES; lane = it - j * LANES; }
-    // the interface left of tile cell j; its stencil is staged cells j .. j + 2G - 1
+  // numerical flux of components q0 .. q1-1 at the interface left of tile cell j
+  // (its stencil is staged cells j .. j + 2G - 1)
+  auto flux_at = [&](int lane, int j, int q0, int q1) {
     F alpha = sR[sidx(lane, j)];
 #pragma unroll
     for (int t = 1; t < 2 * G; ++t) alpha = fmax(alpha, sR[sidx(lane, j + t)]);
     const F ah = F(0.5) * alpha;
 #pragma unroll 1
-    for (int q = 0; q < 5; ++q) {
+    for (int q = q0; q < q1; ++q) {
       F u[2 * G], f[2 * G];
 #pragma unroll
       for (int t = 0; t < 2 * G; ++t) {
@@ -252,7 +250,17 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
         f[t] = sF[q * NCS + sidx(lane, j + t)];
       }
       F hp, hm;
-      if (ORDER == 7) {
+      if constexpr (ORDER == 7 && sizeof(F) == 4) {
+        // lane x: f+ from cells i-3..i+3; lane y: f- mirrored from cells i+4..i-2
+        const float2 ahp = make_float2(ah, -ah);
+        float2 g[7];
+#pragma unroll
+        for (int k = 0; k < 7; ++k)
+          g[k] = fma2(ahp, make_float2(u[k], u[7 - k]), make_float2(f[k], f[7 - k]));
+        const float2 h = weno7_pair(g[0], g[1], g[2], g[3], g[4], g[5], g[6], eps);
+        hp = h.x;
+        hm = h.y;
+      } else if (ORDER == 7) {
         hp = weno7<F>(fma(ah, u[0], f[0]), fma(ah, u[1], f[1]), fma(ah, u[2], f[2]), fma(ah, u[3], f[3]),
                       fma(ah, u[4], f[4]), fma(ah, u[5], f[5]), fma(ah, u[6], f[6]), eps);
         hm = weno7<F>(fma(-ah, u[7], f[7]), fma(-ah, u[6], f[6]), fma(-ah, u[5], f[5]), fma(-ah, u[4], f[4]),
@@ -263,8 +271,21 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
         hm = weno5<F>(fma(-ah, u[5], f[5]), fma(-ah, u[4], f[4]), fma(-ah, u[3], f[3]), fma(-ah, u[2], f[2]),
                       fma(-ah, u[1], f[1]), eps);
       }
-      sH[q * NIF + it] = hp + hm;
+      sH[q * NIF + hidx(lane, j)] = hp + hm;
     }
+  };
+  // the left faces of the tile's cells, all components, then the right face of
+  // each line split into single-component tasks so that no thread does two
+  // whole interfaces while the block waits at the barrier
+  for (int it = threadIdx.x; it < NC; it += kThreads) {
+    int lane, j;
+    if (DIR == 0) { lane = it / SEG; j = it - lane * SEG; }
+    else { j = it / LANES; lane = it - j * LANES; }
+    flux_at(lane, j, 0, 5);
+  }
+  for (int t = threadIdx.x; t < 5 * LANES; t += kThreads) {
+    const int q = t / LANES, lane = t - q * LANES;
+    flux_at(lane, SEG, q, q + 1);
   }
   __syncthreads();
 
