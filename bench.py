@@ -48,6 +48,11 @@ FLOP_PER_CELL_STEP = 3 * sum(FLOP_PER_CELL.values())
 # writes 5; stages 2 and 3 read 10 and write 5) in storage precision.
 FIELD_ACCESSES_PER_CELL_STEP = 40
 
+# DRAM bytes per cell per launch of the FP64 z sweep (the dominant FP64 kernel), from
+# one ncu capture of the 256^3 workload (dram__bytes_read.sum + dram__bytes_write.sum,
+# mean over the three stages of a step); other kernels were not captured at full size.
+TRAFFIC_B_PER_CELL = {("fp64", "sweep_z"): 145.3}
+
 # Peaks for an ALU-bound path, derived from unit counts and clocks: 148 SMs x
 # 128 FP32 lanes x 2 FLOP/FMA x 2.032 GHz; FP64 takes the nominal B300 rate.
 PEAK_FP32_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
@@ -216,7 +221,9 @@ def _roofline(prof, cells, precision):
     peak = PEAK_FP64_TFLOPS if precision == "fp64" else PEAK_FP32_TFLOPS
     total_ms = sum(v["ms"] for v in prof.values())
     return {"bound": "alu", "kernel": dom, "achieved": round(achieved, 4), "peak": round(peak, 3),
-            "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+            "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+            "traffic": (TRAFFIC_B_PER_CELL[(precision, dom)] * cells
+                        if (precision, dom) in TRAFFIC_B_PER_CELL else None),
             "peak_source": ("nominal B300 FP64 rate (profiling recipe)" if precision == "fp64" else
                             "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz"),
             "flop_per_launch": flop, "avg_launch_ms": round(avg_s * 1e3, 4),
@@ -307,7 +314,7 @@ def _batched(hy, steps, warmup):
             "timing": "wall clock around hydro_batch_step (CUDA graph replay, includes host jet tables and sync)"}
 
 
-def _adjoint(hy):
+def _adjoint(hy, grid=128, steps=50):
     """The adjoint configuration: 128^3, 50 steps, checkpoint every 10, one jet
     from (-4, 0, 0) fm along +x, energy in a 30-degree cone of radius 3 fm around
     the jet axis; gradient with respect to k_rad, k_coll and e(x).  Times one
@@ -316,10 +323,10 @@ def _adjoint(hy):
     from paper_1511_02137_b300 import adjoint as A
     from paper_1511_02137_b300 import workloads as W
     jet = W.JetSpec((-4.0, 0.0, 0.0), (1.0, 0.0, 0.0), 1.0)
-    w = W.Workload(name="ellipsoidal-flow 128^3, 50 RK3 steps, 1 jet (adjoint)", n=(128, 128, 128), steps=50,
-                   sigma=(4.0, 5.0, 6.0), jets=(jet,))
+    w = W.Workload(name=f"ellipsoidal-flow {grid}^3, {steps} RK3 steps, 1 jet (adjoint)", n=(grid, grid, grid),
+                   steps=steps, sigma=(4.0, 5.0, 6.0), jets=(jet,))
     prim = W.ellipsoidal_primitives(w)
-    run = A.ConeEnergyRun(hy.hydro_config_default(*w.n), w.steps, 10, w.jets,
+    run = A.ConeEnergyRun(hy.hydro_config_default(*w.n), w.steps, min(10, w.steps), w.jets,
                           torch.from_numpy(prim[1:].copy()).cuda(), apex=jet.x0, axis=jet.direction)
     e = torch.from_numpy(prim[0].copy()).cuda()
     kr = torch.tensor(4.0, dtype=torch.float64, requires_grad=True)
@@ -336,7 +343,7 @@ def _adjoint(hy):
     J.backward()
     torch.cuda.synchronize()
     t_all = time.perf_counter() - t0
-    return {"workload": w.name, "precision": "fp64", "checkpoint_every": 10, "J_GeV": J.item(),
+    return {"workload": w.name, "precision": "fp64", "checkpoint_every": min(10, w.steps), "J_GeV": J.item(),
             "dJ_dk_rad": kr.grad.item(), "dJ_dk_coll": kc.grad.item(),
             "forward_s": round(t_fwd, 3), "backward_s": round(t_all - t_fwd, 3),
             "backward_over_forward": round((t_all - t_fwd) / t_fwd, 3),
@@ -407,7 +414,7 @@ def run_cuda(args, rank, ws):
     if not args.no_batched:
         out["batched"] = _batched(hy, args.steps, args.warmup)
     if not args.no_adjoint:
-        out["adjoint"] = _adjoint(hy)
+        out["adjoint"] = _adjoint(hy, args.adjoint_grid, args.adjoint_steps)
     if not args.no_e2e:
         sec, sb, db = _e2e(hy, w, prim_pinned, out_pinned, args.steps)
         sec = _max_over_ranks(sec, ws)
@@ -465,6 +472,10 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-event batched ensemble measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the 128^3 adjoint timing")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="run only the adjoint section (for profiling its kernels)")
+    ap.add_argument("--adjoint-grid", type=int, default=128)
+    ap.add_argument("--adjoint-steps", type=int, default=50)
     ap.add_argument("--grid", type=int, default=256,
                     help="cube edge; 256 is the paper's run, smaller edges are centre sub-grids for profiling")
     args = ap.parse_args(argv)
@@ -473,7 +484,12 @@ def main(argv=None):
     args.precisions = [p.strip() for p in args.precisions.split(",") if p.strip()]
     args.warmup = max(args.warmup, 3)   # timing rule: at least 3 untimed warm-up steps
     rank, ws, _ = _dist()
-    if args.impl == "reference":
+    if args.adjoint_only:
+        from paper_1511_02137_b300 import build
+        build.build()
+        from paper_1511_02137_b300 import hydro as hy
+        out = {"adjoint": _adjoint(hy, args.adjoint_grid, args.adjoint_steps)} if rank == 0 else None
+    elif args.impl == "reference":
         out = run_reference(args, rank, ws)
     else:
         out = run_cuda(args, rank, ws)
