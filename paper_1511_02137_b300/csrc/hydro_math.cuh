@@ -119,37 +119,6 @@ __device__ __forceinline__ typename M::T spectral_radius(typename M::T vd, typen
   return (fabs(vd) * (P(2) * third) + M::sqrt(disc * third)) * M::rcp(P(1) - v2 * third);
 }
 
-// Jiang-Shu weights w_k ~ d_k / (eps + beta_k)^2 applied to values that
-// already carry the factor d_k (Q_k = d_k q_k), giving
-// sum_k Q_k t_k / sum_k d_k t_k with t_k = 1/(eps + beta_k)^2.
-// FP64: one division, t_k ~ prod_{j != k} (eps + beta_j)^2.
-__device__ __forceinline__ double weno7_combine(double Q0, double Q1, double Q2, double Q3, double b0, double b1,
-                                                double b2, double b3, double eps) {
-  double s0 = eps + b0, s1 = eps + b1, s2 = eps + b2, s3 = eps + b3;
-  s0 *= s0;
-  s1 *= s1;
-  s2 *= s2;
-  s3 *= s3;
-  const double p01 = s0 * s1, p23 = s2 * s3;
-  const double t0 = s1 * p23, t1 = s0 * p23, t2 = s3 * p01, t3 = s2 * p01;
-  const double num = t0 * Q0 + t1 * Q1 + t2 * Q2 + t3 * Q3;
-  const double den = t0 + 12.0 * t1 + 18.0 * t2 + 4.0 * t3;
-  return num / den;
-}
-
-// FP32: the product form could overflow; one approximate reciprocal per weight.
-__device__ __forceinline__ float weno7_combine(float Q0, float Q1, float Q2, float Q3, float b0, float b1, float b2,
-                                               float b3, float eps) {
-  float t0 = rcp_approx(eps + b0), t1 = rcp_approx(eps + b1), t2 = rcp_approx(eps + b2), t3 = rcp_approx(eps + b3);
-  t0 *= t0;
-  t1 *= t1;
-  t2 *= t2;
-  t3 *= t3;
-  const float num = t0 * Q0 + t1 * Q1 + t2 * Q2 + t3 * Q3;
-  const float den = t0 + 12.0f * t1 + 18.0f * t2 + 4.0f * t3;
-  return num * rcp_approx(den);
-}
-
 // Scales of the WENO7 smoothness indicators: 720 beta = 20 A^2 + 780 B^2 + 781 C^2,
 // used as beta' = (720/781) beta = (sqrt(20/781) A)^2 + (sqrt(780/781) B)^2 + C^2.
 constexpr double kW7EpsScale = 720.0 / 781.0;
@@ -158,46 +127,100 @@ constexpr double kW7B = 0.999359590072005;     // sqrt(780/781)
 
 // WENO7 reconstruction at x_{i+1/2} from f0..f6 = f_{i-3..i+3} (finite-difference
 // form: the values are cell averages of the function reconstructed).
-// Candidate cubics on the four 4-cell stencils, linear weights (1, 12, 18, 4)/35,
-// Jiang-Shu weights, Balsara-Shu indicators
+// Candidate cubics q_k on the four 4-cell stencils, linear weights
+// (1, 12, 18, 4)/35, Jiang-Shu weights, Balsara-Shu indicators
 // beta_k = sum_{l=1..3} int_cell (h^l p_k^(l))^2 dx / h.  With p_k = a0 + a1 x +
 // a2 x^2 + a3 x^3 about the cell centre, beta = (a1 + a3/4)^2 + 13/3 a2^2 +
 // 781/20 a3^2, i.e. 720 beta_k = 20 A_k^2 + 780 B_k^2 + 781 C_k^2 with A_k, B_k,
-// C_k integer combinations of the first, second and third differences of the
-// stencil values.  The sum of squares stays non-negative in FP32, where the
-// expanded quadratic form cancels to negative values in smooth regions.
-// eps_s is (720/781) eps.
+// C_k integer combinations of the first (d1), second (d2) and third (c)
+// differences of the stencil values:
+//   A = (2,-7,11).d1[0..2], (-1,5,2).d1[1..3], (2,5,-1).d1[2..4], (11,-7,2).d1[3..5]
+//   B = 2 d2[1] - d2[0], d2[2], d2[2], 2 d2[3] - d2[4];  C_k = c[k].
+// The same terms give the candidates: q_k(x_{i+1/2}) - f_i = (A_k + B_k)/12, so
+//   reconstruction = f_i + sum_k d_k t_k (A_k + B_k)/12 / sum_k d_k t_k,
+// t_k = 1/(eps + beta_k)^2, d = (1, 12, 18, 4).  The sum of squares stays
+// non-negative in FP32, where the expanded quadratic form cancels to negative
+// values in smooth regions.
+//
+// weno7_terms returns z_k = d_k (A_k + B_k)/12 and s_k = eps_s + beta'_k
+// (beta' = 720/781 beta, eps_s = 720/781 eps; the common factor leaves the
+// weights unchanged): eps_s enters the innermost FMA of each indicator and the
+// scaled a_k = kA A_k, b_k = kB B_k serve both the indicators and z_k.
 template <class F>
-__device__ __forceinline__ F weno7(F f0, F f1, F f2, F f3, F f4, F f5, F f6, F eps_s) {
+__device__ __forceinline__ void weno7_terms(F f0, F f1, F f2, F f3, F f4, F f5, F f6, F eps_s, F z[4], F s[4]) {
   const F d10 = f1 - f0, d11 = f2 - f1, d12 = f3 - f2, d13 = f4 - f3, d14 = f5 - f4, d15 = f6 - f5;
-  // candidates q_k = f_i + (difference part); the differences times d_k/12 are R_k, so the
-  // reconstruction is f_i + sum_k t_k R_k / sum_k d_k t_k (the f_i part has weights summing to 1)
-  const F R0 = F(3.0 / 12.0) * d10 + F(-10.0 / 12.0) * d11 + F(13.0 / 12.0) * d12;
-  const F R1 = -d11 + F(4) * d12 + F(3) * d13;
-  const F R2 = F(1.5) * d12 + F(9) * d13 + F(-1.5) * d14;
-  const F R3 = F(3) * d13 + F(-4.0 / 3.0) * d14 + F(1.0 / 3.0) * d15;
   const F d20 = d11 - d10, d21 = d12 - d11, d22 = d13 - d12, d23 = d14 - d13, d24 = d15 - d14;
   const F c0 = d21 - d20, c1 = d22 - d21, c2 = d23 - d22, c3 = d24 - d23;
-  const F B = F(kW7B);
   const F a0 = F(2 * kW7A) * d10 + F(-7 * kW7A) * d11 + F(11 * kW7A) * d12;
   const F a1 = F(-kW7A) * d11 + F(5 * kW7A) * d12 + F(2 * kW7A) * d13;
   const F a2 = F(2 * kW7A) * d12 + F(5 * kW7A) * d13 + F(-kW7A) * d14;
   const F a3 = F(11 * kW7A) * d13 + F(-7 * kW7A) * d14 + F(2 * kW7A) * d15;
-  const F bb0 = F(2 * kW7B) * d21 - B * d20;
-  const F bb12 = B * d22;
-  const F bb3 = F(2 * kW7B) * d23 - B * d24;
-  const F m12 = bb12 * bb12;
-  const F b0 = a0 * a0 + (bb0 * bb0 + c0 * c0);
-  const F b1 = a1 * a1 + (c1 * c1 + m12);
-  const F b2 = a2 * a2 + (c2 * c2 + m12);
-  const F b3 = a3 * a3 + (bb3 * bb3 + c3 * c3);
-  return f3 + weno7_combine(R0, R1, R2, R3, b0, b1, b2, b3, eps_s);
+  const F b0 = F(2 * kW7B) * d21 + F(-kW7B) * d20;
+  const F b12 = F(kW7B) * d22;
+  const F b3 = F(2 * kW7B) * d23 + F(-kW7B) * d24;
+  z[0] = F(1.0 / (12 * kW7A)) * a0 + F(1.0 / (12 * kW7B)) * b0;
+  z[1] = F(1.0 / kW7A) * a1 + d22;
+  z[2] = F(1.5 / kW7A) * a2 + F(1.5) * d22;
+  z[3] = F(1.0 / (3 * kW7A)) * a3 + F(1.0 / (3 * kW7B)) * b3;
+  const F m12 = b12 * b12 + eps_s;
+  s[0] = a0 * a0 + (b0 * b0 + (c0 * c0 + eps_s));
+  s[1] = a1 * a1 + (c1 * c1 + m12);
+  s[2] = a2 * a2 + (c2 * c2 + m12);
+  s[3] = a3 * a3 + (b3 * b3 + (c3 * c3 + eps_s));
 }
 
-// ---- FP32 pair form: the left-biased f+ and the mirrored f- reconstruction of
-// one interface run the same operation sequence, so they are evaluated together
-// in the two lanes of Blackwell's packed FP32x2 instructions (FFMA2, FADD2,
-// FMUL2), halving the issue slots of the reconstruction.
+// FP64 weights in product form, t_k ~ prod_{j != k} s_j^2: the correction is
+// num/den with a single division.
+__device__ __forceinline__ void weno7_numden(const double z[4], const double s[4], double& num, double& den) {
+  const double q0 = s[0] * s[0], q1 = s[1] * s[1], q2 = s[2] * s[2], q3 = s[3] * s[3];
+  const double p01 = q0 * q1, p23 = q2 * q3;
+  const double t0 = q1 * p23, t1 = q0 * p23, t2 = q3 * p01, t3 = q2 * p01;
+  num = t0 * z[0] + t1 * z[1] + t2 * z[2] + t3 * z[3];
+  den = t0 + 12.0 * t1 + 18.0 * t2 + 4.0 * t3;
+}
+
+// FP32: the product form could overflow; one approximate reciprocal per weight.
+__device__ __forceinline__ float weno7_correction(const float z[4], const float s[4]) {
+  float t0 = rcp_approx(s[0]), t1 = rcp_approx(s[1]), t2 = rcp_approx(s[2]), t3 = rcp_approx(s[3]);
+  t0 *= t0;
+  t1 *= t1;
+  t2 *= t2;
+  t3 *= t3;
+  const float num = t0 * z[0] + t1 * z[1] + t2 * z[2] + t3 * z[3];
+  const float den = t0 + 12.0f * t1 + 18.0f * t2 + 4.0f * t3;
+  return num * rcp_approx(den);
+}
+
+__device__ __forceinline__ double weno7_correction(const double z[4], const double s[4]) {
+  double num, den;
+  weno7_numden(z, s, num, den);
+  return num / den;
+}
+
+template <class F>
+__device__ __forceinline__ F weno7(F f0, F f1, F f2, F f3, F f4, F f5, F f6, F eps_s) {
+  F z[4], s[4];
+  weno7_terms(f0, f1, f2, f3, f4, f5, f6, eps_s, z, s);
+  return f3 + weno7_correction(z, s);
+}
+
+// FP64 sum of the two reconstructions of one interface (f+ from g, f- from the
+// mirrored h): both corrections over one common denominator, one division
+// instead of two.  Each denominator lies in [eps_s^6, (eps_s + beta)^6], so the
+// product neither underflows (eps_s >= 1e-20) nor overflows for any indicator
+// below 1e25.
+__device__ __forceinline__ double weno7_sum(const double g[7], const double h[7], double eps_s) {
+  double zg[4], sg[4], zh[4], sh[4], ng, dg, nh, dh;
+  weno7_terms(g[0], g[1], g[2], g[3], g[4], g[5], g[6], eps_s, zg, sg);
+  weno7_terms(h[0], h[1], h[2], h[3], h[4], h[5], h[6], eps_s, zh, sh);
+  weno7_numden(zg, sg, ng, dg);
+  weno7_numden(zh, sh, nh, dh);
+  return (g[3] + h[3]) + (ng * dh + nh * dg) / (dg * dh);
+}
+
+// ---- FP32 pair form: two reconstructions that run the same operation
+// sequence are evaluated together in the two lanes of Blackwell's packed
+// FP32x2 instructions (FFMA2, FADD2, FMUL2), halving the issue slots.
 
 __device__ __forceinline__ float2 bc2(float c) { return make_float2(c, c); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
@@ -206,8 +229,7 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(rcp_approx(a.x), rcp_approx(a.y)); }
 
-// Same arithmetic as weno7<float> per lane (f_i plus the weighted difference
-// correction, scaled sum-of-squares indicators, one reciprocal per weight).
+// Same arithmetic as weno7<float> per lane.
 __device__ __forceinline__ float2 weno7_pair(float2 f0, float2 f1, float2 f2, float2 f3, float2 f4, float2 f5,
                                              float2 f6, float eps_s) {
   const float2 d10 = sub2(f1, f0), d11 = sub2(f2, f1), d12 = sub2(f3, f2), d13 = sub2(f4, f3), d14 = sub2(f5, f4),
@@ -215,30 +237,29 @@ __device__ __forceinline__ float2 weno7_pair(float2 f0, float2 f1, float2 f2, fl
   const float2 d20 = sub2(d11, d10), d21 = sub2(d12, d11), d22 = sub2(d13, d12), d23 = sub2(d14, d13),
                d24 = sub2(d15, d14);
   const float2 c0 = sub2(d21, d20), c1 = sub2(d22, d21), c2 = sub2(d23, d22), c3 = sub2(d24, d23);
-  const float2 R0 = fma2(bc2(3.0f / 12.0f), d10, fma2(bc2(-10.0f / 12.0f), d11, mul2(bc2(13.0f / 12.0f), d12)));
-  const float2 R1 = fma2(bc2(4.0f), d12, fma2(bc2(3.0f), d13, mul2(bc2(-1.0f), d11)));
-  const float2 R2 = fma2(bc2(1.5f), d12, fma2(bc2(9.0f), d13, mul2(bc2(-1.5f), d14)));
-  const float2 R3 = fma2(bc2(3.0f), d13, fma2(bc2(-4.0f / 3.0f), d14, mul2(bc2(1.0f / 3.0f), d15)));
   const float kA = (float)kW7A, kB = (float)kW7B;
   const float2 a0 = fma2(bc2(2 * kA), d10, fma2(bc2(-7 * kA), d11, mul2(bc2(11 * kA), d12)));
   const float2 a1 = fma2(bc2(-kA), d11, fma2(bc2(5 * kA), d12, mul2(bc2(2 * kA), d13)));
   const float2 a2 = fma2(bc2(2 * kA), d12, fma2(bc2(5 * kA), d13, mul2(bc2(-kA), d14)));
   const float2 a3 = fma2(bc2(11 * kA), d13, fma2(bc2(-7 * kA), d14, mul2(bc2(2 * kA), d15)));
-  const float2 bb0 = fma2(bc2(2 * kB), d21, mul2(bc2(-kB), d20));
-  const float2 bb12 = mul2(bc2(kB), d22);
-  const float2 bb3 = fma2(bc2(2 * kB), d23, mul2(bc2(-kB), d24));
-  const float2 m12 = mul2(bb12, bb12);
-  const float2 b0 = fma2(a0, a0, fma2(bb0, bb0, mul2(c0, c0)));
-  const float2 b1 = fma2(a1, a1, fma2(c1, c1, m12));
-  const float2 b2 = fma2(a2, a2, fma2(c2, c2, m12));
-  const float2 b3 = fma2(a3, a3, fma2(bb3, bb3, mul2(c3, c3)));
+  const float2 b0 = fma2(bc2(2 * kB), d21, mul2(bc2(-kB), d20));
+  const float2 b12 = mul2(bc2(kB), d22);
+  const float2 b3 = fma2(bc2(2 * kB), d23, mul2(bc2(-kB), d24));
+  const float2 z0 = fma2(bc2((float)(1.0 / (12 * kW7A))), a0, mul2(bc2((float)(1.0 / (12 * kW7B))), b0));
+  const float2 z1 = fma2(bc2((float)(1.0 / kW7A)), a1, d22);
+  const float2 z2 = fma2(bc2((float)(1.5 / kW7A)), a2, mul2(bc2(1.5f), d22));
+  const float2 z3 = fma2(bc2((float)(1.0 / (3 * kW7A))), a3, mul2(bc2((float)(1.0 / (3 * kW7B))), b3));
   const float2 e = bc2(eps_s);
-  float2 t0 = rcp2(add2(e, b0)), t1 = rcp2(add2(e, b1)), t2 = rcp2(add2(e, b2)), t3 = rcp2(add2(e, b3));
+  const float2 m12 = fma2(b12, b12, e);
+  float2 t0 = rcp2(fma2(a0, a0, fma2(b0, b0, fma2(c0, c0, e))));
+  float2 t1 = rcp2(fma2(a1, a1, fma2(c1, c1, m12)));
+  float2 t2 = rcp2(fma2(a2, a2, fma2(c2, c2, m12)));
+  float2 t3 = rcp2(fma2(a3, a3, fma2(b3, b3, fma2(c3, c3, e))));
   t0 = mul2(t0, t0);
   t1 = mul2(t1, t1);
   t2 = mul2(t2, t2);
   t3 = mul2(t3, t3);
-  const float2 num = fma2(t0, R0, fma2(t1, R1, fma2(t2, R2, mul2(t3, R3))));
+  const float2 num = fma2(t0, z0, fma2(t1, z1, fma2(t2, z2, mul2(t3, z3))));
   const float2 den = fma2(bc2(12.0f), t1, fma2(bc2(18.0f), t2, fma2(bc2(4.0f), t3, t0)));
   return fma2(num, rcp2(den), f3);
 }

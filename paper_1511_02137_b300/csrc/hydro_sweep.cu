@@ -57,6 +57,15 @@ __device__ __forceinline__ int map_along(int i, int n, int periodic) {
   return i < 0 ? 0 : (i >= n ? n - 1 : i);
 }
 
+// Maximum of two non-negative values.  Non-negative doubles order like their
+// bit patterns, so FP64 takes the integer maximum and leaves the FP64 pipe
+// (1/64 of the FP32 rate on this part) to the arithmetic.
+__device__ __forceinline__ double max_nonneg(double a, double b) {
+  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  return __longlong_as_double(ia > ib ? ia : ib);
+}
+__device__ __forceinline__ float max_nonneg(float a, float b) { return fmaxf(a, b); }
+
 // ---- TMA staging (cp.async.bulk.tensor) with an mbarrier, bounded wait
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -126,6 +135,14 @@ __device__ __forceinline__ void publish_block(T vmax, unsigned hits, DevDiag* d,
     if (speed) atomicMax(&d->vmax_bits, (unsigned long long)__double_as_longlong(m));
     if (floors && h) atomicAdd(&d->floor_hits, h);
   }
+}
+
+// Shared memory of one tile, in units of the flux type: U, F_d/2 (5 fields
+// each) and rho_d per staged cell, 5 numerical fluxes per interface.
+template <int ORDER, int SEG, int LANES>
+__host__ __device__ constexpr int tile_smem_words() {
+  constexpr int G = (ORDER == 7) ? 4 : 3, NCS = LANES * (SEG + 2 * G), NIF = LANES * (SEG + 1);
+  return 11 * NCS + 5 * NIF;
 }
 
 // One tile of a sweep: SEG cells along the sweep axis starting at a0, LANES
@@ -239,7 +256,7 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   auto flux_at = [&](int lane, int j, int q0, int q1) {
     F alpha = sR[sidx(lane, j)];
 #pragma unroll
-    for (int t = 1; t < 2 * G; ++t) alpha = fmax(alpha, sR[sidx(lane, j + t)]);
+    for (int t = 1; t < 2 * G; ++t) alpha = max_nonneg(alpha, sR[sidx(lane, j + t)]);
     const F ah = F(0.5) * alpha;
 #pragma unroll 1
     for (int q = q0; q < q1; ++q) {
@@ -249,29 +266,31 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
         u[t] = sU[q * NCS + sidx(lane, j + t)];
         f[t] = sF[q * NCS + sidx(lane, j + t)];
       }
-      F hp, hm;
+      F h;
       if constexpr (ORDER == 7 && sizeof(F) == 4) {
         // lane x: f+ from cells i-3..i+3; lane y: f- mirrored from cells i+4..i-2
         const float2 ahp = make_float2(ah, -ah);
         float2 g[7];
 #pragma unroll
-        for (int k = 0; k < 7; ++k)
-          g[k] = fma2(ahp, make_float2(u[k], u[7 - k]), make_float2(f[k], f[7 - k]));
-        const float2 h = weno7_pair(g[0], g[1], g[2], g[3], g[4], g[5], g[6], eps);
-        hp = h.x;
-        hm = h.y;
-      } else if (ORDER == 7) {
-        hp = weno7<F>(fma(ah, u[0], f[0]), fma(ah, u[1], f[1]), fma(ah, u[2], f[2]), fma(ah, u[3], f[3]),
-                      fma(ah, u[4], f[4]), fma(ah, u[5], f[5]), fma(ah, u[6], f[6]), eps);
-        hm = weno7<F>(fma(-ah, u[7], f[7]), fma(-ah, u[6], f[6]), fma(-ah, u[5], f[5]), fma(-ah, u[4], f[4]),
-                      fma(-ah, u[3], f[3]), fma(-ah, u[2], f[2]), fma(-ah, u[1], f[1]), eps);
+        for (int k = 0; k < 7; ++k) g[k] = fma2(ahp, make_float2(u[k], u[7 - k]), make_float2(f[k], f[7 - k]));
+        const float2 hh = weno7_pair(g[0], g[1], g[2], g[3], g[4], g[5], g[6], eps);
+        h = hh.x + hh.y;
+      } else if constexpr (ORDER == 7) {
+        // FP64: f+ from cells i-3..i+3 and f- mirrored from cells i+4..i-2, one division for both
+        F gp[7], gm[7];
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+          gp[k] = fma(ah, u[k], f[k]);
+          gm[k] = fma(-ah, u[7 - k], f[7 - k]);
+        }
+        h = weno7_sum(gp, gm, eps);
       } else {
-        hp = weno5<F>(fma(ah, u[0], f[0]), fma(ah, u[1], f[1]), fma(ah, u[2], f[2]), fma(ah, u[3], f[3]),
-                      fma(ah, u[4], f[4]), eps);
-        hm = weno5<F>(fma(-ah, u[5], f[5]), fma(-ah, u[4], f[4]), fma(-ah, u[3], f[3]), fma(-ah, u[2], f[2]),
-                      fma(-ah, u[1], f[1]), eps);
+        h = weno5<F>(fma(ah, u[0], f[0]), fma(ah, u[1], f[1]), fma(ah, u[2], f[2]), fma(ah, u[3], f[3]),
+                     fma(ah, u[4], f[4]), eps) +
+            weno5<F>(fma(-ah, u[5], f[5]), fma(-ah, u[4], f[4]), fma(-ah, u[3], f[3]), fma(-ah, u[2], f[2]),
+                     fma(-ah, u[1], f[1]), eps);
       }
-      sH[q * NIF + hidx(lane, j)] = hp + hm;
+      sH[q * NIF + hidx(lane, j)] = h;
     }
   };
   // the left faces of the tile's cells, all components, then the right face of
@@ -426,8 +445,8 @@ __global__ void reset_vmax_kernel(DevDiag* d, int n) {
 template <int PREC, int ORDER, int DIR>
 static cudaError_t launch_one(const SweepArgs& a, cudaStream_t s, const CUtensorMap* tmap) {
   using F = typename Types<PREC>::Flux;
-  constexpr int SEG = Tile<PREC, DIR>::SEG, LANES = Tile<PREC, DIR>::LANES, G = (ORDER == 7) ? 4 : 3;
-  constexpr size_t smem = sizeof(F) * (size_t)(11 * LANES * (SEG + 2 * G) + 5 * LANES * (SEG + 1));
+  constexpr int SEG = Tile<PREC, DIR>::SEG, LANES = Tile<PREC, DIR>::LANES;
+  constexpr size_t smem = sizeof(F) * (size_t)tile_smem_words<ORDER, SEG, LANES>();
   dim3 grid;
   if (DIR == 0) grid = dim3((a.nx + SEG - 1) / SEG, (a.ny + LANES - 1) / LANES, a.nz);
   else if (DIR == 1) grid = dim3((a.nx + LANES - 1) / LANES, (a.ny + SEG - 1) / SEG, a.nz);
@@ -527,7 +546,7 @@ bool encode_sweep_tmaps(int precision, int order, void* const bufs[3], int nx, i
 template <int PREC, int DIR, int SEG, int LANES>
 static constexpr size_t batch_smem() {
   using F = typename Types<PREC>::Flux;
-  return sizeof(F) * (size_t)(11 * LANES * (SEG + 8) + 5 * LANES * (SEG + 1));
+  return sizeof(F) * (size_t)tile_smem_words<7, SEG, LANES>();
 }
 
 template <int PREC, int DIR, int SEG, int LANES>

@@ -60,7 +60,8 @@ def test_workspace_size_counts_three_states_and_rhs(hy):
 
 
 @pytest.mark.parametrize("field,value", [("nx", 0), ("precision", 7), ("boundary", 5), ("weno_order", 6),
-                                         ("dx", 0.0), ("dt", -1.0), ("e_floor", 0.0), ("hbarc", 0.0)])
+                                         ("dx", 0.0), ("dt", -1.0), ("e_floor", 0.0), ("hbarc", 0.0),
+                                         ("weno_eps", 0.0), ("weno_eps", 1e-30), ("weno_eps", 1e30)])
 def test_invalid_configuration_is_rejected_without_touching_the_device(hy, field, value):
     c = hy.hydro_config_default(16, 16, 16)
     setattr(c, field, value)
