@@ -138,9 +138,12 @@ constexpr double kW7B = 0.999359590072005;     // sqrt(780/781)
 //   B = 2 d2[1] - d2[0], d2[2], d2[2], 2 d2[3] - d2[4];  C_k = c[k].
 // The same terms give the candidates: q_k(x_{i+1/2}) - f_i = (A_k + B_k)/12, so
 //   reconstruction = f_i + sum_k d_k t_k (A_k + B_k)/12 / sum_k d_k t_k,
-// t_k = 1/(eps + beta_k)^2, d = (1, 12, 18, 4).  The sum of squares stays
-// non-negative in FP32, where the expanded quadratic form cancels to negative
-// values in smooth regions.
+// t_k = 1/(eps + beta_k)^2, d = (1, 12, 18, 4).  Neighbouring stencils differ
+// by fourth differences e_k = c[k+1] - c[k]:
+//   A_1 = A_0 + 2 e_0,  A_2 = A_1 - e_1,  A_3 = A_2 + 2 e_2,
+//   B_0 = d2[2] - e_0,  B_3 = d2[2] - e_2.
+// The sum of squares stays non-negative in FP32, where the expanded quadratic
+// form cancels to negative values in smooth regions.
 //
 // weno7_terms returns z_k = d_k (A_k + B_k)/12 and s_k = eps_s + beta'_k
 // (beta' = 720/781 beta, eps_s = 720/781 eps; the common factor leaves the
@@ -151,13 +154,14 @@ __device__ __forceinline__ void weno7_terms(F f0, F f1, F f2, F f3, F f4, F f5, 
   const F d10 = f1 - f0, d11 = f2 - f1, d12 = f3 - f2, d13 = f4 - f3, d14 = f5 - f4, d15 = f6 - f5;
   const F d20 = d11 - d10, d21 = d12 - d11, d22 = d13 - d12, d23 = d14 - d13, d24 = d15 - d14;
   const F c0 = d21 - d20, c1 = d22 - d21, c2 = d23 - d22, c3 = d24 - d23;
+  const F e0 = c1 - c0, e1 = c2 - c1, e2 = c3 - c2;
   const F a0 = F(2 * kW7A) * d10 + F(-7 * kW7A) * d11 + F(11 * kW7A) * d12;
-  const F a1 = F(-kW7A) * d11 + F(5 * kW7A) * d12 + F(2 * kW7A) * d13;
-  const F a2 = F(2 * kW7A) * d12 + F(5 * kW7A) * d13 + F(-kW7A) * d14;
-  const F a3 = F(11 * kW7A) * d13 + F(-7 * kW7A) * d14 + F(2 * kW7A) * d15;
-  const F b0 = F(2 * kW7B) * d21 + F(-kW7B) * d20;
+  const F a1 = F(2 * kW7A) * e0 + a0;
+  const F a2 = F(-kW7A) * e1 + a1;
+  const F a3 = F(2 * kW7A) * e2 + a2;
   const F b12 = F(kW7B) * d22;
-  const F b3 = F(2 * kW7B) * d23 + F(-kW7B) * d24;
+  const F b0 = F(-kW7B) * e0 + b12;
+  const F b3 = F(-kW7B) * e2 + b12;
   z[0] = F(1.0 / (12 * kW7A)) * a0 + F(1.0 / (12 * kW7B)) * b0;
   z[1] = F(1.0 / kW7A) * a1 + d22;
   z[2] = F(1.5 / kW7A) * a2 + F(1.5) * d22;
@@ -237,14 +241,15 @@ __device__ __forceinline__ float2 weno7_pair(float2 f0, float2 f1, float2 f2, fl
   const float2 d20 = sub2(d11, d10), d21 = sub2(d12, d11), d22 = sub2(d13, d12), d23 = sub2(d14, d13),
                d24 = sub2(d15, d14);
   const float2 c0 = sub2(d21, d20), c1 = sub2(d22, d21), c2 = sub2(d23, d22), c3 = sub2(d24, d23);
+  const float2 e0 = sub2(c1, c0), e1 = sub2(c2, c1), e2 = sub2(c3, c2);
   const float kA = (float)kW7A, kB = (float)kW7B;
   const float2 a0 = fma2(bc2(2 * kA), d10, fma2(bc2(-7 * kA), d11, mul2(bc2(11 * kA), d12)));
-  const float2 a1 = fma2(bc2(-kA), d11, fma2(bc2(5 * kA), d12, mul2(bc2(2 * kA), d13)));
-  const float2 a2 = fma2(bc2(2 * kA), d12, fma2(bc2(5 * kA), d13, mul2(bc2(-kA), d14)));
-  const float2 a3 = fma2(bc2(11 * kA), d13, fma2(bc2(-7 * kA), d14, mul2(bc2(2 * kA), d15)));
-  const float2 b0 = fma2(bc2(2 * kB), d21, mul2(bc2(-kB), d20));
+  const float2 a1 = fma2(bc2(2 * kA), e0, a0);
+  const float2 a2 = fma2(bc2(-kA), e1, a1);
+  const float2 a3 = fma2(bc2(2 * kA), e2, a2);
   const float2 b12 = mul2(bc2(kB), d22);
-  const float2 b3 = fma2(bc2(2 * kB), d23, mul2(bc2(-kB), d24));
+  const float2 b0 = fma2(bc2(-kB), e0, b12);
+  const float2 b3 = fma2(bc2(-kB), e2, b12);
   const float2 z0 = fma2(bc2((float)(1.0 / (12 * kW7A))), a0, mul2(bc2((float)(1.0 / (12 * kW7B))), b0));
   const float2 z1 = fma2(bc2((float)(1.0 / kW7A)), a1, d22);
   const float2 z2 = fma2(bc2((float)(1.5 / kW7A)), a2, mul2(bc2(1.5f), d22));

@@ -99,6 +99,14 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// Asynchronous global -> shared copies of B bytes (cp.async, L1-allocating).
+template <int B>
+__device__ __forceinline__ void cp_async_ca(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(smem)), "l"(gmem), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Spins on the barrier phase with an iteration limit; false when it gave up.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned phase) {
   for (long it = 0; it < (1L << 24); ++it)
@@ -137,12 +145,28 @@ __device__ __forceinline__ void publish_block(T vmax, unsigned hits, DevDiag* d,
   }
 }
 
+// FP32 flux arithmetic issues fast enough that the phase-3 operands (the
+// accumulator of the y and z sweeps, the step state U0 and, in mixed precision,
+// the stage state) are fetched into shared memory asynchronously at the start
+// of the tile, so that their latency hides behind phases 1 and 2.  FP64 tiles
+// are bound by the FP64 pipe and keep the direct loads (and their occupancy).
+template <int PREC, int DIR>
+struct Prefetch {
+  static constexpr bool on = sizeof(typename Types<PREC>::Flux) == 4 && DIR != 0;
+  static constexpr int rhs = on ? 5 : 0;                      // accumulator fields
+  static constexpr int state = on && DIR == 2 ? (PREC == HYDRO_MIXED ? 10 : 5) : 0;   // U0 (+ U)
+};
+
 // Shared memory of one tile, in units of the flux type: U, F_d/2 (5 fields
-// each) and rho_d per staged cell, 5 numerical fluxes per interface.
-template <int ORDER, int SEG, int LANES>
+// each) and rho_d per staged cell, 5 numerical fluxes per interface, and the
+// prefetched phase-3 operands per updated cell.
+template <int PREC, int ORDER, int DIR, int SEG, int LANES>
 __host__ __device__ constexpr int tile_smem_words() {
-  constexpr int G = (ORDER == 7) ? 4 : 3, NCS = LANES * (SEG + 2 * G), NIF = LANES * (SEG + 1);
-  return 11 * NCS + 5 * NIF;
+  using F = typename Types<PREC>::Flux;
+  using Store = typename Types<PREC>::Store;
+  constexpr int G = (ORDER == 7) ? 4 : 3, NCS = LANES * (SEG + 2 * G), NIF = LANES * (SEG + 1), NC = LANES * SEG;
+  return 11 * NCS + 5 * NIF + Prefetch<PREC, DIR>::rhs * NC +
+         Prefetch<PREC, DIR>::state * NC * (int)(sizeof(Store) / sizeof(F));
 }
 
 // One tile of a sweep: SEG cells along the sweep axis starting at a0, LANES
@@ -181,8 +205,39 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   auto sidx = [&](int lane, int s) { return DIR == 0 ? lane * W + s : s * LANES + lane; };
   auto hidx = [&](int lane, int j) { return DIR == 0 ? lane * (SEG + 1) + j : j * LANES + lane; };
 
-  // ---------------- phase 1: stage cells, primitives, half fluxes, rho
+  // ---------------- phase-3 operands, fetched asynchronously
   const Store* __restrict__ U = static_cast<const Store*>(a.U);
+  using PF = Prefetch<PREC, DIR>;
+  F* sPr = sH + 5 * NIF;                                 // [5][NC] accumulator
+  Store* sP0 = reinterpret_cast<Store*>(sPr + 5 * NC);   // [5][NC] U0, then (mixed) [5][NC] U
+  if constexpr (PF::on) {
+    const bool need_u0 = FINAL && a.a != 0.0;
+    const F* rhs_in = static_cast<const F*>(a.rhs);
+    const Store* U0_in = static_cast<const Store*>(a.U0);
+    for (int c = threadIdx.x; c < NC; c += kThreads) {
+      int lane, j;
+      if (DIR == 0) { lane = c / SEG; j = c - lane * SEG; }
+      else { j = c / LANES; lane = c - j * LANES; }
+      const int ga = a0 + j, gl = l0 + lane;
+      if (ga >= n_along || gl >= n_lane) continue;
+      const size_t o = offset(ga, gl);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) cp_async_ca<sizeof(F)>(sPr + q * NC + c, rhs_in + q * N + o);
+      if constexpr (FINAL) {
+        if (need_u0) {
+#pragma unroll
+          for (int q = 0; q < 5; ++q) cp_async_ca<sizeof(Store)>(sP0 + q * NC + c, U0_in + q * N + o);
+        }
+        if constexpr (PREC == HYDRO_MIXED) {
+#pragma unroll
+          for (int q = 0; q < 5; ++q) cp_async_ca<sizeof(Store)>(sP0 + (5 + q) * NC + c, U + q * N + o);
+        }
+      }
+    }
+    cp_async_commit();
+  }
+
+  // ---------------- phase 1: stage cells, primitives, half fluxes, rho
   // a tile whose halo lies inside the grid needs no ghost cells: one TMA box of all 5 fields
   bool staged = false;
   if constexpr (TMA) {
@@ -323,6 +378,7 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   F* __restrict__ rhs = static_cast<F*>(a.rhs);
   const F inv_dx = (F)a.inv_dx;
   bool bad = false;
+  if constexpr (PF::on) cp_async_wait_all();   // each thread reads only its own copies
   for (int c = threadIdx.x; c < NC; c += kThreads) {
     int lane, j;
     if (DIR == 0) { lane = c / SEG; j = c - lane * SEG; }
@@ -340,13 +396,13 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
         for (int q = 0; q < 5; ++q) rhs[q * N + o] = L[q];
       } else {
 #pragma unroll
-        for (int q = 0; q < 5; ++q) rhs[q * N + o] += L[q];
+        for (int q = 0; q < 5; ++q) rhs[q * N + o] = (PF::on ? sPr[q * NC + c] : rhs[q * N + o]) + L[q];
       }
     } else {
       // accumulate in storage precision (FP64 for FP64 and mixed, FP32 for FP32)
       Store Ld[5];
 #pragma unroll
-      for (int q = 0; q < 5; ++q) Ld[q] = (Store)(rhs[q * N + o] + L[q]);
+      for (int q = 0; q < 5; ++q) Ld[q] = (Store)((PF::on ? sPr[q * NC + c] : rhs[q * N + o]) + L[q]);
       if (jets_here) {
         const int gx = DIR == 0 ? ga : gl;
         const int gy = DIR == 1 ? ga : (DIR == 0 ? gl : fixed);
@@ -378,9 +434,10 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
 #pragma unroll
       for (int q = 0; q < 5; ++q) {
         // the cell's own state is staged already unless storage and flux types differ (mixed)
-        const Store u = (PREC == HYDRO_MIXED) ? U[q * N + o] : (Store)sU[q * NCS + sidx(lane, j + G)];
+        const Store u = (PREC == HYDRO_MIXED) ? (PF::on ? sP0[(5 + q) * NC + c] : U[q * N + o])
+                                              : (Store)sU[q * NCS + sidx(lane, j + G)];
         const Store l = Ld[q];
-        Store out = (a.a == 0.0) ? u + dt * l : ca * U0[q * N + o] + cb * (u + dt * l);
+        Store out = (a.a == 0.0) ? u + dt * l : ca * (PF::on ? sP0[q * NC + c] : U0[q * N + o]) + cb * (u + dt * l);
         bad |= !isfinite(out);
         Uout[q * N + o] = out;
       }
@@ -446,7 +503,7 @@ template <int PREC, int ORDER, int DIR>
 static cudaError_t launch_one(const SweepArgs& a, cudaStream_t s, const CUtensorMap* tmap) {
   using F = typename Types<PREC>::Flux;
   constexpr int SEG = Tile<PREC, DIR>::SEG, LANES = Tile<PREC, DIR>::LANES;
-  constexpr size_t smem = sizeof(F) * (size_t)tile_smem_words<ORDER, SEG, LANES>();
+  constexpr size_t smem = sizeof(F) * (size_t)tile_smem_words<PREC, ORDER, DIR, SEG, LANES>();
   dim3 grid;
   if (DIR == 0) grid = dim3((a.nx + SEG - 1) / SEG, (a.ny + LANES - 1) / LANES, a.nz);
   else if (DIR == 1) grid = dim3((a.nx + LANES - 1) / LANES, (a.ny + SEG - 1) / SEG, a.nz);
@@ -546,7 +603,7 @@ bool encode_sweep_tmaps(int precision, int order, void* const bufs[3], int nx, i
 template <int PREC, int DIR, int SEG, int LANES>
 static constexpr size_t batch_smem() {
   using F = typename Types<PREC>::Flux;
-  return sizeof(F) * (size_t)tile_smem_words<7, SEG, LANES>();
+  return sizeof(F) * (size_t)tile_smem_words<PREC, 7, DIR, SEG, LANES>();
 }
 
 template <int PREC, int DIR, int SEG, int LANES>
