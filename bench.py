@@ -314,11 +314,7 @@ def _batched(hy, steps, warmup):
             "timing": "wall clock around hydro_batch_step (CUDA graph replay, includes host jet tables and sync)"}
 
 
-def _adjoint(hy, grid=128, steps=50):
-    """The adjoint configuration: 128^3, 50 steps, checkpoint every 10, one jet
-    from (-4, 0, 0) fm along +x, energy in a 30-degree cone of radius 3 fm around
-    the jet axis; gradient with respect to k_rad, k_coll and e(x).  Times one
-    forward and one forward + backward through torch.autograd (wall clock, synced)."""
+def _adjoint_one(hy, grid, steps, precision):
     import torch
     from paper_1511_02137_b300 import adjoint as A
     from paper_1511_02137_b300 import workloads as W
@@ -326,7 +322,7 @@ def _adjoint(hy, grid=128, steps=50):
     w = W.Workload(name=f"ellipsoidal-flow {grid}^3, {steps} RK3 steps, 1 jet (adjoint)", n=(grid, grid, grid),
                    steps=steps, sigma=(4.0, 5.0, 6.0), jets=(jet,))
     prim = W.ellipsoidal_primitives(w)
-    run = A.ConeEnergyRun(hy.hydro_config_default(*w.n), w.steps, min(10, w.steps), w.jets,
+    run = A.ConeEnergyRun(hy.hydro_config_default(*w.n, precision=precision), w.steps, min(10, w.steps), w.jets,
                           torch.from_numpy(prim[1:].copy()).cuda(), apex=jet.x0, axis=jet.direction)
     e = torch.from_numpy(prim[0].copy()).cuda()
     kr = torch.tensor(4.0, dtype=torch.float64, requires_grad=True)
@@ -343,11 +339,29 @@ def _adjoint(hy, grid=128, steps=50):
     J.backward()
     torch.cuda.synchronize()
     t_all = time.perf_counter() - t0
-    return {"workload": w.name, "precision": "fp64", "checkpoint_every": min(10, w.steps), "J_GeV": J.item(),
-            "dJ_dk_rad": kr.grad.item(), "dJ_dk_coll": kc.grad.item(),
-            "forward_s": round(t_fwd, 3), "backward_s": round(t_all - t_fwd, 3),
-            "backward_over_forward": round((t_all - t_fwd) / t_fwd, 3),
-            "forward_cell_updates_per_s": w.cells * w.steps / t_fwd}
+    res = {"workload": w.name, "precision": precision, "checkpoint_every": min(10, w.steps), "J_GeV": J.item(),
+           "dJ_dk_rad": kr.grad.item(), "dJ_dk_coll": kc.grad.item(),
+           "forward_s": round(t_fwd, 3), "backward_s": round(t_all - t_fwd, 3),
+           "backward_over_forward": round((t_all - t_fwd) / t_fwd, 3),
+           "forward_cell_updates_per_s": w.cells * w.steps / t_fwd}
+    return res, ev.grad
+
+
+def _adjoint(hy, grid=128, steps=50):
+    """The adjoint configuration: 128^3, 50 steps, checkpoint every 10, one jet
+    from (-4, 0, 0) fm along +x, energy in a 30-degree cone of radius 3 fm around
+    the jet axis; gradient with respect to k_rad, k_coll and e(x), in FP64 and in
+    mixed precision.  Times one forward and one forward + backward through
+    torch.autograd (wall clock, synced).  The mixed entry carries its gradient's
+    deviation from the FP64 gradient (relative, max-norm for the e field)."""
+    out, g64 = _adjoint_one(hy, grid, steps, "fp64")
+    mixed, g32 = _adjoint_one(hy, grid, steps, "mixed")
+    mixed["vs_fp64"] = {"J": abs(mixed["J_GeV"] / out["J_GeV"] - 1),
+                        "dJ_dk_rad": abs(mixed["dJ_dk_rad"] / out["dJ_dk_rad"] - 1),
+                        "dJ_dk_coll": abs(mixed["dJ_dk_coll"] / out["dJ_dk_coll"] - 1),
+                        "dJ_de_maxnorm": float((g32 - g64).abs().max() / g64.abs().max())}
+    out["mixed"] = mixed
+    return out
 
 
 def run_cuda(args, rank, ws):

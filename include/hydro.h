@@ -214,17 +214,21 @@ void hydro_batch_destroy(hydro_batch* b);
  * Adjoint: gradients of a final-time observable, the energy J = sum E dx^3 in a
  * cone (apex, axis, half angle, radius rmax) after nsteps RK3 steps, with
  * respect to k_rad and k_coll of Eq. 3 and the initial energy density field.
- * Reverse mode of the FP64 step written by hand (vector-Jacobian products of
- * the WENO7 fluxes, the LLF split, the primitive recovery and the jet source),
+ * Reverse mode of the step written by hand (vector-Jacobian products of the
+ * WENO7 fluxes, the LLF split, the primitive recovery and the jet source),
  * states checkpointed every `checkpoint_every` steps and recomputed segment by
- * segment in reverse.  FP64, outflow, WENO7 only.  The derivative of the LLF
- * alpha = max over the stencil is split equally among tying cells.
+ * segment in reverse.  Outflow, WENO7 only; precision HYDRO_FP64, or
+ * HYDRO_MIXED (the mixed forward; its vector-Jacobian products in FP32 flux
+ * arithmetic, adjoint states and stage combinations in FP64).  The derivative
+ * of the LLF alpha = max over the stencil is split equally among tying cells
+ * (within 1e-12 relative in FP64, 1e-6 in mixed).
  * ------------------------------------------------------------------------- */
 typedef struct hydro_adjoint hydro_adjoint;
 
 /* Sets up an adjoint run (allocates checkpoint, segment and adjoint buffers
- * with cudaMalloc).  HYDRO_EINVAL unless precision = HYDRO_FP64, boundary =
- * HYDRO_OUTFLOW and weno_order = 7, or for non-positive sizes or cone. */
+ * with cudaMalloc).  HYDRO_EINVAL unless precision is HYDRO_FP64 or
+ * HYDRO_MIXED, boundary = HYDRO_OUTFLOW and weno_order = 7, or for
+ * non-positive sizes or cone. */
 hydro_status hydro_adjoint_create(const hydro_config* cfg, int32_t nsteps, int32_t checkpoint_every,
                                   const double apex[3], const double axis[3], double half_angle_deg, double rmax,
                                   hydro_adjoint** out);

@@ -4,10 +4,10 @@
         half angle 30 deg, radius 3 fm) of E dx^3 after N RK3 steps
 
 as a differentiable function of the initial energy density e(x) and of k_rad,
-k_coll of Eq. 3.  The forward pass runs the FP64 CUDA step keeping a
-checkpoint every k steps; the backward pass calls the library's reverse-mode
-kernels (hydro_adjoint_backward), which recompute each segment from its
-checkpoint.  No autograd tape is recorded inside: torch only carries the
+k_coll of Eq. 3.  The forward pass runs the CUDA step in the precision of the
+configuration (FP64, or mixed) keeping a checkpoint every k steps; the
+backward pass calls the library's reverse-mode kernels
+(hydro_adjoint_backward), which recompute each segment from its checkpoint.  No autograd tape is recorded inside: torch only carries the
 inputs and the gradients.
 """
 from __future__ import annotations

@@ -1,6 +1,9 @@
-// Adjoint (reverse mode) of the FP64 RK3-WENO7 step with jet sources, and a
+// Adjoint (reverse mode) of the RK3-WENO7 step with jet sources, and a
 // cone-energy observable with gradients with respect to k_rad, k_coll and the
 // initial energy density (checkpointed every k steps, recomputed in reverse).
+// Two precisions, as the forward: FP64 throughout, or mixed (FP64 states,
+// stage combinations and adjoint accumulation; FP32 flux arithmetic and its
+// vector-Jacobian products; E^2 - |M|^2 of the recovery in FP64).
 //
 // The vector-Jacobian product of the right-hand side L(U) = -div F + S runs as
 // three sweeps (x, y, z), like the forward.  A tile gathers, for each of its
@@ -17,6 +20,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "hydro.h"
@@ -28,7 +32,11 @@ namespace hydro {
 
 namespace {
 
-constexpr int kAdjThreads = 256;
+// Threads per tile: FP64 tiles are bound by the FP64 pipe and keep 256 (two
+// blocks per SM at ~120 registers); FP32-flux (mixed) tiles take one thread
+// per interface of the tile (kAdjNIF = 288), so that each component's reverse
+// WENO pass is a single round.
+template <int PREC> __host__ __device__ constexpr int adj_threads() { return PREC == HYDRO_MIXED ? 288 : 256; }
 constexpr int kAdjSeg = 64;     // cells per line along the sweep axis
 constexpr int kAdjLanes = 4;    // lines per tile
 constexpr int kAdjW = kAdjSeg + 16;              // staged positions per line: a0-8 .. a0+SEG+7
@@ -36,14 +44,22 @@ constexpr int kAdjNCS = kAdjLanes * kAdjW;
 constexpr int kAdjNI = kAdjSeg + 8;              // interfaces i = a0-4 .. a0+SEG+3
 constexpr int kAdjNIF = kAdjLanes * kAdjNI;
 constexpr int kAdjNC = kAdjLanes * kAdjSeg;
-constexpr size_t kAdjSmem = sizeof(double) * (size_t)(16 * kAdjNCS + 16 * kAdjNIF + 2 * kAdjNIF + 10 * kAdjNC) +
-                            sizeof(unsigned) * kAdjNIF;
+template <class P>
+constexpr size_t adj_smem() {
+  return sizeof(P) * (size_t)(16 * kAdjNCS + 16 * kAdjNIF + 2 * kAdjNIF + 10 * kAdjNC) + sizeof(unsigned) * kAdjNIF;
+}
+
+// Flux arithmetic of the adjoint sweeps: the forward's (FP64, or FP32 for mixed).
+template <int PREC> struct AdjTypes { using P = double; using Math = MathD; };
+template <> struct AdjTypes<HYDRO_MIXED> { using P = float; using Math = MathF; };
 
 struct VjpArgs {
   const double* U;      // stage state the right-hand side was evaluated on
-  const double* lam;    // adjoint of the stage result; a = ascale * lam is the adjoint of L
-  double* r;            // output J_L^T a (x sweep writes, y and z add)
-  double* kbar;         // [2]: dJ/dk_rad, dJ/dk_coll accumulators
+  const double* lam;    // adjoint of the stage result; a = ascale * lam is the adjoint of L (FP64)
+  const float* sh;      // mixed: FP32 shadow of U, [7][n] = E, M^x, M^y, M^z, R, signed floored E, om
+  const float* lamf;    // mixed: a = ascale * lam, already scaled, in FP32
+  void* r;              // output J_L^T a in the flux type (x sweep writes, y and z add)
+  double* kbar;         // [2 kMaxJets]: dJ/dk_rad, dJ/dk_coll per jet (one writer per jet and stage)
   double ascale;
   int nx, ny, nz;
   double inv_dx, e_floor, eps_s;
@@ -53,23 +69,35 @@ struct VjpArgs {
 
 __device__ __forceinline__ int clampi(int i, int n) { return i < 0 ? 0 : (i >= n ? n - 1 : i); }
 
-template <int DIR>
-__global__ void __launch_bounds__(kAdjThreads) vjp_kernel(const VjpArgs p) {
+__device__ __forceinline__ long long bits_of(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ int bits_of(float x) { return __float_as_int(x); }
+template <class P> __device__ __forceinline__ P from_bits(long long b) { return __longlong_as_double(b); }
+template <> __device__ __forceinline__ float from_bits<float>(long long b) { return __int_as_float((int)b); }
+
+template <int PREC, int DIR>
+__global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs p) {
+  constexpr int kAdjThreads = adj_threads<PREC>();
+  using P = typename AdjTypes<PREC>::P;
+  using Math = typename AdjTypes<PREC>::Math;
+  constexpr bool MIXED = PREC == HYDRO_MIXED;
   constexpr int SEG = kAdjSeg, LANES = kAdjLanes, W = kAdjW, NCS = kAdjNCS, NI = kAdjNI, NIF = kAdjNIF,
                 NC = kAdjNC;
   constexpr bool FINAL = DIR == 2;
+  // cells whose alpha lies within this relative distance of the maximum share its derivative
+  constexpr P kTie = MIXED ? P(1e-6) : P(1e-12);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* sU = reinterpret_cast<double*>(smem_raw);   // [5][NCS]
-  double* sF = sU + 5 * NCS;                          // [5][NCS] F_d/2
-  double* sA = sF + 5 * NCS;                          // [5][NCS] adjoint of L (0 outside the grid)
-  double* sR = sA + 5 * NCS;                          // [NCS] rho_d
-  double* cF = sR + NCS;                              // [NIF][8] adjoint of F_d/2 per stencil slot
-  double* cU = cF + 8 * NIF;                          // [NIF][8] direct adjoint of U per stencil slot
-  double* sAl = cU + 8 * NIF;                         // [NIF] alpha
-  double* sAhb = sAl + NIF;                           // [NIF] adjoint of alpha/2
-  double* sFb = sAhb + NIF;                           // [5][NC] gathered adjoint of F_d/2
-  double* sUb = sFb + 5 * NC;                         // [5][NC] gathered direct adjoint of U
+  P* sU = reinterpret_cast<P*>(smem_raw);   // [5][NCS]
+  P* sF = sU + 5 * NCS;                     // [5][NCS] F_d/2
+  P* sA = sF + 5 * NCS;                     // [5][NCS] adjoint of L (0 outside the grid)
+  P* sR = sA + 5 * NCS;                     // [NCS] rho_d
+  P* cF = sR + NCS;                         // [8][NIF] adjoint of F_d/2 per stencil slot
+  P* cU = cF + 8 * NIF;                     // [8][NIF] direct adjoint of U per stencil slot
+  P* sAl = cU + 8 * NIF;                    // [NIF] alpha
+  P* sAhb = sAl + NIF;                      // [NIF] adjoint of alpha/2
+  P* sFb = sAhb + NIF;                      // [5][NC] gathered adjoint of F_d/2
+  P* sUb = sFb + 5 * NC;                    // [5][NC] gathered direct adjoint of U
   unsigned* sTie = reinterpret_cast<unsigned*>(sUb + 5 * NC);   // [NIF] slots attaining max rho
+  P* r_out = static_cast<P*>(p.r);
 
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   const size_t N = (size_t)nx * ny * nz;
@@ -96,22 +124,31 @@ __global__ void __launch_bounds__(kAdjThreads) vjp_kernel(const VjpArgs p) {
     const int ga = a0 - 8 + s;
     const int gl = l0 + lane;
     const size_t o = offset(clampi(ga, n_along), gl < n_lane ? gl : n_lane - 1);
-    const double E = p.U[o], Mx = p.U[N + o], My = p.U[2 * N + o], Mz = p.U[3 * N + o], R = p.U[4 * N + o];
-    double e, vx, vy, vz;
+    P e, vx, vy, vz, E, Mx, My, Mz, R;
     int hit = 0;
-    cons_to_prim<MathD>(E, Mx, My, Mz, p.e_floor, e, vx, vy, vz, hit);
-    const double pr = e * (1.0 / 3.0);
-    const double vd = DIR == 0 ? vx : (DIR == 1 ? vy : vz);
+    if constexpr (MIXED) {
+      E = p.sh[o]; Mx = p.sh[N + o]; My = p.sh[2 * N + o]; Mz = p.sh[3 * N + o]; R = p.sh[4 * N + o];
+      cons_to_prim_om(p.sh[5 * N + o], Mx, My, Mz, p.sh[6 * N + o], e, vx, vy, vz, hit);
+    } else {
+      E = p.U[o]; Mx = p.U[N + o]; My = p.U[2 * N + o]; Mz = p.U[3 * N + o]; R = p.U[4 * N + o];
+      cons_to_prim<MathD>(E, Mx, My, Mz, p.e_floor, e, vx, vy, vz, hit);
+    }
+    const P pr = e * P(1.0 / 3.0);
+    const P vd = DIR == 0 ? vx : (DIR == 1 ? vy : vz);
     sU[c] = E; sU[NCS + c] = Mx; sU[2 * NCS + c] = My; sU[3 * NCS + c] = Mz; sU[4 * NCS + c] = R;
-    sF[c] = 0.5 * (DIR == 0 ? Mx : (DIR == 1 ? My : Mz));
-    sF[NCS + c] = 0.5 * (Mx * vd + (DIR == 0 ? pr : 0.0));
-    sF[2 * NCS + c] = 0.5 * (My * vd + (DIR == 1 ? pr : 0.0));
-    sF[3 * NCS + c] = 0.5 * (Mz * vd + (DIR == 2 ? pr : 0.0));
-    sF[4 * NCS + c] = 0.5 * (R * vd);
-    sR[c] = spectral_radius<MathD>(vd, vx * vx + vy * vy + vz * vz);
+    sF[c] = P(0.5) * (DIR == 0 ? Mx : (DIR == 1 ? My : Mz));
+    sF[NCS + c] = P(0.5) * (Mx * vd + (DIR == 0 ? pr : P(0)));
+    sF[2 * NCS + c] = P(0.5) * (My * vd + (DIR == 1 ? pr : P(0)));
+    sF[3 * NCS + c] = P(0.5) * (Mz * vd + (DIR == 2 ? pr : P(0)));
+    sF[4 * NCS + c] = P(0.5) * (R * vd);
+    sR[c] = spectral_radius<Math>(vd, vx * vx + vy * vy + vz * vz);
     const bool inside = ga >= 0 && ga < n_along && gl < n_lane;
     const size_t oa = offset(inside ? ga : 0, gl < n_lane ? gl : 0);
-    for (int q = 0; q < 5; ++q) sA[q * NCS + c] = inside ? p.ascale * p.lam[q * N + oa] : 0.0;
+    if constexpr (MIXED) {
+      for (int q = 0; q < 5; ++q) sA[q * NCS + c] = inside ? p.lamf[q * N + oa] : P(0);
+    } else {
+      for (int q = 0; q < 5; ++q) sA[q * NCS + c] = inside ? p.ascale * p.lam[q * N + oa] : P(0);
+    }
   }
   __syncthreads();
 
@@ -122,15 +159,23 @@ __global__ void __launch_bounds__(kAdjThreads) vjp_kernel(const VjpArgs p) {
     else { ii = it / LANES; lane = it - ii * LANES; }
     const int i = a0 - 4 + ii;
     const bool valid = i >= -1 && i <= n_along - 1 && l0 + lane < n_lane;
-    double al = 0.0;
-    for (int t = 0; t < 8; ++t) al = fmax(al, sR[sidx(lane, ii + 1 + t)]);
+    // rho >= 0: compared as bit patterns (integer pipe), which order like the values
+    using I = typename std::conditional<sizeof(P) == 8, long long, int>::type;
+    I alb = 0;
+    for (int t = 0; t < 8; ++t) {
+      const I rb = bits_of(sR[sidx(lane, ii + 1 + t)]);
+      alb = rb > alb ? rb : alb;
+    }
+    const P al = from_bits<P>(alb);
     unsigned mask = 0;
-    if (valid)
+    if (valid) {
+      const I thr = bits_of(al * (P(1) - kTie));
       for (int t = 0; t < 8; ++t)
-        if (sR[sidx(lane, ii + 1 + t)] >= al * (1.0 - 1e-12)) mask |= 1u << t;
+        if (bits_of(sR[sidx(lane, ii + 1 + t)]) >= thr) mask |= 1u << t;
+    }
     sAl[iidx(lane, ii)] = al;
     sTie[iidx(lane, ii)] = mask;
-    sAhb[iidx(lane, ii)] = 0.0;
+    sAhb[iidx(lane, ii)] = P(0);
   }
   __syncthreads();
 
@@ -141,33 +186,50 @@ __global__ void __launch_bounds__(kAdjThreads) vjp_kernel(const VjpArgs p) {
       if (DIR == 0) { lane = it / NI; ii = it - lane * NI; }
       else { ii = it / LANES; lane = it - ii * LANES; }
       const int x = iidx(lane, ii);
-      double* cf = cF + 8 * x;
-      double* cu = cU + 8 * x;
+      P* cf = cF + x;   // slot t at cf[t * NIF]: consecutive interfaces hit consecutive banks
+      P* cu = cU + x;
       if (sTie[x] == 0u) {
-        for (int t = 0; t < 8; ++t) { cf[t] = 0.0; cu[t] = 0.0; }
+#pragma unroll
+        for (int t = 0; t < 8; ++t) { cf[t * NIF] = P(0); cu[t * NIF] = P(0); }
         continue;
       }
-      const double ah = 0.5 * sAl[x];
-      double u[8], fh[8];
+      const P ah = P(0.5) * sAl[x];
+      P u[8], fh[8];
       for (int t = 0; t < 8; ++t) {
         u[t] = sU[q * NCS + sidx(lane, ii + 1 + t)];
         fh[t] = sF[q * NCS + sidx(lane, ii + 1 + t)];
       }
       // adjoint of Fhat_{i+1/2}: L_i holds -Fhat inv_dx, L_{i+1} holds +Fhat inv_dx
-      const double g = (sA[q * NCS + sidx(lane, ii + 5)] - sA[q * NCS + sidx(lane, ii + 4)]) * p.inv_dx;
-      double fp[7], fm[7], gp[7], gm[7];
-      for (int t = 0; t < 7; ++t) {
-        fp[t] = fh[t] + ah * u[t];
-        fm[t] = fh[7 - t] - ah * u[7 - t];   // mirrored: cells i+4 .. i-2
+      const P g = (sA[q * NCS + sidx(lane, ii + 5)] - sA[q * NCS + sidx(lane, ii + 4)]) * (P)p.inv_dx;
+      P gp[7], gm[7];
+      if constexpr (MIXED) {
+        // f+ and the mirrored f- (cells i+4 .. i-2) in the two lanes of packed FP32x2
+        float2 fpm[7], gb[7];
+        const float2 ahp = make_float2(ah, -ah);
+#pragma unroll
+        for (int t = 0; t < 7; ++t) fpm[t] = fma2(ahp, make_float2(u[t], u[7 - t]), make_float2(fh[t], fh[7 - t]));
+        weno7_vjp_pair(fpm, (float)p.eps_s, make_float2(g, g), gb);
+#pragma unroll
+        for (int t = 0; t < 7; ++t) {
+          gp[t] = gb[t].x;
+          gm[t] = gb[t].y;
+        }
+      } else {
+        P fp[7], fm[7];
+        for (int t = 0; t < 7; ++t) {
+          fp[t] = fh[t] + ah * u[t];
+          fm[t] = fh[7 - t] - ah * u[7 - t];   // mirrored: cells i+4 .. i-2
+        }
+        weno7_vjp<P>(fp, (P)p.eps_s, g, gp);
+        weno7_vjp<P>(fm, (P)p.eps_s, g, gm);
       }
-      weno7_vjp(fp, p.eps_s, g, gp);
-      weno7_vjp(fm, p.eps_s, g, gm);
-      double ahb = 0.0;
+      P ahb = P(0);
+#pragma unroll
       for (int t = 0; t < 8; ++t) {
-        const double bp = t <= 6 ? gp[t] : 0.0;
-        const double bm = t >= 1 ? gm[7 - t] : 0.0;
-        cf[t] = bp + bm;
-        cu[t] = ah * (bp - bm);
+        const P bp = t <= 6 ? gp[t] : P(0);
+        const P bm = t >= 1 ? gm[7 - t] : P(0);
+        cf[t * NIF] = bp + bm;
+        cu[t * NIF] = ah * (bp - bm);
         ahb += u[t] * (bp - bm);
       }
       sAhb[x] += ahb;
@@ -178,22 +240,24 @@ __global__ void __launch_bounds__(kAdjThreads) vjp_kernel(const VjpArgs p) {
       if (DIR == 0) { lane = c / SEG; j = c - lane * SEG; }
       else { j = c / LANES; lane = c - j * LANES; }
       const int gcell = a0 + j;
-      double fb = 0.0, ub = 0.0;
-      if (gcell < n_along) {
-        const bool interior = gcell >= 4 && gcell <= n_along - 5;
-        for (int ii = j; ii <= j + 7; ++ii) {
-          const int x = iidx(lane, ii);
-          if (interior) {
-            const int t = j + 7 - ii;   // stencil slot holding cell gcell
-            fb += cF[8 * x + t];
-            ub += cU[8 * x + t];
-          } else {
-            const int i = a0 - 4 + ii;
-            for (int t = 0; t < 8; ++t)
-              if (clampi(i - 3 + t, n_along) == gcell) {
-                fb += cF[8 * x + t];
-                ub += cU[8 * x + t];
-              }
+      P fb = P(0), ub = P(0);
+      // cell gcell is slot 7 - k of interface j + k; the edge cells also own the
+      // clamped ghost slots beyond them (interfaces outside the grid hold zeros)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int x = iidx(lane, j + k);
+        fb += cF[(7 - k) * NIF + x];
+        ub += cU[(7 - k) * NIF + x];
+      }
+      if (gcell == 0 || gcell == n_along - 1) {
+        for (int k = 0; k < 8; ++k) {
+          const int x = iidx(lane, j + k);
+          for (int t = 0; t < 8; ++t) {
+            const bool ghost = (gcell == 0 && t < 7 - k) || (gcell == n_along - 1 && t > 7 - k);
+            if (ghost) {
+              fb += cF[t * NIF + x];
+              ub += cU[t * NIF + x];
+            }
           }
         }
       }
@@ -210,30 +274,39 @@ __global__ void __launch_bounds__(kAdjThreads) vjp_kernel(const VjpArgs p) {
     else { j = c / LANES; lane = c - j * LANES; }
     const int gcell = a0 + j, gl = l0 + lane;
     if (gcell >= n_along || gl >= n_lane) continue;
-    double rhob = 0.0;
-    for (int ii = j; ii <= j + 7; ++ii) {
-      const int x = iidx(lane, ii);
+    // cell gcell is slot 7 - k of interface j + k (the edge cells also own the
+    // clamped ghost slots beyond them); each tying slot gets an equal share
+    P rhob = P(0);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int x = iidx(lane, j + k);
       const unsigned mask = sTie[x];
-      if (!mask) continue;
-      const double albar = 0.5 * sAhb[x] / (double)__popc(mask);
-      const int i = a0 - 4 + ii;
-      for (int t = 0; t < 8; ++t)
-        if ((mask >> t) & 1u)
-          if (clampi(i - 3 + t, n_along) == gcell) rhob += albar;
+      unsigned own = (mask >> (7 - k)) & 1u;
+      if (gcell == 0) own += __popc(mask & ((1u << (7 - k)) - 1u));
+      if (gcell == n_along - 1) own += __popc(mask >> (8 - k));
+      if (own) rhob += P(0.5) * (P)own * sAhb[x] / (P)__popc(mask);
     }
     const int sc = sidx(lane, j + 8);
-    const double E = sU[sc], Mx = sU[NCS + sc], My = sU[2 * NCS + sc], Mz = sU[3 * NCS + sc], R = sU[4 * NCS + sc];
-    double e, vx, vy, vz;
+    const size_t o = offset(gcell, gl);
+    const P Mx = sU[NCS + sc], My = sU[2 * NCS + sc], Mz = sU[3 * NCS + sc], R = sU[4 * NCS + sc];
+    P e, vx, vy, vz;
     int hit = 0;
-    cons_to_prim<MathD>(E, Mx, My, Mz, p.e_floor, e, vx, vy, vz, hit);
-    const double v[3] = {vx, vy, vz};
-    const double vd = v[DIR];
+    float Efs = 0.0f, om = 0.0f;
+    if constexpr (MIXED) {
+      Efs = p.sh[5 * N + o];
+      om = p.sh[6 * N + o];
+      cons_to_prim_om(Efs, Mx, My, Mz, om, e, vx, vy, vz, hit);
+    } else {
+      cons_to_prim<MathD>(sU[sc], Mx, My, Mz, p.e_floor, e, vx, vy, vz, hit);
+    }
+    const P v[3] = {vx, vy, vz};
+    const P vd = v[DIR];
     const int ci = cidx(lane, j);
     // F/2 adjoint -> F adjoint
-    double Fb[5];
-    for (int k = 0; k < 5; ++k) Fb[k] = 0.5 * sFb[k * NC + ci];
-    double Mb[3] = {0.0, 0.0, 0.0}, vb[3] = {0.0, 0.0, 0.0}, Rb = 0.0, pb = 0.0;
-    const double M[3] = {Mx, My, Mz};
+    P Fb[5];
+    for (int k = 0; k < 5; ++k) Fb[k] = P(0.5) * sFb[k * NC + ci];
+    P Mb[3] = {P(0), P(0), P(0)}, vb[3] = {P(0), P(0), P(0)}, Rb = P(0), pb = P(0);
+    const P M[3] = {Mx, My, Mz};
     Mb[DIR] += Fb[0];
     for (int k = 0; k < 3; ++k) {
       Mb[k] += Fb[1 + k] * vd;
@@ -242,76 +315,132 @@ __global__ void __launch_bounds__(kAdjThreads) vjp_kernel(const VjpArgs p) {
     pb += Fb[1 + DIR];
     Rb += Fb[4] * vd;
     vb[DIR] += Fb[4] * R;
-    double d_vd, d_v2;
-    spectral_radius_grad(vd, vx * vx + vy * vy + vz * vz, d_vd, d_v2);
+    P d_vd, d_v2;
+    spectral_radius_grad<Math>(vd, vx * vx + vy * vy + vz * vz, d_vd, d_v2);
     vb[DIR] += rhob * d_vd;
-    for (int k = 0; k < 3; ++k) vb[k] += rhob * d_v2 * 2.0 * v[k];
-    double Eb = sUb[ci];
-    double Mbx = sUb[NC + ci] + Mb[0], Mby = sUb[2 * NC + ci] + Mb[1], Mbz = sUb[3 * NC + ci] + Mb[2];
+    for (int k = 0; k < 3; ++k) vb[k] += rhob * d_v2 * P(2) * v[k];
+    P Eb = sUb[ci];
+    P Mbx = sUb[NC + ci] + Mb[0], Mby = sUb[2 * NC + ci] + Mb[1], Mbz = sUb[3 * NC + ci] + Mb[2];
     Rb += sUb[4 * NC + ci];
-    cons_to_prim_vjp(E, Mx, My, Mz, p.e_floor, pb * (1.0 / 3.0), vb[0], vb[1], vb[2], Eb, Mbx, Mby, Mbz);
-    if (FINAL) {
-      const int gx = DIR == 0 ? gcell : gl;
-      const int gy = DIR == 1 ? gcell : (DIR == 0 ? gl : fixed);
-      const int gz = DIR == 2 ? gcell : fixed;
+    if constexpr (MIXED)
+      cons_to_prim_vjp_om(Efs, Mx, My, Mz, om, pb * P(1.0 / 3.0), vb[0], vb[1], vb[2], Eb, Mbx, Mby, Mbz);
+    else
+      cons_to_prim_vjp(sU[sc], Mx, My, Mz, p.e_floor, pb * (1.0 / 3.0), vb[0], vb[1], vb[2], Eb, Mbx, Mby, Mbz);
+    const P out[5] = {Eb, Mbx, Mby, Mbz, Rb};
+    if (DIR == 0) {
+      for (int k = 0; k < 5; ++k) r_out[k * N + o] = out[k];
+    } else {
+      for (int k = 0; k < 5; ++k) r_out[k * N + o] += out[k];
+    }
+  }
+
+  // ---- z sweep: adjoint of the jet source (Eqs. 2-3) at the jet cells of this
+  // tile, one thread, after the cells' own contributions (global writes of the
+  // block are visible to it after the barrier)
+  if constexpr (FINAL) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
       for (int jn = 0; jn < p.jets.n; ++jn) {
         const int* cl = p.jets.cell[jn];
-        if (cl[0] != gx || cl[1] != gy || cl[2] != gz) continue;
-        // S0 = inv_vol (k_rad C T^3 l / hc^2 + k_coll C T^2 / hc), T = (e t4)^(1/4): S = (S0, n S0, 0)
+        if (cl[0] < 0 || cl[1] != fixed || cl[2] < a0 || cl[2] >= a0 + SEG || cl[2] >= n_along || cl[0] < l0 ||
+            cl[0] >= l0 + LANES)
+          continue;
+        const int j = cl[2] - a0, lane = cl[0] - l0;
+        const int sc = sidx(lane, j + 8);
+        const size_t o = offset(cl[2], cl[0]);
+        const double Ed = p.U[o], Mxd = p.U[N + o], Myd = p.U[2 * N + o], Mzd = p.U[3 * N + o];
+        // S0 = inv_vol (k_rad C T^3 l / hc^2 + k_coll C T^2 / hc), T = (e t4)^(1/4): S = (S0, n S0, 0).
+        // The source runs in FP64 in both precisions (FP64 recovery at the jet cell).
         const double aE = sA[sc], aMx = sA[NCS + sc], aMy = sA[2 * NCS + sc], aMz = sA[3 * NCS + sc];
         const double Sb = aE + p.jets.dir[jn][0] * aMx + p.jets.dir[jn][1] * aMy + p.jets.dir[jn][2] * aMz;
-        const double T = temperature(e, p.t4coef);
+        double es, vsx, vsy, vsz;
+        int hs = 0;
+        cons_to_prim<MathD>(Ed, Mxd, Myd, Mzd, p.e_floor, es, vsx, vsy, vsz, hs);
+        const double T = temperature(es, p.t4coef);
         const double l = p.jets.ell[jn];
-        p.kbar[0] += Sb * p.rad_per_k * T * T * T * l * p.inv_vol;
-        p.kbar[1] += Sb * p.coll_per_k * T * T * p.inv_vol;
-        if (e > 0.0 && T > 0.0) {
+        p.kbar[2 * jn] += Sb * p.rad_per_k * T * T * T * l * p.inv_vol;
+        p.kbar[2 * jn + 1] += Sb * p.coll_per_k * T * T * p.inv_vol;
+        if (es > 0.0 && T > 0.0) {
           const double dS_dT = (3.0 * p.k_rad * p.rad_per_k * T * T * l + 2.0 * p.k_coll * p.coll_per_k * T) * p.inv_vol;
-          const double dT_de = T / (4.0 * e);
-          cons_to_prim_vjp(E, Mx, My, Mz, p.e_floor, Sb * dS_dT * dT_de, 0.0, 0.0, 0.0, Eb, Mbx, Mby, Mbz);
+          const double dT_de = T / (4.0 * es);
+          double sE = 0.0, sMx = 0.0, sMy = 0.0, sMz = 0.0;
+          cons_to_prim_vjp(Ed, Mxd, Myd, Mzd, p.e_floor, Sb * dS_dT * dT_de, 0.0, 0.0, 0.0, sE, sMx, sMy, sMz);
+          r_out[o] += (P)sE;
+          r_out[N + o] += (P)sMx;
+          r_out[2 * N + o] += (P)sMy;
+          r_out[3 * N + o] += (P)sMz;
         }
       }
-    }
-    const size_t o = offset(gcell, gl);
-    const double out[5] = {Eb, Mbx, Mby, Mbz, Rb};
-    if (DIR == 0) {
-      for (int k = 0; k < 5; ++k) p.r[k * N + o] = out[k];
-    } else {
-      for (int k = 0; k < 5; ++k) p.r[k * N + o] += out[k];
     }
   }
 }
 
-template <int DIR>
+template <int PREC, int DIR>
 cudaError_t launch_vjp(const VjpArgs& p, cudaStream_t s) {
+  using P = typename AdjTypes<PREC>::P;
+  constexpr size_t smem = adj_smem<P>();
   dim3 grid;
   if (DIR == 0) grid = dim3((p.nx + kAdjSeg - 1) / kAdjSeg, (p.ny + kAdjLanes - 1) / kAdjLanes, p.nz);
   else if (DIR == 1) grid = dim3((p.nx + kAdjLanes - 1) / kAdjLanes, (p.ny + kAdjSeg - 1) / kAdjSeg, p.nz);
   else grid = dim3((p.nx + kAdjLanes - 1) / kAdjLanes, (p.nz + kAdjSeg - 1) / kAdjSeg, p.ny);
-  cudaError_t err = cudaFuncSetAttribute(vjp_kernel<DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjSmem);
+  auto kern = vjp_kernel<PREC, DIR>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  vjp_kernel<DIR><<<grid, kAdjThreads, kAdjSmem, s>>>(p);
+  kern<<<grid, adj_threads<PREC>(), smem, s>>>(p);
   return cudaGetLastError();
 }
 
-// Reverse of one stage combination Uout = ca U0 + cb (Uk + dt L(Uk)).
+// Reverse of one stage combination Uout = ca U0 + cb (Uk + dt L(Uk)), in FP64;
+// r is the adjoint of the right-hand side in the flux type.
 // mode 0 (stage 3): lamB = cb lamA + r;  lam0 = ca lamA
 // mode 1 (stage 2): lamA = cb lamB + r;  lam0 += ca lamB
 // mode 2 (stage 1): lam0 += lamA + r
+// Mixed precision: the adjoint the next reverse sweep reads (lamB, lamA, lam0
+// for modes 0, 1, 2) also goes to lamf, scaled by that sweep's fscale, in FP32.
+template <class R>
 __global__ void adj_combine_kernel(int mode, double ca, double cb, double* lamA, double* lamB, double* lam0,
-                                   const double* r, size_t n) {
+                                   const R* r, size_t n, float* lamf, double fscale) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double ri = (double)r[i];
+    double next;
     if (mode == 0) {
       const double la = lamA[i];
-      lamB[i] = cb * la + r[i];
+      next = cb * la + ri;
+      lamB[i] = next;
       lam0[i] = ca * la;
     } else if (mode == 1) {
       const double lb = lamB[i];
-      lamA[i] = cb * lb + r[i];
+      next = cb * lb + ri;
+      lamA[i] = next;
       lam0[i] += ca * lb;
     } else {
-      lam0[i] += lamA[i] + r[i];
+      next = lam0[i] + (lamA[i] + ri);
+      lam0[i] = next;
     }
+    if (lamf) lamf[i] = (float)(fscale * next);
   }
+}
+
+// Mixed precision: FP32 shadow of a stage state for the reverse sweeps, with
+// the floored E and om = 1 - |M|/E of the recovery (E^2 - |M|^2 in FP64).
+__global__ void shadow_kernel(const double* U, float* sh, size_t n, double e_floor) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double E = U[i], Mx = U[n + i], My = U[2 * n + i], Mz = U[3 * n + i];
+    float Efs, om;
+    mixed_om(E, Mx, My, Mz, e_floor, Efs, om);
+    sh[i] = (float)E;
+    sh[n + i] = (float)Mx;
+    sh[2 * n + i] = (float)My;
+    sh[3 * n + i] = (float)Mz;
+    sh[4 * n + i] = (float)U[4 * n + i];
+    sh[5 * n + i] = Efs;
+    sh[6 * n + i] = om;
+  }
+}
+
+__global__ void scale_to_float_kernel(const double* x, float* y, double scale, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = (float)(scale * x[i]);
 }
 
 struct ConeArgs {
@@ -389,6 +518,8 @@ struct hydro_adjoint {
   double* rhs = nullptr;
   std::vector<double*> stages;   // every x 2 stage states (U1, U2) of the segment
   double *lamA = nullptr, *lamB = nullptr, *lam0 = nullptr, *r = nullptr, *prim = nullptr;
+  float* sh = nullptr;           // mixed: FP32 shadow of the stage state under reverse [7][n]
+  float* lamf = nullptr;         // mixed: FP32 scaled adjoint input of the next reverse sweep [5][n]
   double* kbar = nullptr;        // [2]
   double* partial = nullptr;     // cone partial sums
   DevDiag* diag = nullptr;
@@ -396,6 +527,7 @@ struct hydro_adjoint {
   double jx0[kMaxJets][3], jn[kMaxJets][3], jt[kMaxJets];
   ConeArgs cone;
   bool forward_done = false;
+  bool last_kept = false;        // the forward left the last segment's states in seg / stages
   double J = 0.0;
 };
 
@@ -463,7 +595,7 @@ cudaError_t forward_step(hydro_adjoint* a, int64_t n, const double* in, double* 
     s.Uout = Uo[st];
     s.a = kA[st];
     s.b = kB[st];
-    for (int d = 0; d < 3 && err == cudaSuccess; ++d) err = launch_sweep(HYDRO_FP64, 7, d, s, a->stream);
+    for (int d = 0; d < 3 && err == cudaSuccess; ++d) err = launch_sweep(a->cfg.precision, 7, d, s, a->stream);
   }
   return err;
 }
@@ -490,10 +622,35 @@ cudaError_t vjp(hydro_adjoint* a, int64_t n, int st, const double* Uk, const dou
   p.t4coef = g.hbarc * g.hbarc * g.hbarc / (M_PI * M_PI / 30.0 * g.dof);
   p.inv_vol = 1.0 / (g.dx * g.dx * g.dx);
   jet_stage(a, g.t0 + ((double)n + kStageC[st]) * g.dt, p.jets);
-  cudaError_t err = launch_vjp<0>(p, a->stream);
-  if (err == cudaSuccess) err = launch_vjp<1>(p, a->stream);
-  if (err == cudaSuccess) err = launch_vjp<2>(p, a->stream);
+  cudaError_t err;
+  if (g.precision == HYDRO_MIXED) {
+    p.sh = a->sh;
+    p.lamf = a->lamf;
+    shadow_kernel<<<grid_1d(a->n), 256, 0, a->stream>>>(Uk, a->sh, a->n, g.e_floor);
+    err = cudaGetLastError();
+    if (err == cudaSuccess) err = launch_vjp<HYDRO_MIXED, 0>(p, a->stream);
+    if (err == cudaSuccess) err = launch_vjp<HYDRO_MIXED, 1>(p, a->stream);
+    if (err == cudaSuccess) err = launch_vjp<HYDRO_MIXED, 2>(p, a->stream);
+  } else {
+    err = launch_vjp<HYDRO_FP64, 0>(p, a->stream);
+    if (err == cudaSuccess) err = launch_vjp<HYDRO_FP64, 1>(p, a->stream);
+    if (err == cudaSuccess) err = launch_vjp<HYDRO_FP64, 2>(p, a->stream);
+  }
   return err;
+}
+
+// Reverse of the stage combination of stage st; the reverse sweep that follows
+// is stage st - 1 of the same step, or stage 3 of the previous step.
+cudaError_t combine(hydro_adjoint* a, int mode, int st) {
+  const size_t n5 = 5 * a->n;
+  const double fscale = kB[st == 0 ? 2 : st - 1] * a->cfg.dt;
+  if (a->cfg.precision == HYDRO_MIXED)
+    adj_combine_kernel<float><<<grid_1d(n5), 256, 0, a->stream>>>(
+        mode, kA[st], kB[st], a->lamA, a->lamB, a->lam0, reinterpret_cast<const float*>(a->r), n5, a->lamf, fscale);
+  else
+    adj_combine_kernel<double><<<grid_1d(n5), 256, 0, a->stream>>>(mode, kA[st], kB[st], a->lamA, a->lamB, a->lam0,
+                                                                   a->r, n5, nullptr, 0.0);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -505,7 +662,8 @@ hydro_status hydro_adjoint_create(const hydro_config* cfg, int32_t nsteps, int32
                                   hydro_adjoint** out) {
   if (!out) return HYDRO_EINVAL;
   *out = nullptr;
-  if (!cfg || cfg->precision != HYDRO_FP64 || cfg->boundary != HYDRO_OUTFLOW || cfg->weno_order != 7)
+  if (!cfg || (cfg->precision != HYDRO_FP64 && cfg->precision != HYDRO_MIXED) || cfg->boundary != HYDRO_OUTFLOW ||
+      cfg->weno_order != 7)
     return HYDRO_EINVAL;
   if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1 || nsteps < 1 || checkpoint_every < 1 || !apex || !axis)
     return HYDRO_EINVAL;
@@ -534,7 +692,9 @@ hydro_status hydro_adjoint_create(const hydro_config* cfg, int32_t nsteps, int32
   // buffers: checkpoints, the segment's step states and stage states, adjoints, scratch
   const size_t f5 = 5 * a->n * sizeof(double);
   const size_t nbuf = (size_t)a->nckpt + (size_t)(a->every + 1) + 2 * (size_t)a->every + 1 + 4 + 1;
-  const size_t bytes = nbuf * f5 + a->n * sizeof(double) + 64 + kConeBlocks * sizeof(double) + sizeof(DevDiag) + 4096;
+  const size_t shadow = cfg->precision == HYDRO_MIXED ? 12 * a->n * sizeof(float) + 512 : 0;
+  const size_t bytes = nbuf * f5 + a->n * sizeof(double) + 2 * kMaxJets * sizeof(double) +
+                       kConeBlocks * sizeof(double) + sizeof(DevDiag) + shadow + 4096;
   if (cudaMalloc(&a->ws, bytes) != cudaSuccess) {
     cudaGetLastError();
     delete a;
@@ -555,7 +715,11 @@ hydro_status hydro_adjoint_create(const hydro_config* cfg, int32_t nsteps, int32
   a->lam0 = reinterpret_cast<double*>(take(f5));
   a->r = reinterpret_cast<double*>(take(f5));
   a->prim = reinterpret_cast<double*>(take(f5));
-  a->kbar = reinterpret_cast<double*>(take(64));
+  if (cfg->precision == HYDRO_MIXED) {
+    a->sh = reinterpret_cast<float*>(take(7 * a->n * sizeof(float)));
+    a->lamf = reinterpret_cast<float*>(take(5 * a->n * sizeof(float)));
+  }
+  a->kbar = reinterpret_cast<double*>(take(2 * kMaxJets * sizeof(double)));
   a->partial = reinterpret_cast<double*>(take(kConeBlocks * sizeof(double)));
   a->diag = reinterpret_cast<DevDiag*>(take(sizeof(DevDiag)));
   *out = a;
@@ -589,10 +753,20 @@ hydro_status hydro_adjoint_forward(hydro_adjoint* a, const double* d_prim5, doub
   cudaError_t err = cudaMemcpyAsync(a->prim, d_prim5, f5, cudaMemcpyDeviceToDevice, a->stream);
   if (err == cudaSuccess) err = cudaMemsetAsync(a->diag, 0, sizeof(DevDiag), a->stream);
   if (err == cudaSuccess) err = launch_init(HYDRO_FP64, HYDRO_PRIMITIVE, a->prim, a->ckpt[0], a->n, a->diag, a->stream);
-  // march, keeping a checkpoint every `every` steps; other states ping-pong in seg[0], seg[1]
+  // march, keeping a checkpoint every `every` steps; other states ping-pong in
+  // seg[0], seg[1].  The last segment keeps its step and stage states where the
+  // reverse sweep expects them, so that the reverse sweep need not replay it.
+  const int s_last = (a->nckpt - 1) * a->every;
   const double* cur = a->ckpt[0];
   int pp = 0;
   for (int s = 0; s < a->nsteps && err == cudaSuccess; ++s) {
+    if (s >= s_last) {
+      const int i = s - s_last;
+      if (i == 0) err = cudaMemcpyAsync(a->seg[0], cur, 5 * a->n * sizeof(double), cudaMemcpyDeviceToDevice, a->stream);
+      if (err == cudaSuccess) err = forward_step(a, s, a->seg[i], a->stages[2 * i], a->stages[2 * i + 1], a->seg[i + 1]);
+      cur = a->seg[i + 1];
+      continue;
+    }
     const int k = (s + 1) / a->every;
     double* next;
     if ((s + 1) % a->every == 0 && k < a->nckpt) {
@@ -620,6 +794,7 @@ hydro_status hydro_adjoint_forward(hydro_adjoint* a, const double* d_prim5, doub
   a->J = sum;
   *J = sum;
   a->forward_done = true;
+  a->last_kept = true;
   return HYDRO_OK;
 }
 
@@ -627,11 +802,14 @@ hydro_status hydro_adjoint_backward(hydro_adjoint* a, double dJ, double* grad_k_
                                     double* d_grad_e) {
   if (!a || !d_grad_e) return HYDRO_EINVAL;
   if (!a->forward_done) return HYDRO_ESTATE;
-  cudaError_t err = cudaMemsetAsync(a->kbar, 0, 2 * sizeof(double), a->stream);
-  const unsigned g1 = grid_1d(5 * a->n);
+  cudaError_t err = cudaMemsetAsync(a->kbar, 0, 2 * kMaxJets * sizeof(double), a->stream);
   if (err == cudaSuccess) {
     cone_seed_kernel<<<grid_1d(a->n), 256, 0, a->stream>>>(a->lamA, a->cone, dJ);
     err = cudaGetLastError();
+    if (err == cudaSuccess && a->lamf) {
+      scale_to_float_kernel<<<grid_1d(5 * a->n), 256, 0, a->stream>>>(a->lamA, a->lamf, kB[2] * a->cfg.dt, 5 * a->n);
+      err = cudaGetLastError();
+    }
   }
   // segments in reverse: recompute the step states of the segment from its
   // checkpoint, then walk its steps backwards
@@ -639,30 +817,24 @@ hydro_status hydro_adjoint_backward(hydro_adjoint* a, double dJ, double* grad_k_
     const int s0 = k * a->every;
     const int s1 = std::min(a->nsteps, s0 + a->every);
     const int len = s1 - s0;
-    err = cudaMemcpyAsync(a->seg[0], a->ckpt[k], 5 * a->n * sizeof(double), cudaMemcpyDeviceToDevice, a->stream);
-    for (int s = 0; s < len && err == cudaSuccess; ++s)
-      err = forward_step(a, s0 + s, a->seg[s], a->stages[2 * s], a->stages[2 * s + 1], a->seg[s + 1]);
+    if (!(k == a->nckpt - 1 && a->last_kept)) {
+      err = cudaMemcpyAsync(a->seg[0], a->ckpt[k], 5 * a->n * sizeof(double), cudaMemcpyDeviceToDevice, a->stream);
+      for (int s = 0; s < len && err == cudaSuccess; ++s)
+        err = forward_step(a, s0 + s, a->seg[s], a->stages[2 * s], a->stages[2 * s + 1], a->seg[s + 1]);
+    }
+    a->last_kept = false;   // the replays below overwrite the segment buffers
     for (int s = len - 1; s >= 0 && err == cudaSuccess; --s) {
       const int64_t n = s0 + s;
       const double* Us[3] = {a->seg[s], a->stages[2 * s], a->stages[2 * s + 1]};
       // stage 3: U = 1/3 U0 + 2/3 (U2 + dt L(U2))
       err = vjp(a, n, 2, Us[2], a->lamA, kB[2] * a->cfg.dt);
-      if (err == cudaSuccess) {
-        adj_combine_kernel<<<g1, 256, 0, a->stream>>>(0, kA[2], kB[2], a->lamA, a->lamB, a->lam0, a->r, 5 * a->n);
-        err = cudaGetLastError();
-      }
+      if (err == cudaSuccess) err = combine(a, 0, 2);
       // stage 2: U2 = 3/4 U0 + 1/4 (U1 + dt L(U1))
       if (err == cudaSuccess) err = vjp(a, n, 1, Us[1], a->lamB, kB[1] * a->cfg.dt);
-      if (err == cudaSuccess) {
-        adj_combine_kernel<<<g1, 256, 0, a->stream>>>(1, kA[1], kB[1], a->lamA, a->lamB, a->lam0, a->r, 5 * a->n);
-        err = cudaGetLastError();
-      }
+      if (err == cudaSuccess) err = combine(a, 1, 1);
       // stage 1: U1 = U0 + dt L(U0)
       if (err == cudaSuccess) err = vjp(a, n, 0, Us[0], a->lamA, kB[0] * a->cfg.dt);
-      if (err == cudaSuccess) {
-        adj_combine_kernel<<<g1, 256, 0, a->stream>>>(2, kA[0], kB[0], a->lamA, a->lamB, a->lam0, a->r, 5 * a->n);
-        err = cudaGetLastError();
-      }
+      if (err == cudaSuccess) err = combine(a, 2, 0);
       std::swap(a->lamA, a->lam0);   // adjoint of the step's input becomes the next output adjoint
     }
   }
@@ -670,12 +842,17 @@ hydro_status hydro_adjoint_backward(hydro_adjoint* a, double dJ, double* grad_k_
     grad_e_kernel<<<grid_1d(a->n), 256, 0, a->stream>>>(a->prim, a->lamA, d_grad_e, a->n);
     err = cudaGetLastError();
   }
-  double kb[2] = {0.0, 0.0};
+  double kb[2 * kMaxJets];
   if (err == cudaSuccess) err = cudaMemcpyAsync(kb, a->kbar, sizeof(kb), cudaMemcpyDeviceToHost, a->stream);
   if (err == cudaSuccess) err = cudaStreamSynchronize(a->stream);
   if (err != cudaSuccess) return HYDRO_ECUDA;
-  if (grad_k_rad) *grad_k_rad = kb[0];
-  if (grad_k_coll) *grad_k_coll = kb[1];
+  double gr = 0.0, gc = 0.0;
+  for (int j = 0; j < a->njet; ++j) {
+    gr += kb[2 * j];
+    gc += kb[2 * j + 1];
+  }
+  if (grad_k_rad) *grad_k_rad = gr;
+  if (grad_k_coll) *grad_k_coll = gc;
   return HYDRO_OK;
 }
 

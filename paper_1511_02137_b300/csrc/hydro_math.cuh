@@ -76,18 +76,27 @@ __device__ __forceinline__ void cons_to_prim(typename M::T E, typename M::T Mx, 
 // FP32 accuracy, and runs in FP32:
 //   4 - 3m^2 = 1 + 3 om (2 - om),  1 - v = 3 om (1 + (2 - om)/(s + 1)) / (2 + s),
 //   1 - m v = (1 - v) + v om,  with s = sqrt(4 - 3m^2).
-__device__ __forceinline__ void cons_to_prim_mixed(double E, double Mx, double My, double Mz, double e_floor,
-                                                   float& e, float& vx, float& vy, float& vz, int& hit) {
+// Split in two: mixed_om forms the floored E (as FP32, negated when the floor
+// acted) and om; cons_to_prim_om recovers the primitives from them in FP32.
+__device__ __forceinline__ void mixed_om(double E, double Mx, double My, double Mz, double e_floor, float& Ef_signed,
+                                         float& om) {
   double Ee = E;
-  if (!(Ee >= e_floor)) {
-    Ee = e_floor;
-    hit = 1;
-  }
+  const bool floored = !(Ee >= e_floor);
+  if (floored) Ee = e_floor;
   const double D = Ee * Ee - (Mx * Mx + My * My + Mz * Mz);
   const float Ef = (float)Ee, mx = (float)Mx, my = (float)My, mz = (float)Mz;
   const float Mabs = sqrt_approx(mx * mx + my * my + mz * mz);
+  om = (float)D * rcp_approx(Ef * (Ef + Mabs));
+  Ef_signed = floored ? -Ef : Ef;
+}
+
+__device__ __forceinline__ void cons_to_prim_om(float Ef_signed, float mx, float my, float mz, float om_in, float& e,
+                                                float& vx, float& vy, float& vz, int& hit) {
+  if (Ef_signed < 0.0f) hit = 1;
+  const float Ef = fabsf(Ef_signed);
+  const float Mabs = sqrt_approx(mx * mx + my * my + mz * mz);
   const float invE = rcp_approx(Ef);
-  float om = (float)D * rcp_approx(Ef * (Ef + Mabs));
+  float om = om_in;
   const float om_min = (float)(1.0 - MathD::m_max);
   float m_over_M = invE;   // m / |M|
   if (!(om >= om_min)) {
@@ -104,6 +113,13 @@ __device__ __forceinline__ void cons_to_prim_mixed(double E, double Mx, double M
   vx = mx * vs;
   vy = my * vs;
   vz = mz * vs;
+}
+
+__device__ __forceinline__ void cons_to_prim_mixed(double E, double Mx, double My, double Mz, double e_floor,
+                                                   float& e, float& vx, float& vy, float& vz, int& hit) {
+  float Ef_signed, om;
+  mixed_om(E, Mx, My, Mz, e_floor, Ef_signed, om);
+  cons_to_prim_om(Ef_signed, (float)Mx, (float)My, (float)Mz, om, e, vx, vy, vz, hit);
 }
 
 // Spectral radius of the flux Jacobian along an axis: max |lambda_pm| with

@@ -117,3 +117,28 @@ def test_ensemble_recipe():
         for j in w.jets:
             assert sum(x * x for x in j.x0) ** 0.5 < 0.4 * half + 1e-12
     assert {w.n[0] for w in E.events} == {64, 96, 128, 160}
+
+
+@pytest.mark.parametrize("field,value", [("precision", 1), ("boundary", 1), ("weno_order", 5), ("nx", 0),
+                                         ("weno_eps", 0.0)])
+def test_adjoint_rejects_unsupported_configurations_before_allocating(hy, field, value):
+    """The adjoint runs FP64 or mixed, outflow, WENO7: anything else is EINVAL
+    before any device allocation (precision 1 is FP32)."""
+    c = hy.hydro_config_default(16, 16, 16)
+    setattr(c, field, value)
+    h = ctypes.c_void_p()
+    d3 = ctypes.c_double * 3
+    rc = hy._lib().hydro_adjoint_create(ctypes.byref(c), 4, 2, d3(0, 0, 0), d3(1, 0, 0), 30.0, 3.0, ctypes.byref(h))
+    assert rc == hy.HYDRO_EINVAL and not h.value
+
+
+@pytest.mark.parametrize("nsteps,every,axis,angle,rmax", [(0, 1, (1, 0, 0), 30.0, 3.0), (4, 0, (1, 0, 0), 30.0, 3.0),
+                                                           (4, 2, (0, 0, 0), 30.0, 3.0), (4, 2, (1, 0, 0), 0.0, 3.0),
+                                                           (4, 2, (1, 0, 0), 30.0, -1.0)])
+def test_adjoint_rejects_invalid_runs_and_cones(hy, nsteps, every, axis, angle, rmax):
+    c = hy.hydro_config_default(16, 16, 16, precision="mixed")
+    h = ctypes.c_void_p()
+    d3 = ctypes.c_double * 3
+    rc = hy._lib().hydro_adjoint_create(ctypes.byref(c), nsteps, every, d3(0, 0, 0), d3(*axis), angle, rmax,
+                                        ctypes.byref(h))
+    assert rc == hy.HYDRO_EINVAL and not h.value
