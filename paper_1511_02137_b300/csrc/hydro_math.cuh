@@ -165,9 +165,10 @@ constexpr double kW7B = 0.999359590072005;     // sqrt(780/781)
 // (beta' = 720/781 beta, eps_s = 720/781 eps; the common factor leaves the
 // weights unchanged): eps_s enters the innermost FMA of each indicator and the
 // scaled a_k = kA A_k, b_k = kB B_k serve both the indicators and z_k.
+// From the first differences d1[j] = f_{j+1} - f_j of the stencil values.
 template <class F>
-__device__ __forceinline__ void weno7_terms(F f0, F f1, F f2, F f3, F f4, F f5, F f6, F eps_s, F z[4], F s[4]) {
-  const F d10 = f1 - f0, d11 = f2 - f1, d12 = f3 - f2, d13 = f4 - f3, d14 = f5 - f4, d15 = f6 - f5;
+__device__ __forceinline__ void weno7_terms_d1(const F d1[6], F eps_s, F z[4], F s[4]) {
+  const F d10 = d1[0], d11 = d1[1], d12 = d1[2], d13 = d1[3], d14 = d1[4], d15 = d1[5];
   const F d20 = d11 - d10, d21 = d12 - d11, d22 = d13 - d12, d23 = d14 - d13, d24 = d15 - d14;
   const F c0 = d21 - d20, c1 = d22 - d21, c2 = d23 - d22, c3 = d24 - d23;
   const F e0 = c1 - c0, e1 = c2 - c1, e2 = c3 - c2;
@@ -187,6 +188,12 @@ __device__ __forceinline__ void weno7_terms(F f0, F f1, F f2, F f3, F f4, F f5, 
   s[1] = a1 * a1 + (c1 * c1 + m12);
   s[2] = a2 * a2 + (c2 * c2 + m12);
   s[3] = a3 * a3 + (b3 * b3 + (c3 * c3 + eps_s));
+}
+
+template <class F>
+__device__ __forceinline__ void weno7_terms(F f0, F f1, F f2, F f3, F f4, F f5, F f6, F eps_s, F z[4], F s[4]) {
+  const F d1[6] = {f1 - f0, f2 - f1, f3 - f2, f4 - f3, f5 - f4, f6 - f5};
+  weno7_terms_d1(d1, eps_s, z, s);
 }
 
 // FP64 weights in product form, t_k ~ prod_{j != k} s_j^2: the correction is
@@ -236,6 +243,20 @@ __device__ __forceinline__ double weno7_sum(const double g[7], const double h[7]
   weno7_numden(zg, sg, ng, dg);
   weno7_numden(zh, sh, nh, dh);
   return (g[3] + h[3]) + (ng * dh + nh * dg) / (dg * dh);
+}
+
+// weno7_sum from first differences: g3 and dg[6] describe f+ (g3 = f+_i),
+// h3 and dh[6] the negated mirrored f- (h3 = -f-_{i+1}); the reconstruction of
+// a negated stencil is the negated reconstruction, so the sum of the two
+// reconstructions is g3 - h3 + (ng dh - nh dg)/(dg dh).
+__device__ __forceinline__ double weno7_sum_d1(double g3, const double dg[6], double h3, const double dh[6],
+                                               double eps_s) {
+  double zg[4], sg[4], zh[4], sh[4], ng, qg, nh, qh;
+  weno7_terms_d1(dg, eps_s, zg, sg);
+  weno7_terms_d1(dh, eps_s, zh, sh);
+  weno7_numden(zg, sg, ng, qg);
+  weno7_numden(zh, sh, nh, qh);
+  return (g3 - h3) + (ng * qh - nh * qg) / (qg * qh);
 }
 
 // ---- FP32 pair form: two reconstructions that run the same operation

@@ -165,8 +165,9 @@ __host__ __device__ constexpr int tile_smem_words() {
   using F = typename Types<PREC>::Flux;
   using Store = typename Types<PREC>::Store;
   constexpr int G = (ORDER == 7) ? 4 : 3, NCS = LANES * (SEG + 2 * G), NIF = LANES * (SEG + 1), NC = LANES * SEG;
+  constexpr int delta = (sizeof(F) == 8 && ORDER == 7) ? 10 * NCS : 0;   // FP64 WENO7: neighbour differences
   return 11 * NCS + 5 * NIF + Prefetch<PREC, DIR>::rhs * NC +
-         Prefetch<PREC, DIR>::state * NC * (int)(sizeof(Store) / sizeof(F));
+         Prefetch<PREC, DIR>::state * NC * (int)(sizeof(Store) / sizeof(F)) + delta;
 }
 
 // One tile of a sweep: SEG cells along the sweep axis starting at a0, LANES
@@ -304,6 +305,28 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   if (a.reduce_speed || a.count_floors) publish_block(vmax, hits, a.diag, a.reduce_speed, a.count_floors);
   __syncthreads();
 
+  // FP64 WENO7: differences of U and F/2 between neighbouring staged cells, once
+  // per cell pair; each interface then forms its split-flux differences with one
+  // FMA apiece instead of splitting 8 cells and differencing per interface.
+  constexpr bool DELTA = sizeof(F) == 8 && ORDER == 7;
+  F* sDU = sH + 5 * NIF + PF::rhs * NC + PF::state * NC * (int)(sizeof(Store) / sizeof(F));   // [5][NCS] U(c+1) - U(c)
+  F* sDF = sDU + 5 * NCS;                                                                     // [5][NCS] F(c+1) - F(c)
+  if constexpr (DELTA) {
+    for (int c = threadIdx.x; c < NCS; c += kThreads) {
+      int lane, s;
+      if (DIR == 0) { lane = c / W; s = c - lane * W; }
+      else { s = c / LANES; lane = c - s * LANES; }
+      if (s + 1 >= W) continue;
+      const int cn = sidx(lane, s + 1);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        sDU[q * NCS + c] = sU[q * NCS + cn] - sU[q * NCS + c];
+        sDF[q * NCS + c] = sF[q * NCS + cn] - sF[q * NCS + c];
+      }
+    }
+    __syncthreads();
+  }
+
   // ---------------- phase 2: numerical flux at every interface of the tile
   const F eps = (ORDER == 7) ? (F)(kW7EpsScale * a.eps) : (F)(kW5EpsScale * a.eps);
   // numerical flux of components q0 .. q1-1 at the interface left of tile cell j
@@ -331,14 +354,15 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
         const float2 hh = weno7_pair(g[0], g[1], g[2], g[3], g[4], g[5], g[6], eps);
         h = hh.x + hh.y;
       } else if constexpr (ORDER == 7) {
-        // FP64: f+ from cells i-3..i+3 and f- mirrored from cells i+4..i-2, one division for both
-        F gp[7], gm[7];
+        // FP64: f+ from cells i-3..i+3 and the negated mirrored f- from cells i+4..i-2,
+        // their differences from the neighbour differences; one division for both
+        F dp[6], dm[6];
 #pragma unroll
-        for (int k = 0; k < 7; ++k) {
-          gp[k] = fma(ah, u[k], f[k]);
-          gm[k] = fma(-ah, u[7 - k], f[7 - k]);
+        for (int k = 0; k < 6; ++k) {
+          dp[k] = fma(ah, sDU[q * NCS + sidx(lane, j + k)], sDF[q * NCS + sidx(lane, j + k)]);
+          dm[k] = fma(-ah, sDU[q * NCS + sidx(lane, j + 6 - k)], sDF[q * NCS + sidx(lane, j + 6 - k)]);
         }
-        h = weno7_sum(gp, gm, eps);
+        h = weno7_sum_d1(fma(ah, u[3], f[3]), dp, fma(ah, u[4], -f[4]), dm, eps);
       } else {
         h = weno5<F>(fma(ah, u[0], f[0]), fma(ah, u[1], f[1]), fma(ah, u[2], f[2]), fma(ah, u[3], f[3]),
                      fma(ah, u[4], f[4]), eps) +
