@@ -32,21 +32,29 @@ namespace hydro {
 
 namespace {
 
-// Threads per tile: FP64 tiles are bound by the FP64 pipe and keep 256 (two
-// blocks per SM at ~120 registers); FP32-flux (mixed) tiles take one thread
-// per interface of the tile (kAdjNIF = 288), so that each component's reverse
-// WENO pass is a single round.
-template <int PREC> __host__ __device__ constexpr int adj_threads() { return PREC == HYDRO_MIXED ? 288 : 256; }
-constexpr int kAdjSeg = 64;     // cells per line along the sweep axis
-constexpr int kAdjLanes = 4;    // lines per tile
-constexpr int kAdjW = kAdjSeg + 16;              // staged positions per line: a0-8 .. a0+SEG+7
-constexpr int kAdjNCS = kAdjLanes * kAdjW;
-constexpr int kAdjNI = kAdjSeg + 8;              // interfaces i = a0-4 .. a0+SEG+3
-constexpr int kAdjNIF = kAdjLanes * kAdjNI;
-constexpr int kAdjNC = kAdjLanes * kAdjSeg;
-template <class P>
+// Tile geometry of the reverse sweeps: SEG cells per line along the sweep axis,
+// LANES lines, 8 staged cells of halo on each side and SEG + 8 interfaces per
+// line.  FP64 tiles are bound by the FP64 pipe: long lines recompute fewer halo
+// interfaces (136 per 128 cells), 256 threads, two blocks per SM at ~120
+// registers.  FP32-flux (mixed) tiles are 64 x 4 with one thread per interface
+// (288), so that each component's reverse WENO pass is a single round.
+template <int PREC>
+struct AdjTile {
+  static constexpr int SEG = PREC == HYDRO_MIXED ? 64 : 128;
+  static constexpr int LANES = PREC == HYDRO_MIXED ? 4 : 2;
+  static constexpr int W = SEG + 16;       // staged positions per line: a0-8 .. a0+SEG+7
+  static constexpr int NCS = LANES * W;
+  static constexpr int NI = SEG + 8;       // interfaces i = a0-4 .. a0+SEG+3
+  static constexpr int NIF = LANES * NI;
+  static constexpr int NC = LANES * SEG;
+  static constexpr int THREADS = PREC == HYDRO_MIXED ? NIF : 256;
+};
+template <int PREC> __host__ __device__ constexpr int adj_threads() { return AdjTile<PREC>::THREADS; }
+
+template <int PREC, class P>
 constexpr size_t adj_smem() {
-  return sizeof(P) * (size_t)(16 * kAdjNCS + 16 * kAdjNIF + 2 * kAdjNIF + 10 * kAdjNC) + sizeof(unsigned) * kAdjNIF;
+  using T = AdjTile<PREC>;
+  return sizeof(P) * (size_t)(16 * T::NCS + 16 * T::NIF + 2 * T::NIF + 10 * T::NC) + sizeof(unsigned) * T::NIF;
 }
 
 // Flux arithmetic of the adjoint sweeps: the forward's (FP64, or FP32 for mixed).
@@ -80,8 +88,8 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
   using P = typename AdjTypes<PREC>::P;
   using Math = typename AdjTypes<PREC>::Math;
   constexpr bool MIXED = PREC == HYDRO_MIXED;
-  constexpr int SEG = kAdjSeg, LANES = kAdjLanes, W = kAdjW, NCS = kAdjNCS, NI = kAdjNI, NIF = kAdjNIF,
-                NC = kAdjNC;
+  using T = AdjTile<PREC>;
+  constexpr int SEG = T::SEG, LANES = T::LANES, W = T::W, NCS = T::NCS, NI = T::NI, NIF = T::NIF, NC = T::NC;
   constexpr bool FINAL = DIR == 2;
   // cells whose alpha lies within this relative distance of the maximum share its derivative
   constexpr P kTie = MIXED ? P(1e-6) : P(1e-12);
@@ -290,15 +298,9 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
     const size_t o = offset(gcell, gl);
     const P Mx = sU[NCS + sc], My = sU[2 * NCS + sc], Mz = sU[3 * NCS + sc], R = sU[4 * NCS + sc];
     P e, vx, vy, vz;
-    int hit = 0;
-    float Efs = 0.0f, om = 0.0f;
-    if constexpr (MIXED) {
-      Efs = p.sh[5 * N + o];
-      om = p.sh[6 * N + o];
-      cons_to_prim_om(Efs, Mx, My, Mz, om, e, vx, vy, vz, hit);
-    } else {
-      cons_to_prim<MathD>(sU[sc], Mx, My, Mz, p.e_floor, e, vx, vy, vz, hit);
-    }
+    C2PTape<P> tape;
+    if constexpr (MIXED) cons_to_prim_om_tape(p.sh[5 * N + o], Mx, My, Mz, p.sh[6 * N + o], tape, e, vx, vy, vz);
+    else cons_to_prim_tape(sU[sc], Mx, My, Mz, p.e_floor, tape, e, vx, vy, vz);
     const P v[3] = {vx, vy, vz};
     const P vd = v[DIR];
     const int ci = cidx(lane, j);
@@ -322,10 +324,8 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
     P Eb = sUb[ci];
     P Mbx = sUb[NC + ci] + Mb[0], Mby = sUb[2 * NC + ci] + Mb[1], Mbz = sUb[3 * NC + ci] + Mb[2];
     Rb += sUb[4 * NC + ci];
-    if constexpr (MIXED)
-      cons_to_prim_vjp_om(Efs, Mx, My, Mz, om, pb * P(1.0 / 3.0), vb[0], vb[1], vb[2], Eb, Mbx, Mby, Mbz);
-    else
-      cons_to_prim_vjp(sU[sc], Mx, My, Mz, p.e_floor, pb * (1.0 / 3.0), vb[0], vb[1], vb[2], Eb, Mbx, Mby, Mbz);
+    c2p_vjp_core<Math>(tape.m, tape.s, tape.r, tape.v, tape.vs, tape.invE, tape.nx, tape.ny, tape.nz, tape.capped,
+                       tape.floored, pb * P(1.0 / 3.0), vb[0], vb[1], vb[2], Eb, Mbx, Mby, Mbz);
     const P out[5] = {Eb, Mbx, Mby, Mbz, Rb};
     if (DIR == 0) {
       for (int k = 0; k < 5; ++k) r_out[k * N + o] = out[k];
@@ -378,11 +378,12 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
 template <int PREC, int DIR>
 cudaError_t launch_vjp(const VjpArgs& p, cudaStream_t s) {
   using P = typename AdjTypes<PREC>::P;
-  constexpr size_t smem = adj_smem<P>();
+  constexpr size_t smem = adj_smem<PREC, P>();
+  constexpr int SEG = AdjTile<PREC>::SEG, LANES = AdjTile<PREC>::LANES;
   dim3 grid;
-  if (DIR == 0) grid = dim3((p.nx + kAdjSeg - 1) / kAdjSeg, (p.ny + kAdjLanes - 1) / kAdjLanes, p.nz);
-  else if (DIR == 1) grid = dim3((p.nx + kAdjLanes - 1) / kAdjLanes, (p.ny + kAdjSeg - 1) / kAdjSeg, p.nz);
-  else grid = dim3((p.nx + kAdjLanes - 1) / kAdjLanes, (p.nz + kAdjSeg - 1) / kAdjSeg, p.ny);
+  if (DIR == 0) grid = dim3((p.nx + SEG - 1) / SEG, (p.ny + LANES - 1) / LANES, p.nz);
+  else if (DIR == 1) grid = dim3((p.nx + LANES - 1) / LANES, (p.ny + SEG - 1) / SEG, p.nz);
+  else grid = dim3((p.nx + LANES - 1) / LANES, (p.nz + SEG - 1) / SEG, p.ny);
   auto kern = vjp_kernel<PREC, DIR>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;

@@ -76,38 +76,81 @@ __device__ __forceinline__ void cons_to_prim_vjp(double E, double Mx, double My,
                       Mbz);
 }
 
-// Mixed-precision recovery adjoint (the recovery of cons_to_prim_om): the
-// intermediate values come from the floored E (negative when the floor acted)
-// and om = 1 - m = (E^2 - |M|^2)/(E (E + |M|)) of mixed_om, whose E^2 - |M|^2
-// is FP64; the derivative arithmetic is FP32.
-__device__ __forceinline__ void cons_to_prim_vjp_om(float Ef_signed, float mx, float my, float mz, float om_in,
-                                                    float ebar, float vbx, float vby, float vbz, float& Ebar,
-                                                    float& Mbx, float& Mby, float& Mbz) {
-  const bool e_floored = Ef_signed < 0.0f;
+// Intermediate values of the closed-form recovery, kept for its adjoint.
+template <class P>
+struct C2PTape {
+  P m, s, r, v, vs, invE, nx, ny, nz;
+  bool capped, floored;
+};
+
+// FP64 recovery (the arithmetic of cons_to_prim<MathD>) keeping its intermediates.
+__device__ __forceinline__ void cons_to_prim_tape(double E, double Mx, double My, double Mz, double e_floor,
+                                                  C2PTape<double>& t, double& e, double& vx, double& vy,
+                                                  double& vz) {
+  const double Mabs = sqrt(Mx * Mx + My * My + Mz * Mz);
+  double Ee = E;
+  t.floored = !(Ee >= e_floor);
+  if (t.floored) Ee = e_floor;
+  t.invE = 1.0 / Ee;
+  double m = Mabs * t.invE;
+  double m_over_M = t.invE;
+  t.capped = !(m <= MathD::m_max);
+  if (t.capped) {
+    m = MathD::m_max;
+    m_over_M = m / Mabs;
+  }
+  t.m = m;
+  t.s = sqrt(4.0 - 3.0 * m * m);
+  t.r = 1.0 / (2.0 + t.s);
+  t.v = 3.0 * m * t.r;
+  e = Ee * (1.0 - m * t.v);
+  t.vs = 3.0 * m_over_M * t.r;
+  vx = Mx * t.vs;
+  vy = My * t.vs;
+  vz = Mz * t.vs;
+  t.nx = t.ny = t.nz = 0.0;
+  if (Mabs > 0.0) {
+    const double im = 1.0 / Mabs;
+    t.nx = Mx * im;
+    t.ny = My * im;
+    t.nz = Mz * im;
+  }
+}
+
+// Mixed recovery from the floored E and om (the arithmetic of cons_to_prim_om)
+// keeping its intermediates.
+__device__ __forceinline__ void cons_to_prim_om_tape(float Ef_signed, float mx, float my, float mz, float om_in,
+                                                     C2PTape<float>& t, float& e, float& vx, float& vy,
+                                                     float& vz) {
+  t.floored = Ef_signed < 0.0f;
   const float Ef = fabsf(Ef_signed);
   const float Mabs = sqrt_approx(mx * mx + my * my + mz * mz);
-  const float invE = rcp_approx(Ef);
+  t.invE = rcp_approx(Ef);
   float om = om_in;
   const float om_min = (float)(1.0 - MathD::m_max);
-  bool m_capped = false;
-  if (!(om >= om_min)) {
+  float m_over_M = t.invE;
+  t.capped = !(om >= om_min);
+  if (t.capped) {
     om = om_min;
-    m_capped = true;
+    m_over_M = (1.0f - om) / Mabs;
   }
-  const float s = sqrt_approx(1.0f + 3.0f * om * (2.0f - om));
-  const float r = rcp_approx(2.0f + s);
-  const float v = 1.0f - 3.0f * om * (1.0f + (2.0f - om) * rcp_approx(s + 1.0f)) * r;
-  const float m = 1.0f - om;
-  const float vs = m_capped ? v * rcp_approx(Mabs) : 3.0f * invE * r;
-  float nx = 0.0f, ny = 0.0f, nz = 0.0f;
+  t.s = sqrt_approx(1.0f + 3.0f * om * (2.0f - om));
+  t.r = rcp_approx(2.0f + t.s);
+  const float omv = 3.0f * om * (1.0f + (2.0f - om) * rcp_approx(t.s + 1.0f)) * t.r;   // 1 - v
+  t.v = 1.0f - omv;
+  t.m = 1.0f - om;
+  e = Ef * (omv + t.v * om);
+  t.vs = 3.0f * m_over_M * t.r;
+  vx = mx * t.vs;
+  vy = my * t.vs;
+  vz = mz * t.vs;
+  t.nx = t.ny = t.nz = 0.0f;
   if (Mabs > 0.0f) {
     const float im = rcp_approx(Mabs);
-    nx = mx * im;
-    ny = my * im;
-    nz = mz * im;
+    t.nx = mx * im;
+    t.ny = my * im;
+    t.nz = mz * im;
   }
-  c2p_vjp_core<MathF>(m, s, r, v, vs, invE, nx, ny, nz, m_capped, e_floored, ebar, vbx, vby, vbz, Ebar, Mbx, Mby,
-                      Mbz);
 }
 
 // Gradient of the spectral radius rho(v_d, v^2) of hydro_math.cuh.
