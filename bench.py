@@ -48,10 +48,14 @@ FLOP_PER_CELL_STEP = 3 * sum(FLOP_PER_CELL.values())
 # writes 5; stages 2 and 3 read 10 and write 5) in storage precision.
 FIELD_ACCESSES_PER_CELL_STEP = 40
 
-# DRAM bytes per cell per launch of the FP64 z sweep (the dominant FP64 kernel), from
-# one ncu capture of the 256^3 workload (dram__bytes_read.sum + dram__bytes_write.sum,
-# mean over the three stages of a step); other kernels were not captured at full size.
-TRAFFIC_B_PER_CELL = {("fp64", "sweep_z"): 145.3}
+# DRAM bytes per cell per sweep launch, from ncu captures of the 256^3 workload
+# (dram__bytes_read.sum + dram__bytes_write.sum, mean over the three stages of a step),
+# taken with the kernels as built; a kernel change makes them stale.
+TRAFFIC_B_PER_CELL = {
+    ("fp64", "sweep_x"): 77.5, ("fp64", "sweep_y"): 117.7, ("fp64", "sweep_z"): 145.3,
+    ("fp32", "sweep_x"): 37.5, ("fp32", "sweep_y"): 57.7, ("fp32", "sweep_z"): 72.0,
+    ("mixed", "sweep_x"): 58.3, ("mixed", "sweep_y"): 78.4, ("mixed", "sweep_z"): 124.9,
+}
 
 # Peaks for an ALU-bound path, derived from unit counts and clocks: 148 SMs x
 # 128 FP32 lanes x 2 FLOP/FMA x 2.032 GHz; FP64 takes the nominal B300 rate.
