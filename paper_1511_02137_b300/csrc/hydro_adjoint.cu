@@ -124,7 +124,43 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
   auto iidx = [&](int lane, int ii) { return DIR == 0 ? lane * NI + ii : ii * LANES + lane; };
   auto cidx = [&](int lane, int j) { return DIR == 0 ? lane * SEG + j : j * LANES + lane; };
 
-  // ---- stage: U, F_d/2, rho_d at positions a0-8 .. a0+SEG+7 (clamped), adjoint a (zero outside)
+  // ---- adjoint a of L at positions a0-8 .. a0+SEG+7 (zero outside the grid).  A tile
+  // whose window holds no nonzero adjoint contributes exactly zero (every term of
+  // J_L^T a carries a factor of a): it writes its zeros (x sweep) and stops.  The
+  // adjoint of a localised observable starts on a small support that each stage
+  // widens by the stencil reach.
+  bool live = false;
+  for (int c = threadIdx.x; c < NCS; c += kAdjThreads) {
+    int lane, s;
+    if (DIR == 0) { lane = c / W; s = c - lane * W; }
+    else { s = c / LANES; lane = c - s * LANES; }
+    const int ga = a0 - 8 + s;
+    const int gl = l0 + lane;
+    const bool inside = ga >= 0 && ga < n_along && gl < n_lane;
+    const size_t oa = offset(inside ? ga : 0, gl < n_lane ? gl : 0);
+    for (int q = 0; q < 5; ++q) {
+      P aq;
+      if constexpr (MIXED) aq = inside ? p.lamf[q * N + oa] : P(0);
+      else aq = inside ? p.ascale * p.lam[q * N + oa] : P(0);
+      sA[q * NCS + c] = aq;
+      live |= aq != P(0);
+    }
+  }
+  if (!__syncthreads_or(live)) {
+    if (DIR == 0) {
+      for (int c = threadIdx.x; c < NC; c += kAdjThreads) {
+        int lane, j;
+        lane = c / SEG;
+        j = c - lane * SEG;
+        if (a0 + j >= n_along || l0 + lane >= n_lane) continue;
+        const size_t o = offset(a0 + j, l0 + lane);
+        for (int k = 0; k < 5; ++k) r_out[k * N + o] = P(0);
+      }
+    }
+    return;
+  }
+
+  // ---- stage: U, F_d/2, rho_d at positions a0-8 .. a0+SEG+7 (clamped)
   for (int c = threadIdx.x; c < NCS; c += kAdjThreads) {
     int lane, s;
     if (DIR == 0) { lane = c / W; s = c - lane * W; }
@@ -150,13 +186,6 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
     sF[3 * NCS + c] = P(0.5) * (Mz * vd + (DIR == 2 ? pr : P(0)));
     sF[4 * NCS + c] = P(0.5) * (R * vd);
     sR[c] = spectral_radius<Math>(vd, vx * vx + vy * vy + vz * vz);
-    const bool inside = ga >= 0 && ga < n_along && gl < n_lane;
-    const size_t oa = offset(inside ? ga : 0, gl < n_lane ? gl : 0);
-    if constexpr (MIXED) {
-      for (int q = 0; q < 5; ++q) sA[q * NCS + c] = inside ? p.lamf[q * N + oa] : P(0);
-    } else {
-      for (int q = 0; q < 5; ++q) sA[q * NCS + c] = inside ? p.ascale * p.lam[q * N + oa] : P(0);
-    }
   }
   __syncthreads();
 
@@ -196,7 +225,10 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
       const int x = iidx(lane, ii);
       P* cf = cF + x;   // slot t at cf[t * NIF]: consecutive interfaces hit consecutive banks
       P* cu = cU + x;
-      if (sTie[x] == 0u) {
+      // adjoint of Fhat_{i+1/2}: L_i holds -Fhat inv_dx, L_{i+1} holds +Fhat inv_dx; the
+      // reverse of an interface whose flux adjoint is zero is zero
+      const P g = (sA[q * NCS + sidx(lane, ii + 5)] - sA[q * NCS + sidx(lane, ii + 4)]) * (P)p.inv_dx;
+      if (sTie[x] == 0u || g == P(0)) {
 #pragma unroll
         for (int t = 0; t < 8; ++t) { cf[t * NIF] = P(0); cu[t * NIF] = P(0); }
         continue;
@@ -207,8 +239,6 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
         u[t] = sU[q * NCS + sidx(lane, ii + 1 + t)];
         fh[t] = sF[q * NCS + sidx(lane, ii + 1 + t)];
       }
-      // adjoint of Fhat_{i+1/2}: L_i holds -Fhat inv_dx, L_{i+1} holds +Fhat inv_dx
-      const P g = (sA[q * NCS + sidx(lane, ii + 5)] - sA[q * NCS + sidx(lane, ii + 4)]) * (P)p.inv_dx;
       P gp[7], gm[7];
       if constexpr (MIXED) {
         // f+ and the mirrored f- (cells i+4 .. i-2) in the two lanes of packed FP32x2
