@@ -91,7 +91,7 @@ __device__ __forceinline__ void cons_to_prim_tape(double E, double Mx, double My
   double Ee = E;
   t.floored = !(Ee >= e_floor);
   if (t.floored) Ee = e_floor;
-  t.invE = 1.0 / Ee;
+  t.invE = rcp_nr(Ee);
   double m = Mabs * t.invE;
   double m_over_M = t.invE;
   t.capped = !(m <= MathD::m_max);
@@ -101,7 +101,7 @@ __device__ __forceinline__ void cons_to_prim_tape(double E, double Mx, double My
   }
   t.m = m;
   t.s = sqrt(4.0 - 3.0 * m * m);
-  t.r = 1.0 / (2.0 + t.s);
+  t.r = rcp_nr(2.0 + t.s);
   t.v = 3.0 * m * t.r;
   e = Ee * (1.0 - m * t.v);
   t.vs = 3.0 * m_over_M * t.r;
@@ -230,7 +230,7 @@ __device__ __forceinline__ P weno7_vjp(const P f[7], P eps_s, P gbar, P fb[7]) {
   const P num = t[0] * z[0] + t[1] * z[1] + t[2] * z[2] + t[3] * z[3];
   const P den = t[0] + P(12) * t[1] + P(18) * t[2] + P(4) * t[3];
   P rden;
-  if constexpr (sizeof(P) == 8) rden = P(1) / den;
+  if constexpr (sizeof(P) == 8) rden = rcp_nr(den);
   else rden = rcp_approx(den);
   const P corr = num * rden;
   // ---- reverse: weights

@@ -23,10 +23,25 @@ __device__ __forceinline__ float sqrt_approx(float x) {
   return r;
 }
 
+// FP64 reciprocal by Newton-Raphson iteration for 1/d (the classical method, e.g.
+// P. Markstein, IBM J. Res. Dev. 34 (1990) 111), seeded by the hardware
+// approximation rcp.approx.ftz.f64: one third-order step y (1 + e + e^2) and one
+// second-order step y (1 + e), e = 1 - d y.  For normal d with a normal
+// reciprocal (every call site: floored energies, 2 + s, 1 - v^2/3, products of
+// shifted WENO indicators); five FP64 operations where IEEE division takes eight.
+__device__ __forceinline__ double rcp_nr(double d) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
+  double e = fma(-d, y, 1.0);
+  y = fma(y, fma(e, e, e), y);
+  e = fma(-d, y, 1.0);
+  return fma(y, e, y);
+}
+
 struct MathD {
   using T = double;
   static constexpr double m_max = 1.0 - 1e-12;   // cap on |M|/E (|M| -> E as v -> 1)
-  static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+  static __device__ __forceinline__ double rcp(double x) { return rcp_nr(x); }
   static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
 };
 
@@ -221,7 +236,7 @@ __device__ __forceinline__ float weno7_correction(const float z[4], const float 
 __device__ __forceinline__ double weno7_correction(const double z[4], const double s[4]) {
   double num, den;
   weno7_numden(z, s, num, den);
-  return num / den;
+  return num * rcp_nr(den);
 }
 
 template <class F>
@@ -242,7 +257,7 @@ __device__ __forceinline__ double weno7_sum(const double g[7], const double h[7]
   weno7_terms(h[0], h[1], h[2], h[3], h[4], h[5], h[6], eps_s, zh, sh);
   weno7_numden(zg, sg, ng, dg);
   weno7_numden(zh, sh, nh, dh);
-  return (g[3] + h[3]) + (ng * dh + nh * dg) / (dg * dh);
+  return (g[3] + h[3]) + (ng * dh + nh * dg) * rcp_nr(dg * dh);
 }
 
 // weno7_sum from first differences: g3 and dg[6] describe f+ (g3 = f+_i),
@@ -256,7 +271,7 @@ __device__ __forceinline__ double weno7_sum_d1(double g3, const double dg[6], do
   weno7_terms_d1(dh, eps_s, zh, sh);
   weno7_numden(zg, sg, ng, qg);
   weno7_numden(zh, sh, nh, qh);
-  return (g3 - h3) + (ng * qh - nh * qg) / (qg * qh);
+  return (g3 - h3) + (ng * qh - nh * qg) * rcp_nr(qg * qh);
 }
 
 // ---- FP32 pair form: two reconstructions that run the same operation
