@@ -91,6 +91,41 @@ __device__ __forceinline__ void cons_to_prim(typename M::T E, typename M::T Mx, 
 // FP32 accuracy, and runs in FP32:
 //   4 - 3m^2 = 1 + 3 om (2 - om),  1 - v = 3 om (1 + (2 - om)/(s + 1)) / (2 + s),
 //   1 - m v = (1 - v) + v om,  with s = sqrt(4 - 3m^2).
+// FP64 <-> FP32 conversions on the integer pipe, from the IEEE 754 binary64 and
+// binary32 layouts (B300 runs the hardware conversions at the FP64 rate, 1/64 of
+// FP32, and the mixed sweeps convert every staged value).  d2f_rn rounds to
+// nearest even; results below the FP32 normal range flush to signed zero, above
+// it become infinity, NaN stays NaN.  f2d is exact for normal FP32 values and
+// zero; FP32 subnormals flush to signed zero.
+__device__ __forceinline__ float d2f_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u;
+  const int ex = (int)((hi >> 20) & 0x7ffu) - 896;            // binary32 biased exponent
+  unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);             // top 23 of the 52 fraction bits
+  const unsigned rem = lo & 0x1fffffffu, half = 0x10000000u;    // the 29 bits dropped
+  m += (rem > half || (rem == half && (m & 1u))) ? 1u : 0u;     // a carry lands in the exponent
+  unsigned r = sign | (((unsigned)ex << 23) + m);
+  if (ex <= 0) r = sign;
+  if (ex >= 255) r = sign | 0x7f800000u | ((((hi & 0xfffffu) | lo) != 0u && ex == 1151) ? 0x400000u : 0u);
+  return __uint_as_float(r);
+}
+
+// Finite test of a double on the integer pipe (exponent field not all ones).
+__device__ __forceinline__ bool finite_bits(double x) {
+  return ((unsigned)__double2hiint(x) & 0x7ff00000u) != 0x7ff00000u;
+}
+__device__ __forceinline__ bool finite_bits(float x) { return isfinite(x); }
+
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xffu, sign = u & 0x80000000u, m = u & 0x7fffffu;
+  unsigned hi = sign | ((ex + 896u) << 20) | (m >> 3), lo = m << 29;
+  if (ex == 0u) { hi = sign; lo = 0u; }
+  if (ex == 0xffu) hi = sign | 0x7ff00000u | (m >> 3);
+  return __hiloint2double((int)hi, (int)lo);
+}
+
 // Split in two: mixed_om forms the floored E (as FP32, negated when the floor
 // acted) and om; cons_to_prim_om recovers the primitives from them in FP32.
 __device__ __forceinline__ void mixed_om(double E, double Mx, double My, double Mz, double e_floor, float& Ef_signed,
@@ -135,6 +170,28 @@ __device__ __forceinline__ void cons_to_prim_mixed(double E, double Mx, double M
   float Ef_signed, om;
   mixed_om(E, Mx, My, Mz, e_floor, Ef_signed, om);
   cons_to_prim_om(Ef_signed, (float)Mx, (float)My, (float)Mz, om, e, vx, vy, vz, hit);
+}
+
+// The mixed recovery of the sweeps, given the state in FP64 and its FP32
+// roundings (converted once, on the integer pipe, and shared with the fluxes).
+__device__ __forceinline__ void cons_to_prim_mixed_f(double E, double Mx, double My, double Mz, float Ef, float mx,
+                                                     float my, float mz, double e_floor, float& e, float& vx,
+                                                     float& vy, float& vz, int& hit) {
+  double Ee = E;
+  // !(E >= e_floor) (e_floor > 0) on the integer pipe: non-negative doubles order
+  // like their bit patterns, negative ones have negative patterns, NaN floors
+  const long long eb = __double_as_longlong(E);
+  const bool nan = !finite_bits(E) && (eb & 0xfffffffffffffLL) != 0;
+  const bool floored = eb < __double_as_longlong(e_floor) || nan;
+  float Eef = Ef;
+  if (floored) {
+    Ee = e_floor;
+    Eef = d2f_rn(e_floor);
+  }
+  const double D = Ee * Ee - (Mx * Mx + My * My + Mz * Mz);
+  const float Mabs = sqrt_approx(mx * mx + my * my + mz * mz);
+  const float om = d2f_rn(D) * rcp_approx(Eef * (Eef + Mabs));
+  cons_to_prim_om(floored ? -Eef : Eef, mx, my, mz, om, e, vx, vy, vz, hit);
 }
 
 // Spectral radius of the flux Jacobian along an axis: max |lambda_pm| with

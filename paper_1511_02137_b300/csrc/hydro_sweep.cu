@@ -272,14 +272,15 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
       const size_t o = offset(map_along(ga, n_along, a.periodic), gl < n_lane ? gl : n_lane - 1);
       Es = U[o]; Mxs = U[N + o]; Mys = U[2 * N + o]; Mzs = U[3 * N + o]; Rs = U[4 * N + o];
     }
-    F e, vx, vy, vz;
+    F e, vx, vy, vz, E, Mx, My, Mz, R;
     int hit = 0;
     if constexpr (PREC == HYDRO_MIXED) {
-      cons_to_prim_mixed(Es, Mxs, Mys, Mzs, a.e_floor, e, vx, vy, vz, hit);
+      E = d2f_rn(Es); Mx = d2f_rn(Mxs); My = d2f_rn(Mys); Mz = d2f_rn(Mzs); R = d2f_rn(Rs);
+      cons_to_prim_mixed_f(Es, Mxs, Mys, Mzs, E, Mx, My, Mz, a.e_floor, e, vx, vy, vz, hit);
     } else {
       cons_to_prim<Math>(Es, Mxs, Mys, Mzs, (F)a.e_floor, e, vx, vy, vz, hit);
+      E = (F)Es; Mx = (F)Mxs; My = (F)Mys; Mz = (F)Mzs; R = (F)Rs;
     }
-    const F E = (F)Es, Mx = (F)Mxs, My = (F)Mys, Mz = (F)Mzs, R = (F)Rs;
     const F p = e * F(1.0 / 3.0);
     const F vd = DIR == 0 ? vx : (DIR == 1 ? vy : vz);
     const F rho = spectral_radius<Math>(vd, vx * vx + vy * vy + vz * vz);
@@ -426,7 +427,11 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
       // accumulate in storage precision (FP64 for FP64 and mixed, FP32 for FP32)
       Store Ld[5];
 #pragma unroll
-      for (int q = 0; q < 5; ++q) Ld[q] = (Store)((PF::on ? sPr[q * NC + c] : rhs[q * N + o]) + L[q]);
+      for (int q = 0; q < 5; ++q) {
+        const F lq = (PF::on ? sPr[q * NC + c] : rhs[q * N + o]) + L[q];
+        if constexpr (PREC == HYDRO_MIXED) Ld[q] = f2d(lq);
+        else Ld[q] = (Store)lq;
+      }
       if (jets_here) {
         const int gx = DIR == 0 ? ga : gl;
         const int gy = DIR == 1 ? ga : (DIR == 0 ? gl : fixed);
@@ -462,7 +467,7 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
                                               : (Store)sU[q * NCS + sidx(lane, j + G)];
         const Store l = Ld[q];
         Store out = (a.a == 0.0) ? u + dt * l : ca * (PF::on ? sP0[q * NC + c] : U0[q * N + o]) + cb * (u + dt * l);
-        bad |= !isfinite(out);
+        bad |= !finite_bits(out);
         Uout[q * N + o] = out;
       }
     }
