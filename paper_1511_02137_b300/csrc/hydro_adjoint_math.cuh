@@ -177,7 +177,7 @@ __device__ __forceinline__ void spectral_radius_grad(typename M::T vd, typename 
   d_v2 = (dN_v2 + rho * third) * iD;
 }
 
-// WENO7 reconstruction (as weno7<F>: folded candidates, chained indicator
+// WENO7 reconstruction (as weno7_terms: folded candidates, chained indicator
 // terms) and the adjoint of its 7 inputs for an output adjoint gbar.  The
 // forward keeps the indicator terms a_k, b_k, c_k, the candidate terms z_k and
 // the shifted indicators s_k = eps_s + beta'_k; the weights run in product form

@@ -165,13 +165,6 @@ __device__ __forceinline__ void cons_to_prim_om(float Ef_signed, float mx, float
   vz = mz * vs;
 }
 
-__device__ __forceinline__ void cons_to_prim_mixed(double E, double Mx, double My, double Mz, double e_floor,
-                                                   float& e, float& vx, float& vy, float& vz, int& hit) {
-  float Ef_signed, om;
-  mixed_om(E, Mx, My, Mz, e_floor, Ef_signed, om);
-  cons_to_prim_om(Ef_signed, (float)Mx, (float)My, (float)Mz, om, e, vx, vy, vz, hit);
-}
-
 // The mixed recovery of the sweeps, given the state in FP64 and its FP32
 // roundings (converted once, on the integer pipe, and shared with the fluxes).
 __device__ __forceinline__ void cons_to_prim_mixed_f(double E, double Mx, double My, double Mz, float Ef, float mx,
@@ -278,49 +271,13 @@ __device__ __forceinline__ void weno7_numden(const double z[4], const double s[4
   den = t0 + 12.0 * t1 + 18.0 * t2 + 4.0 * t3;
 }
 
-// FP32: the product form could overflow; one approximate reciprocal per weight.
-__device__ __forceinline__ float weno7_correction(const float z[4], const float s[4]) {
-  float t0 = rcp_approx(s[0]), t1 = rcp_approx(s[1]), t2 = rcp_approx(s[2]), t3 = rcp_approx(s[3]);
-  t0 *= t0;
-  t1 *= t1;
-  t2 *= t2;
-  t3 *= t3;
-  const float num = t0 * z[0] + t1 * z[1] + t2 * z[2] + t3 * z[3];
-  const float den = t0 + 12.0f * t1 + 18.0f * t2 + 4.0f * t3;
-  return num * rcp_approx(den);
-}
-
-__device__ __forceinline__ double weno7_correction(const double z[4], const double s[4]) {
-  double num, den;
-  weno7_numden(z, s, num, den);
-  return num * rcp_nr(den);
-}
-
-template <class F>
-__device__ __forceinline__ F weno7(F f0, F f1, F f2, F f3, F f4, F f5, F f6, F eps_s) {
-  F z[4], s[4];
-  weno7_terms(f0, f1, f2, f3, f4, f5, f6, eps_s, z, s);
-  return f3 + weno7_correction(z, s);
-}
-
-// FP64 sum of the two reconstructions of one interface (f+ from g, f- from the
-// mirrored h): both corrections over one common denominator, one division
-// instead of two.  Each denominator lies in [eps_s^6, (eps_s + beta)^6], so the
-// product neither underflows (eps_s >= 1e-20) nor overflows for any indicator
-// below 1e25.
-__device__ __forceinline__ double weno7_sum(const double g[7], const double h[7], double eps_s) {
-  double zg[4], sg[4], zh[4], sh[4], ng, dg, nh, dh;
-  weno7_terms(g[0], g[1], g[2], g[3], g[4], g[5], g[6], eps_s, zg, sg);
-  weno7_terms(h[0], h[1], h[2], h[3], h[4], h[5], h[6], eps_s, zh, sh);
-  weno7_numden(zg, sg, ng, dg);
-  weno7_numden(zh, sh, nh, dh);
-  return (g[3] + h[3]) + (ng * dh + nh * dg) * rcp_nr(dg * dh);
-}
-
-// weno7_sum from first differences: g3 and dg[6] describe f+ (g3 = f+_i),
-// h3 and dh[6] the negated mirrored f- (h3 = -f-_{i+1}); the reconstruction of
-// a negated stencil is the negated reconstruction, so the sum of the two
-// reconstructions is g3 - h3 + (ng dh - nh dg)/(dg dh).
+// FP64 sum of the two reconstructions of one interface from first differences:
+// g3 and dg[6] describe f+ (g3 = f+_i), h3 and dh[6] the negated mirrored f-
+// (h3 = -f-_{i+1}); the reconstruction of a negated stencil is the negated
+// reconstruction, so the sum is g3 - h3 + (ng dh - nh dg)/(dg dh): both
+// corrections over one common denominator, one reciprocal instead of two.
+// Each denominator lies in [eps_s^6, (eps_s + beta)^6], so the product neither
+// underflows (eps_s >= 1e-20) nor overflows for any indicator below 1e25.
 __device__ __forceinline__ double weno7_sum_d1(double g3, const double dg[6], double h3, const double dh[6],
                                                double eps_s) {
   double zg[4], sg[4], zh[4], sh[4], ng, qg, nh, qh;
@@ -342,7 +299,7 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(rcp_approx(a.x), rcp_approx(a.y)); }
 
-// Same arithmetic as weno7<float> per lane.
+// The reconstruction of weno7_terms with reciprocal weights per lane.
 __device__ __forceinline__ float2 weno7_pair(float2 f0, float2 f1, float2 f2, float2 f3, float2 f4, float2 f5,
                                              float2 f6, float eps_s) {
   const float2 d10 = sub2(f1, f0), d11 = sub2(f2, f1), d12 = sub2(f3, f2), d13 = sub2(f4, f3), d14 = sub2(f5, f4),
