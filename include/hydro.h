@@ -67,7 +67,9 @@ typedef struct {
   double hbarc;         /* hbar c [GeV fm] (0.1973) */
   double dof;           /* degrees of freedom in e = (pi^2/30) dof T^4/(hbar c)^3 (47.5) */
   double e_floor;       /* floor on E in the primitive recovery [GeV/fm^3] */
-  double weno_eps;      /* epsilon of the WENO weights (1e-6); must lie in [1e-20, 1e20] */
+  double weno_eps;      /* epsilon of the WENO weights (1e-6); must lie in [1e-20, 1e20] for
+                           HYDRO_FP64 and in [1e-18, 1e18] for HYDRO_FP32 and HYDRO_MIXED, whose
+                           FP32 weights 1/(eps + beta)^2 must stay finite and normal */
   double cfl_limit;     /* hydro_step returns HYDRO_ECFL when max speed * dt/dx exceeds it; <= 0: off */
   void* cuda_stream;    /* cudaStream_t for all device work; NULL = legacy default stream */
   void* workspace;      /* device buffer of >= hydro_workspace_size() bytes, 256-byte aligned,

@@ -698,7 +698,7 @@ hydro_status hydro_adjoint_create(const hydro_config* cfg, int32_t nsteps, int32
     return HYDRO_EINVAL;
   if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1 || nsteps < 1 || checkpoint_every < 1 || !apex || !axis)
     return HYDRO_EINVAL;
-  if (!(cfg->dx > 0.0) || !(cfg->dt > 0.0) || !(cfg->e_floor > 0.0) || !(cfg->weno_eps >= 1e-20 && cfg->weno_eps <= 1e20)) return HYDRO_EINVAL;
+  if (!(cfg->dx > 0.0) || !(cfg->dt > 0.0) || !(cfg->e_floor > 0.0) || !weno_eps_ok(cfg->precision, cfg->weno_eps)) return HYDRO_EINVAL;
   const double al = std::sqrt(axis[0] * axis[0] + axis[1] * axis[1] + axis[2] * axis[2]);
   if (!(al > 0.0) || !(rmax > 0.0) || !(half_angle_deg > 0.0 && half_angle_deg < 180.0)) return HYDRO_EINVAL;
   hydro_adjoint* a = new (std::nothrow) hydro_adjoint;

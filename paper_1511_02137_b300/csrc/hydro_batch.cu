@@ -32,7 +32,7 @@ bool config_ok(const hydro_config* c) {
   if (c->boundary != HYDRO_OUTFLOW && c->boundary != HYDRO_PERIODIC) return false;
   if (c->weno_order != 7) return false;   // the batched kernels are compiled for WENO7
   if (!(c->dx > 0.0) || !(c->dt > 0.0) || !std::isfinite(c->t0)) return false;
-  if (!(c->hbarc > 0.0) || !(c->dof > 0.0) || !(c->e_floor > 0.0) || !(c->weno_eps >= 1e-20 && c->weno_eps <= 1e20)) return false;
+  if (!(c->hbarc > 0.0) || !(c->dof > 0.0) || !(c->e_floor > 0.0) || !weno_eps_ok(c->precision, c->weno_eps)) return false;
   if (!std::isfinite(c->k_rad) || !std::isfinite(c->k_coll) || !std::isfinite(c->cr_over_cf)) return false;
   if (c->workspace && ((uintptr_t)c->workspace % kAlign) != 0) return false;
   return true;

@@ -7,6 +7,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include "hydro.h"
+
 namespace hydro {
 
 constexpr int kMaxJets = 16;
@@ -39,6 +41,25 @@ struct SourceCoef {
   double wdt_vol; // dt * RK3 weight of the stage * dx^3 (deposit diagnostic)
 };
 
+// The launch constants in the forms the sweep kernels use, derived on the host
+// (derive_constants) so that no thread converts an FP64 argument: B300 runs FP64
+// arithmetic and FP64<->FP32 conversions at 1/64 of the FP32 rate.
+struct LaunchConst {
+  double eps_s;     // WENO epsilon in the scaled indicator form of the order in use
+  float eps_s_f;    // the same rounded to FP32
+  float inv_dx_f, dt_f, a_f, b_f, e_floor_f;
+  int first;        // a == 0: the stage result is U + dt L
+};
+
+// Range of the WENO epsilon each precision can represent in its weights.  FP64
+// forms products of two denominators (eps_s^6 .. (eps_s + beta)^6 each); FP32
+// squares reciprocals of eps_s + beta and sums four of them, so eps_s must keep
+// 35 / eps_s^2 below the FP32 maximum and 1 / (eps_s + beta)^2 above its
+// smallest normal.
+inline bool weno_eps_ok(int precision, double eps) {
+  return precision == HYDRO_FP64 ? (eps >= 1e-20 && eps <= 1e20) : (eps >= 1e-18 && eps <= 1e18);
+}
+
 // Everything a sweep tile needs except the jet list.
 struct GridArgs {
   const void* U;    // state the right-hand side is evaluated on
@@ -56,6 +77,7 @@ struct GridArgs {
   int reduce_speed; // 1: fold spectral radii into diag->vmax_bits
   int count_floors; // 1: count floor hits (x sweep of each stage)
   SourceCoef src;
+  LaunchConst k;    // filled by the launchers from the fields above
 };
 
 // Arguments of a single-grid sweep launch.
@@ -86,6 +108,7 @@ struct BatchArgs {
   double inv_dx, dt, a, b, e_floor, eps;
   int reduce_speed, count_floors;
   SourceCoef src;
+  LaunchConst k;    // filled by launch_batch_sweep
 };
 
 // Tile shapes the batched sweeps can use (index = autotuner choice):

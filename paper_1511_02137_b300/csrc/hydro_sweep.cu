@@ -57,6 +57,14 @@ __device__ __forceinline__ int map_along(int i, int n, int periodic) {
   return i < 0 ? 0 : (i >= n ? n - 1 : i);
 }
 
+// A launch constant in the flux or storage type: the host-rounded FP32 copy or
+// the FP64 original.
+template <class T>
+__device__ __forceinline__ T kconst(double d, float f) {
+  if constexpr (sizeof(T) == 4) return f;
+  else return d;
+}
+
 // Maximum of two non-negative values.  Non-negative doubles order like their
 // bit patterns, so FP64 takes the integer maximum and leaves the FP64 pipe
 // (1/64 of the FP32 rate on this part) to the arithmetic.
@@ -212,7 +220,7 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   F* sPr = sH + 5 * NIF;                                 // [5][NC] accumulator
   Store* sP0 = reinterpret_cast<Store*>(sPr + 5 * NC);   // [5][NC] U0, then (mixed) [5][NC] U
   if constexpr (PF::on) {
-    const bool need_u0 = FINAL && a.a != 0.0;
+    const bool need_u0 = FINAL && !a.k.first;
     const F* rhs_in = static_cast<const F*>(a.rhs);
     const Store* U0_in = static_cast<const Store*>(a.U0);
     for (int c = threadIdx.x; c < NC; c += kThreads) {
@@ -278,7 +286,7 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
       E = d2f_rn(Es); Mx = d2f_rn(Mxs); My = d2f_rn(Mys); Mz = d2f_rn(Mzs); R = d2f_rn(Rs);
       cons_to_prim_mixed_f(Es, Mxs, Mys, Mzs, E, Mx, My, Mz, a.e_floor, e, vx, vy, vz, hit);
     } else {
-      cons_to_prim<Math>(Es, Mxs, Mys, Mzs, (F)a.e_floor, e, vx, vy, vz, hit);
+      cons_to_prim<Math>(Es, Mxs, Mys, Mzs, kconst<F>(a.e_floor, a.k.e_floor_f), e, vx, vy, vz, hit);
       E = (F)Es; Mx = (F)Mxs; My = (F)Mys; Mz = (F)Mzs; R = (F)Rs;
     }
     const F p = e * F(1.0 / 3.0);
@@ -329,7 +337,7 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   }
 
   // ---------------- phase 2: numerical flux at every interface of the tile
-  const F eps = (ORDER == 7) ? (F)(kW7EpsScale * a.eps) : (F)(kW5EpsScale * a.eps);
+  const F eps = kconst<F>(a.k.eps_s, a.k.eps_s_f);
   // numerical flux of components q0 .. q1-1 at the interface left of tile cell j
   // (its stencil is staged cells j .. j + 2G - 1)
   auto flux_at = [&](int lane, int j, int q0, int q1) {
@@ -401,7 +409,7 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
     }
   }
   F* __restrict__ rhs = static_cast<F*>(a.rhs);
-  const F inv_dx = (F)a.inv_dx;
+  const F inv_dx = kconst<F>(a.inv_dx, a.k.inv_dx_f);
   bool bad = false;
   if constexpr (PF::on) cp_async_wait_all();   // each thread reads only its own copies
   for (int c = threadIdx.x; c < NC; c += kThreads) {
@@ -459,14 +467,14 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
       // U0 and Uout alias at the last stage (in-place update of the step state)
       const Store* U0 = static_cast<const Store*>(a.U0);
       Store* Uout = static_cast<Store*>(a.Uout);
-      const Store dt = (Store)a.dt, ca = (Store)a.a, cb = (Store)a.b;
+      const Store dt = kconst<Store>(a.dt, a.k.dt_f), ca = kconst<Store>(a.a, a.k.a_f), cb = kconst<Store>(a.b, a.k.b_f);
 #pragma unroll
       for (int q = 0; q < 5; ++q) {
         // the cell's own state is staged already unless storage and flux types differ (mixed)
         const Store u = (PREC == HYDRO_MIXED) ? (PF::on ? sP0[(5 + q) * NC + c] : U[q * N + o])
                                               : (Store)sU[q * NCS + sidx(lane, j + G)];
         const Store l = Ld[q];
-        Store out = (a.a == 0.0) ? u + dt * l : ca * (PF::on ? sP0[q * NC + c] : U0[q * N + o]) + cb * (u + dt * l);
+        Store out = a.k.first ? u + dt * l : ca * (PF::on ? sP0[q * NC + c] : U0[q * N + o]) + cb * (u + dt * l);
         bad |= !finite_bits(out);
         Uout[q * N + o] = out;
       }
@@ -518,6 +526,7 @@ __global__ void __launch_bounds__(kThreads) batch_sweep_kernel(const BatchArgs b
     g.reduce_speed = b.reduce_speed;
     g.count_floors = b.count_floors;
     g.src = b.src;
+    g.k = b.k;
     sweep_tile<PREC, 7, DIR, FINAL, SEG, LANES>(g, b.jets[td.x], td.y, td.z, td.w, smem_raw);
     __syncthreads();   // the next tile overwrites shared memory
   }
@@ -568,8 +577,24 @@ static cudaError_t launch_order(int order, int dir, const SweepArgs& a, cudaStre
   return order == 5 ? launch_dir<PREC, 5>(dir, a, s, t) : launch_dir<PREC, 7>(dir, a, s, t);
 }
 
-cudaError_t launch_sweep(int precision, int order, int dir, const SweepArgs& a, cudaStream_t s,
+LaunchConst derive_constants(const GridArgs& g, int order) {
+  LaunchConst k;
+  // the indicators are used in scaled form (720/781 beta for WENO7, 12/13 beta for WENO5)
+  k.eps_s = (order == 7 ? kW7EpsScale : kW5EpsScale) * g.eps;
+  k.eps_s_f = (float)k.eps_s;
+  k.inv_dx_f = (float)g.inv_dx;
+  k.dt_f = (float)g.dt;
+  k.a_f = (float)g.a;
+  k.b_f = (float)g.b;
+  k.e_floor_f = (float)g.e_floor;
+  k.first = g.a == 0.0;
+  return k;
+}
+
+cudaError_t launch_sweep(int precision, int order, int dir, const SweepArgs& args, cudaStream_t s,
                          const CUtensorMap* tmap) {
+  SweepArgs a = args;
+  a.k = derive_constants(a, order);
   switch (precision) {
     case HYDRO_FP64: return launch_order<HYDRO_FP64>(order, dir, a, s, tmap);
     case HYDRO_FP32: return launch_order<HYDRO_FP32>(order, dir, a, s, tmap);
@@ -700,8 +725,17 @@ static int batch_occupancy_prec(int dir, int variant) {
   }
 }
 
-cudaError_t launch_batch_sweep(int precision, int dir, int variant, const BatchArgs& a, int grid, cudaStream_t s) {
-  if (grid <= 0 || a.ntiles <= 0) return cudaSuccess;
+cudaError_t launch_batch_sweep(int precision, int dir, int variant, const BatchArgs& args, int grid, cudaStream_t s) {
+  if (grid <= 0 || args.ntiles <= 0) return cudaSuccess;
+  BatchArgs a = args;
+  GridArgs g;
+  g.inv_dx = a.inv_dx;
+  g.dt = a.dt;
+  g.a = a.a;
+  g.b = a.b;
+  g.e_floor = a.e_floor;
+  g.eps = a.eps;
+  a.k = derive_constants(g, 7);
   switch (precision) {
     case HYDRO_FP64: return batch_launch_prec<HYDRO_FP64>(dir, variant, a, grid, s);
     case HYDRO_FP32: return batch_launch_prec<HYDRO_FP32>(dir, variant, a, grid, s);

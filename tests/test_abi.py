@@ -72,6 +72,25 @@ def test_invalid_configuration_is_rejected_without_touching_the_device(hy, field
     assert h.value is None
 
 
+@pytest.mark.parametrize("precision,eps,ok", [("fp64", 1e-19, True), ("fp64", 1e19, True), ("fp32", 1e-18, True),
+                                               ("fp32", 1e18, True), ("fp32", 1e-19, False), ("fp32", 1e19, False),
+                                               ("mixed", 1e-19, False), ("mixed", 1e19, False)])
+def test_weno_eps_range_depends_on_the_precision_of_the_weights(hy, precision, eps, ok):
+    """FP32 weights 1/(eps + beta)^2 overflow below eps ~ 3e-19 (flat regions have
+    beta = 0) and fall below the smallest normal above ~ 1e19; FP64 weights in
+    product form take [1e-20, 1e20]."""
+    c = hy.hydro_config_default(16, 16, 16, precision=precision, weno_eps=eps)
+    size = ctypes.c_size_t()
+    rc = hy._lib().hydro_workspace_size(ctypes.byref(c), ctypes.byref(size))
+    assert (rc == hy.HYDRO_OK) == ok and (rc == hy.HYDRO_EINVAL) == (not ok)
+    if precision == "mixed" and not ok:   # the mixed adjoint rejects it before allocating
+        h = ctypes.c_void_p()
+        d3 = ctypes.c_double * 3
+        rc = hy._lib().hydro_adjoint_create(ctypes.byref(c), 4, 2, d3(0, 0, 0), d3(1, 0, 0), 30.0, 3.0,
+                                            ctypes.byref(h))
+        assert rc == hy.HYDRO_EINVAL and not h.value
+
+
 def test_misaligned_workspace_is_rejected(hy):
     c = hy.hydro_config_default(8, 8, 8)
     c.workspace = 0x1000 + 8

@@ -148,6 +148,25 @@ def test_reduced_precision_error_against_fp64_oracle(hy, orc, W, precision, tol)
     assert gd["jet_cells"][0] == od.jet_cells[0]
 
 
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+@pytest.mark.parametrize("eps", [1e-18, 1e18])
+def test_reduced_precision_weights_at_the_ends_of_the_eps_range(hy, W, precision, eps):
+    """The FP32 weights at the smallest and largest accepted epsilon: the vacuum
+    around the fireball is flat (beta = 0, weights 1/eps_s^2) and the result
+    stays finite and close to the FP64 path with the same epsilon."""
+    w = W.ELLIPSOIDAL_32
+    res = {}
+    for prec in ("fp64", precision):
+        ctx = gpu_context(hy, w, prec, eps=eps)
+        hy.hydro_step(ctx, w.steps)
+        res[prec] = hy.hydro_read_fields(ctx, hy.HYDRO_CONSERVED)
+        hy.hydro_destroy(ctx)
+    assert np.isfinite(res[precision]).all()
+    err = norm_rel_err(res[precision], res["fp64"])
+    print(precision, "eps", eps, "error vs FP64 per field:", err)
+    assert np.all(err <= 1e-4), err
+
+
 def test_full_size_one_step_fp64_against_oracle(hy, orc, W):
     """The paper's 256^3 grid, one RK3 step in the bench's launch configuration,
     every cell compared with the oracle."""
