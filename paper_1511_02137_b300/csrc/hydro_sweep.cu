@@ -128,10 +128,15 @@ template <class T>
 __device__ __forceinline__ void publish_block(T vmax, unsigned hits, DevDiag* d, bool speed, bool floors) {
   __shared__ T wmax[kThreads / 32];
   __shared__ unsigned whits[kThreads / 32];
+  // warp reductions: one redux.sync each for the hit count and, in FP32, for the
+  // maximum (vmax >= 0 and never NaN: fmax drops NaN spectral radii, and
+  // non-negative floats order like their bit patterns); FP64 maxima by shuffles
+  hits = __reduce_add_sync(0xffffffffu, hits);
+  if constexpr (sizeof(T) == 4) {
+    vmax = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(vmax)));
+  } else {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-    hits += __shfl_xor_sync(0xffffffffu, hits, o);
+    for (int o = 16; o > 0; o >>= 1) vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
   }
   const int w = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0) {
@@ -195,9 +200,13 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   constexpr int NIF = LANES * (SEG + 1);    // interfaces
   constexpr int NC = LANES * SEG;           // updated cells
 
-  F* sU = reinterpret_cast<F*>(smem_raw);   // [5][NCS] conserved
-  F* sF = sU + 5 * NCS;                     // [5][NCS] F_d / 2
-  F* sR = sF + 5 * NCS;                     // [NCS]    rho_d
+  // FP32 flux type: U and F_d/2 of a cell interleaved ([5][NCS] float2), so that
+  // one 64-bit load brings both to an interface; FP64: [5][NCS] U then [5][NCS] F_d/2
+  constexpr bool IL = sizeof(F) == 4;
+  F* sU = reinterpret_cast<F*>(smem_raw);   // [5][NCS] conserved (FP64)
+  F* sF = sU + 5 * NCS;                     // [5][NCS] F_d / 2 (FP64)
+  float2* sUF = reinterpret_cast<float2*>(smem_raw);   // [5][NCS] (U, F_d/2) (FP32)
+  F* sR = sU + 10 * NCS;                    // [NCS]    rho_d
   F* sH = sR + NCS;                         // [5][NIF] numerical flux
 
   const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -250,7 +259,7 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   // a tile whose halo lies inside the grid needs no ghost cells: one TMA box of all 5 fields
   bool staged = false;
   if constexpr (TMA) {
-    static_assert(sizeof(Store) == sizeof(F), "TMA staging writes the stored type into the flux-type tile");
+    static_assert(sizeof(Store) == sizeof(F) && !IL, "TMA staging writes the stored type into the FP64 tile");
     if (a0 - G >= 0 && a0 + SEG + G <= n_along && l0 + LANES <= n_lane) {
       if (threadIdx.x == 0) mbar_init(bar, 1);
       __syncthreads();
@@ -293,18 +302,26 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
     const F vd = DIR == 0 ? vx : (DIR == 1 ? vy : vz);
     const F rho = spectral_radius<Math>(vd, vx * vx + vy * vy + vz * vz);
     const F Md = DIR == 0 ? Mx : (DIR == 1 ? My : Mz);
-    if (!staged) {
-      sU[0 * NCS + c] = E;
-      sU[1 * NCS + c] = Mx;
-      sU[2 * NCS + c] = My;
-      sU[3 * NCS + c] = Mz;
-      sU[4 * NCS + c] = R;
+    const F Fh[5] = {F(0.5) * Md, F(0.5) * (Mx * vd + (DIR == 0 ? p : F(0))),
+                     F(0.5) * (My * vd + (DIR == 1 ? p : F(0))), F(0.5) * (Mz * vd + (DIR == 2 ? p : F(0))),
+                     F(0.5) * (R * vd)};
+    if constexpr (IL) {
+      sUF[0 * NCS + c] = make_float2(E, Fh[0]);
+      sUF[1 * NCS + c] = make_float2(Mx, Fh[1]);
+      sUF[2 * NCS + c] = make_float2(My, Fh[2]);
+      sUF[3 * NCS + c] = make_float2(Mz, Fh[3]);
+      sUF[4 * NCS + c] = make_float2(R, Fh[4]);
+    } else {
+      if (!staged) {
+        sU[0 * NCS + c] = E;
+        sU[1 * NCS + c] = Mx;
+        sU[2 * NCS + c] = My;
+        sU[3 * NCS + c] = Mz;
+        sU[4 * NCS + c] = R;
+      }
+#pragma unroll
+      for (int q = 0; q < 5; ++q) sF[q * NCS + c] = Fh[q];
     }
-    sF[0 * NCS + c] = F(0.5) * Md;
-    sF[1 * NCS + c] = F(0.5) * (Mx * vd + (DIR == 0 ? p : F(0)));
-    sF[2 * NCS + c] = F(0.5) * (My * vd + (DIR == 1 ? p : F(0)));
-    sF[3 * NCS + c] = F(0.5) * (Mz * vd + (DIR == 2 ? p : F(0)));
-    sF[4 * NCS + c] = F(0.5) * (R * vd);
     sR[c] = rho;
     if (s >= G && s < G + SEG && ga < n_along && gl < n_lane) {
       vmax = fmax(vmax, rho);
@@ -350,16 +367,23 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
       F u[2 * G], f[2 * G];
 #pragma unroll
       for (int t = 0; t < 2 * G; ++t) {
-        u[t] = sU[q * NCS + sidx(lane, j + t)];
-        f[t] = sF[q * NCS + sidx(lane, j + t)];
+        if constexpr (IL) {
+          const float2 uf = sUF[q * NCS + sidx(lane, j + t)];
+          u[t] = uf.x;
+          f[t] = uf.y;
+        } else {
+          u[t] = sU[q * NCS + sidx(lane, j + t)];
+          f[t] = sF[q * NCS + sidx(lane, j + t)];
+        }
       }
       F h;
       if constexpr (ORDER == 7 && sizeof(F) == 4) {
         // lane x: f+ from cells i-3..i+3; lane y: f- mirrored from cells i+4..i-2
-        const float2 ahp = make_float2(ah, -ah);
+        // (scalar FMAs that write the two lanes directly: a packed split would first
+        // have to move each cell's values into two different register pairs)
         float2 g[7];
 #pragma unroll
-        for (int k = 0; k < 7; ++k) g[k] = fma2(ahp, make_float2(u[k], u[7 - k]), make_float2(f[k], f[7 - k]));
+        for (int k = 0; k < 7; ++k) g[k] = make_float2(fmaf(ah, u[k], f[k]), fmaf(-ah, u[7 - k], f[7 - k]));
         const float2 hh = weno7_pair(g[0], g[1], g[2], g[3], g[4], g[5], g[6], eps);
         h = hh.x + hh.y;
       } else if constexpr (ORDER == 7) {
@@ -432,14 +456,10 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
         for (int q = 0; q < 5; ++q) rhs[q * N + o] = (PF::on ? sPr[q * NC + c] : rhs[q * N + o]) + L[q];
       }
     } else {
-      // accumulate in storage precision (FP64 for FP64 and mixed, FP32 for FP32)
-      Store Ld[5];
+      // the stage's right-hand side in the flux type
+      F Lq[5];
 #pragma unroll
-      for (int q = 0; q < 5; ++q) {
-        const F lq = (PF::on ? sPr[q * NC + c] : rhs[q * N + o]) + L[q];
-        if constexpr (PREC == HYDRO_MIXED) Ld[q] = f2d(lq);
-        else Ld[q] = (Store)lq;
-      }
+      for (int q = 0; q < 5; ++q) Lq[q] = (PF::on ? sPr[q * NC + c] : rhs[q * N + o]) + L[q];
       if (jets_here) {
         const int gx = DIR == 0 ? ga : gl;
         const int gy = DIR == 1 ? ga : (DIR == 0 ? gl : fixed);
@@ -454,10 +474,10 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
                                a.e_floor, e, vx, vy, vz, hit);
           const double T = temperature(e, a.src.t4coef);
           const double S0 = (a.src.rad * T * T * T * jets.ell[jn] + a.src.coll * T * T) * a.src.inv_vol;
-          Ld[0] += (Store)S0;
-          Ld[1] += (Store)(jets.dir[jn][0] * S0);
-          Ld[2] += (Store)(jets.dir[jn][1] * S0);
-          Ld[3] += (Store)(jets.dir[jn][2] * S0);
+          Lq[0] += (F)S0;
+          Lq[1] += (F)(jets.dir[jn][0] * S0);
+          Lq[2] += (F)(jets.dir[jn][1] * S0);
+          Lq[3] += (F)(jets.dir[jn][2] * S0);
           a.diag->dep[jn] += a.src.wdt_vol * S0;
           a.diag->cell[jn][0] = gx;
           a.diag->cell[jn][1] = gy;
@@ -470,11 +490,21 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
       const Store dt = kconst<Store>(a.dt, a.k.dt_f), ca = kconst<Store>(a.a, a.k.a_f), cb = kconst<Store>(a.b, a.k.b_f);
 #pragma unroll
       for (int q = 0; q < 5; ++q) {
-        // the cell's own state is staged already unless storage and flux types differ (mixed)
-        const Store u = (PREC == HYDRO_MIXED) ? (PF::on ? sP0[(5 + q) * NC + c] : U[q * N + o])
-                                              : (Store)sU[q * NCS + sidx(lane, j + G)];
-        const Store l = Ld[q];
-        Store out = a.k.first ? u + dt * l : ca * (PF::on ? sP0[q * NC + c] : U0[q * N + o]) + cb * (u + dt * l);
+        Store out;
+        if constexpr (PREC == HYDRO_MIXED) {
+          // a U0 + b (u + dt L) = u + a (U0 - u) + b dt L (a + b = 1): the FP64
+          // state takes an FP32 increment, which carries the FP32 accuracy of L
+          // anyway; two FP64 additions per field instead of three operations
+          const double u = PF::on ? sP0[(5 + q) * NC + c] : U[q * N + o];
+          float inc = a.k.bdt_f * Lq[q];
+          if (!a.k.first) inc = fmaf(a.k.a_f, d2f_rn((PF::on ? sP0[q * NC + c] : U0[q * N + o]) - u), inc);
+          out = u + f2d(inc);
+        } else {
+          // the cell's own state is staged already
+          const Store u = IL ? (Store)sUF[q * NCS + sidx(lane, j + G)].x : (Store)sU[q * NCS + sidx(lane, j + G)];
+          const Store l = Lq[q];
+          out = a.k.first ? u + dt * l : ca * (PF::on ? sP0[q * NC + c] : U0[q * N + o]) + cb * (u + dt * l);
+        }
         bad |= !finite_bits(out);
         Uout[q * N + o] = out;
       }
@@ -546,7 +576,7 @@ static cudaError_t launch_one(const SweepArgs& a, cudaStream_t s, const CUtensor
   if (DIR == 0) grid = dim3((a.nx + SEG - 1) / SEG, (a.ny + LANES - 1) / LANES, a.nz);
   else if (DIR == 1) grid = dim3((a.nx + LANES - 1) / LANES, (a.ny + SEG - 1) / SEG, a.nz);
   else grid = dim3((a.nx + LANES - 1) / LANES, (a.nz + SEG - 1) / SEG, a.ny);
-  constexpr bool kTmaCapable = PREC != HYDRO_MIXED && ORDER == 7;
+  constexpr bool kTmaCapable = PREC == HYDRO_FP64 && ORDER == 7;
   if (kTmaCapable && tmap) {
     auto kern = sweep_kernel<PREC, ORDER, DIR, DIR == 2, kTmaCapable>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -587,6 +617,7 @@ LaunchConst derive_constants(const GridArgs& g, int order) {
   k.a_f = (float)g.a;
   k.b_f = (float)g.b;
   k.e_floor_f = (float)g.e_floor;
+  k.bdt_f = (float)(g.b * g.dt);
   k.first = g.a == 0.0;
   return k;
 }
@@ -615,8 +646,9 @@ static void tma_box(cuuint32_t box[4]) {
 
 bool encode_sweep_tmaps(int precision, int order, void* const bufs[3], int nx, int ny, int nz,
                         CUtensorMap maps[3][3]) {
-  if (precision == HYDRO_MIXED || order != 7) return false;
-  const size_t es = precision == HYDRO_FP32 ? 4 : 8;
+  // FP32 and mixed tiles interleave U with F_d/2 per cell, which a tiled copy cannot produce
+  if (precision != HYDRO_FP64 || order != 7) return false;
+  const size_t es = 8;
   const cuuint64_t dim[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, 5};
   const cuuint64_t stride[3] = {(cuuint64_t)nx * es, (cuuint64_t)nx * ny * es, (cuuint64_t)nx * ny * nz * es};
   for (int k = 0; k < 3; ++k)
@@ -632,17 +664,12 @@ bool encode_sweep_tmaps(int precision, int order, void* const bufs[3], int nx, i
                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
   Encode encode = reinterpret_cast<Encode>(fn);
-  const CUtensorMapDataType dt = precision == HYDRO_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                                         : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  const CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   for (int b = 0; b < 3; ++b)
     for (int d = 0; d < 3; ++d) {
       cuuint32_t box[4];
-      if (precision == HYDRO_FP32) {
-        if (d == 0) tma_box<HYDRO_FP32, 0>(box); else if (d == 1) tma_box<HYDRO_FP32, 1>(box); else tma_box<HYDRO_FP32, 2>(box);
-      } else {
-        if (d == 0) tma_box<HYDRO_FP64, 0>(box); else if (d == 1) tma_box<HYDRO_FP64, 1>(box); else tma_box<HYDRO_FP64, 2>(box);
-      }
+      if (d == 0) tma_box<HYDRO_FP64, 0>(box); else if (d == 1) tma_box<HYDRO_FP64, 1>(box); else tma_box<HYDRO_FP64, 2>(box);
       if ((box[0] * es) % 16 != 0) return false;
       if (encode(&maps[b][d], dt, 4, bufs[b], dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
