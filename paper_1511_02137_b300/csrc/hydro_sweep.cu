@@ -170,17 +170,30 @@ struct Prefetch {
   static constexpr int state = on && DIR == 2 ? (PREC == HYDRO_MIXED ? 10 : 5) : 0;   // U0 (+ U)
 };
 
+// Single-grid WENO7 sweeps stage interior tiles with one TMA copy.  FP64 copies
+// straight into the tile's U array; FP32 tiles interleave U with F_d/2, so their
+// copy lands in a separate staging box that phase 1 reads.  Mixed tiles convert
+// every staged value and load through registers.
+template <int PREC>
+__host__ __device__ constexpr bool tma_staged() {
+  return PREC != HYDRO_MIXED;
+}
+
 // Shared memory of one tile, in units of the flux type: U, F_d/2 (5 fields
-// each) and rho_d per staged cell, 5 numerical fluxes per interface, and the
-// prefetched phase-3 operands per updated cell.
-template <int PREC, int ORDER, int DIR, int SEG, int LANES>
+// each) and rho_d per staged cell, 5 numerical fluxes per interface, the
+// prefetched phase-3 operands per updated cell, and (FP32 with TMA staging)
+// the staging box of 5 fields per staged cell.
+template <int PREC, int ORDER, int DIR, int SEG, int LANES, bool STAGE = false>
 __host__ __device__ constexpr int tile_smem_words() {
   using F = typename Types<PREC>::Flux;
   using Store = typename Types<PREC>::Store;
   constexpr int G = (ORDER == 7) ? 4 : 3, NCS = LANES * (SEG + 2 * G), NIF = LANES * (SEG + 1), NC = LANES * SEG;
   constexpr int delta = (sizeof(F) == 8 && ORDER == 7) ? 10 * NCS : 0;   // FP64 WENO7: neighbour differences
-  return 11 * NCS + 5 * NIF + Prefetch<PREC, DIR>::rhs * NC +
-         Prefetch<PREC, DIR>::state * NC * (int)(sizeof(Store) / sizeof(F)) + delta;
+  constexpr int body = 11 * NCS + 5 * NIF + Prefetch<PREC, DIR>::rhs * NC +
+                       Prefetch<PREC, DIR>::state * NC * (int)(sizeof(Store) / sizeof(F)) + delta;
+  // the staging box starts on a 128-byte boundary
+  constexpr int align = 128 / (int)sizeof(F);
+  return (STAGE && sizeof(F) == 4) ? (body + align - 1) / align * align + 5 * NCS : body;
 }
 
 // One tile of a sweep: SEG cells along the sweep axis starting at a0, LANES
@@ -258,16 +271,18 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   // ---------------- phase 1: stage cells, primitives, half fluxes, rho
   // a tile whose halo lies inside the grid needs no ghost cells: one TMA box of all 5 fields
   bool staged = false;
+  constexpr int kStageOff = tile_smem_words<PREC, ORDER, DIR, SEG, LANES, TMA>() - 5 * NCS;
+  F* sStage = IL ? reinterpret_cast<F*>(smem_raw) + kStageOff : sU;   // [5][NCS] U as copied
   if constexpr (TMA) {
-    static_assert(sizeof(Store) == sizeof(F) && !IL, "TMA staging writes the stored type into the FP64 tile");
+    static_assert(sizeof(Store) == sizeof(F), "TMA staging copies the stored type into the flux-type tile");
     if (a0 - G >= 0 && a0 + SEG + G <= n_along && l0 + LANES <= n_lane) {
       if (threadIdx.x == 0) mbar_init(bar, 1);
       __syncthreads();
       if (threadIdx.x == 0) {
         mbar_expect_tx(bar, (unsigned)(5 * NCS * sizeof(Store)));
-        if (DIR == 0) tma_load_4d(sU, tmap, a0 - G, l0, fixed, 0, bar);
-        else if (DIR == 1) tma_load_4d(sU, tmap, l0, a0 - G, fixed, 0, bar);
-        else tma_load_4d(sU, tmap, l0, fixed, a0 - G, 0, bar);
+        if (DIR == 0) tma_load_4d(sStage, tmap, a0 - G, l0, fixed, 0, bar);
+        else if (DIR == 1) tma_load_4d(sStage, tmap, l0, a0 - G, fixed, 0, bar);
+        else tma_load_4d(sStage, tmap, l0, fixed, a0 - G, 0, bar);
       }
       if (!mbar_wait_bounded(bar, 0)) atomicCAS(&a.diag->status, 0, (int)HYDRO_ETIMEOUT);
       staged = true;
@@ -283,8 +298,8 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
     const int gl = l0 + lane;
     Store Es, Mxs, Mys, Mzs, Rs;
     if (staged) {
-      Es = (Store)sU[c]; Mxs = (Store)sU[NCS + c]; Mys = (Store)sU[2 * NCS + c];
-      Mzs = (Store)sU[3 * NCS + c]; Rs = (Store)sU[4 * NCS + c];
+      Es = (Store)sStage[c]; Mxs = (Store)sStage[NCS + c]; Mys = (Store)sStage[2 * NCS + c];
+      Mzs = (Store)sStage[3 * NCS + c]; Rs = (Store)sStage[4 * NCS + c];
     } else {
       const size_t o = offset(map_along(ga, n_along, a.periodic), gl < n_lane ? gl : n_lane - 1);
       Es = U[o]; Mxs = U[N + o]; Mys = U[2 * N + o]; Mzs = U[3 * N + o]; Rs = U[4 * N + o];
@@ -571,17 +586,18 @@ template <int PREC, int ORDER, int DIR>
 static cudaError_t launch_one(const SweepArgs& a, cudaStream_t s, const CUtensorMap* tmap) {
   using F = typename Types<PREC>::Flux;
   constexpr int SEG = Tile<PREC, DIR>::SEG, LANES = Tile<PREC, DIR>::LANES;
+  constexpr bool kTmaCapable = ORDER == 7 && tma_staged<PREC>();
   constexpr size_t smem = sizeof(F) * (size_t)tile_smem_words<PREC, ORDER, DIR, SEG, LANES>();
+  constexpr size_t smem_tma = sizeof(F) * (size_t)tile_smem_words<PREC, ORDER, DIR, SEG, LANES, kTmaCapable>();
   dim3 grid;
   if (DIR == 0) grid = dim3((a.nx + SEG - 1) / SEG, (a.ny + LANES - 1) / LANES, a.nz);
   else if (DIR == 1) grid = dim3((a.nx + LANES - 1) / LANES, (a.ny + SEG - 1) / SEG, a.nz);
   else grid = dim3((a.nx + LANES - 1) / LANES, (a.nz + SEG - 1) / SEG, a.ny);
-  constexpr bool kTmaCapable = PREC == HYDRO_FP64 && ORDER == 7;
   if (kTmaCapable && tmap) {
     auto kern = sweep_kernel<PREC, ORDER, DIR, DIR == 2, kTmaCapable>;
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tma);
     if (err != cudaSuccess) return err;
-    kern<<<grid, kThreads, smem, s>>>(a, *tmap);
+    kern<<<grid, kThreads, smem_tma, s>>>(a, *tmap);
     return cudaGetLastError();
   }
   auto kern = sweep_kernel<PREC, ORDER, DIR, DIR == 2, false>;
@@ -646,9 +662,8 @@ static void tma_box(cuuint32_t box[4]) {
 
 bool encode_sweep_tmaps(int precision, int order, void* const bufs[3], int nx, int ny, int nz,
                         CUtensorMap maps[3][3]) {
-  // FP32 and mixed tiles interleave U with F_d/2 per cell, which a tiled copy cannot produce
-  if (precision != HYDRO_FP64 || order != 7) return false;
-  const size_t es = 8;
+  if (precision == HYDRO_MIXED || order != 7) return false;
+  const size_t es = precision == HYDRO_FP32 ? 4 : 8;
   const cuuint64_t dim[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, 5};
   const cuuint64_t stride[3] = {(cuuint64_t)nx * es, (cuuint64_t)nx * ny * es, (cuuint64_t)nx * ny * nz * es};
   for (int k = 0; k < 3; ++k)
@@ -664,12 +679,17 @@ bool encode_sweep_tmaps(int precision, int order, void* const bufs[3], int nx, i
                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
   Encode encode = reinterpret_cast<Encode>(fn);
-  const CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  const CUtensorMapDataType dt = precision == HYDRO_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                         : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   for (int b = 0; b < 3; ++b)
     for (int d = 0; d < 3; ++d) {
       cuuint32_t box[4];
-      if (d == 0) tma_box<HYDRO_FP64, 0>(box); else if (d == 1) tma_box<HYDRO_FP64, 1>(box); else tma_box<HYDRO_FP64, 2>(box);
+      if (precision == HYDRO_FP32) {
+        if (d == 0) tma_box<HYDRO_FP32, 0>(box); else if (d == 1) tma_box<HYDRO_FP32, 1>(box); else tma_box<HYDRO_FP32, 2>(box);
+      } else {
+        if (d == 0) tma_box<HYDRO_FP64, 0>(box); else if (d == 1) tma_box<HYDRO_FP64, 1>(box); else tma_box<HYDRO_FP64, 2>(box);
+      }
       if ((box[0] * es) % 16 != 0) return false;
       if (encode(&maps[b][d], dt, 4, bufs[b], dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
