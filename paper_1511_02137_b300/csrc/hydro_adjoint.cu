@@ -71,6 +71,7 @@ struct VjpArgs {
   double ascale;
   int nx, ny, nz;
   double inv_dx, e_floor, eps_s;
+  float inv_dx_f, eps_s_f;   // the same rounded to FP32 on the host (mixed)
   double rad_per_k, coll_per_k, k_rad, k_coll, t4coef, inv_vol;
   JetStage jets;
 };
@@ -227,7 +228,8 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
       P* cu = cU + x;
       // adjoint of Fhat_{i+1/2}: L_i holds -Fhat inv_dx, L_{i+1} holds +Fhat inv_dx; the
       // reverse of an interface whose flux adjoint is zero is zero
-      const P g = (sA[q * NCS + sidx(lane, ii + 5)] - sA[q * NCS + sidx(lane, ii + 4)]) * (P)p.inv_dx;
+      const P g = (sA[q * NCS + sidx(lane, ii + 5)] - sA[q * NCS + sidx(lane, ii + 4)]) *
+                  (MIXED ? (P)p.inv_dx_f : (P)p.inv_dx);
       if (sTie[x] == 0u || g == P(0)) {
 #pragma unroll
         for (int t = 0; t < 8; ++t) { cf[t * NIF] = P(0); cu[t * NIF] = P(0); }
@@ -241,12 +243,12 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
       }
       P gp[7], gm[7];
       if constexpr (MIXED) {
-        // f+ and the mirrored f- (cells i+4 .. i-2) in the two lanes of packed FP32x2
+        // f+ and the mirrored f- (cells i+4 .. i-2) in the two lanes of packed FP32x2,
+        // split by scalar FMAs that write the lanes directly
         float2 fpm[7], gb[7];
-        const float2 ahp = make_float2(ah, -ah);
 #pragma unroll
-        for (int t = 0; t < 7; ++t) fpm[t] = fma2(ahp, make_float2(u[t], u[7 - t]), make_float2(fh[t], fh[7 - t]));
-        weno7_vjp_pair(fpm, (float)p.eps_s, make_float2(g, g), gb);
+        for (int t = 0; t < 7; ++t) fpm[t] = make_float2(fmaf(ah, u[t], fh[t]), fmaf(-ah, u[7 - t], fh[7 - t]));
+        weno7_vjp_pair(fpm, p.eps_s_f, make_float2(g, g), gb);
 #pragma unroll
         for (int t = 0; t < 7; ++t) {
           gp[t] = gb[t].x;
@@ -430,9 +432,12 @@ cudaError_t launch_vjp(const VjpArgs& p, cudaStream_t s) {
 // for modes 0, 1, 2) also goes to lamf, scaled by that sweep's fscale, in FP32.
 template <class R>
 __global__ void adj_combine_kernel(int mode, double ca, double cb, double* lamA, double* lamB, double* lam0,
-                                   const R* r, size_t n, float* lamf, double fscale) {
+                                   const R* r, size_t n, float* lamf, float fscale) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double ri = (double)r[i];
+    // FP32 <-> FP64 conversions on the integer pipe (B300 runs FP64 at 1/64 rate)
+    double ri;
+    if constexpr (sizeof(R) == 4) ri = f2d(r[i]);
+    else ri = r[i];
     double next;
     if (mode == 0) {
       const double la = lamA[i];
@@ -448,7 +453,7 @@ __global__ void adj_combine_kernel(int mode, double ca, double cb, double* lamA,
       next = lam0[i] + (lamA[i] + ri);
       lam0[i] = next;
     }
-    if (lamf) lamf[i] = (float)(fscale * next);
+    if (lamf) lamf[i] = fscale * d2f_rn(next);
   }
 }
 
@@ -459,11 +464,11 @@ __global__ void shadow_kernel(const double* U, float* sh, size_t n, double e_flo
     const double E = U[i], Mx = U[n + i], My = U[2 * n + i], Mz = U[3 * n + i];
     float Efs, om;
     mixed_om(E, Mx, My, Mz, e_floor, Efs, om);
-    sh[i] = (float)E;
-    sh[n + i] = (float)Mx;
-    sh[2 * n + i] = (float)My;
-    sh[3 * n + i] = (float)Mz;
-    sh[4 * n + i] = (float)U[4 * n + i];
+    sh[i] = d2f_rn(E);
+    sh[n + i] = d2f_rn(Mx);
+    sh[2 * n + i] = d2f_rn(My);
+    sh[3 * n + i] = d2f_rn(Mz);
+    sh[4 * n + i] = d2f_rn(U[4 * n + i]);
     sh[5 * n + i] = Efs;
     sh[6 * n + i] = om;
   }
@@ -471,7 +476,7 @@ __global__ void shadow_kernel(const double* U, float* sh, size_t n, double e_flo
 
 __global__ void scale_to_float_kernel(const double* x, float* y, double scale, size_t n) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    y[i] = (float)(scale * x[i]);
+    y[i] = d2f_rn(scale * x[i]);
 }
 
 struct ConeArgs {
@@ -646,6 +651,8 @@ cudaError_t vjp(hydro_adjoint* a, int64_t n, int st, const double* Uk, const dou
   p.inv_dx = 1.0 / g.dx;
   p.e_floor = g.e_floor;
   p.eps_s = kW7EpsScale * g.weno_eps;
+  p.inv_dx_f = (float)p.inv_dx;
+  p.eps_s_f = (float)p.eps_s;
   p.rad_per_k = g.cr_over_cf / (g.hbarc * g.hbarc);
   p.coll_per_k = g.cr_over_cf / g.hbarc;
   p.k_rad = g.k_rad;
@@ -677,10 +684,11 @@ cudaError_t combine(hydro_adjoint* a, int mode, int st) {
   const double fscale = kB[st == 0 ? 2 : st - 1] * a->cfg.dt;
   if (a->cfg.precision == HYDRO_MIXED)
     adj_combine_kernel<float><<<grid_1d(n5), 256, 0, a->stream>>>(
-        mode, kA[st], kB[st], a->lamA, a->lamB, a->lam0, reinterpret_cast<const float*>(a->r), n5, a->lamf, fscale);
+        mode, kA[st], kB[st], a->lamA, a->lamB, a->lam0, reinterpret_cast<const float*>(a->r), n5, a->lamf,
+        (float)fscale);
   else
     adj_combine_kernel<double><<<grid_1d(n5), 256, 0, a->stream>>>(mode, kA[st], kB[st], a->lamA, a->lamB, a->lam0,
-                                                                   a->r, n5, nullptr, 0.0);
+                                                                   a->r, n5, nullptr, 0.0f);
   return cudaGetLastError();
 }
 

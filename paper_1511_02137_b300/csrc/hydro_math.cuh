@@ -134,9 +134,9 @@ __device__ __forceinline__ void mixed_om(double E, double Mx, double My, double 
   const bool floored = !(Ee >= e_floor);
   if (floored) Ee = e_floor;
   const double D = Ee * Ee - (Mx * Mx + My * My + Mz * Mz);
-  const float Ef = (float)Ee, mx = (float)Mx, my = (float)My, mz = (float)Mz;
+  const float Ef = d2f_rn(Ee), mx = d2f_rn(Mx), my = d2f_rn(My), mz = d2f_rn(Mz);
   const float Mabs = sqrt_approx(mx * mx + my * my + mz * mz);
-  om = (float)D * rcp_approx(Ef * (Ef + Mabs));
+  om = d2f_rn(D) * rcp_approx(Ef * (Ef + Mabs));
   Ef_signed = floored ? -Ef : Ef;
 }
 
