@@ -241,16 +241,18 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   using PF = Prefetch<PREC, DIR>;
   F* sPr = sH + 5 * NIF;                                 // [5][NC] accumulator
   Store* sP0 = reinterpret_cast<Store*>(sPr + 5 * NC);   // [5][NC] U0, then (mixed) [5][NC] U
+  // every tile shape updates one cell per thread (phase 3 and its operands)
+  static_assert(NC == kThreads, "one updated cell per thread");
   if constexpr (PF::on) {
     const bool need_u0 = FINAL && !a.k.first;
     const F* rhs_in = static_cast<const F*>(a.rhs);
     const Store* U0_in = static_cast<const Store*>(a.U0);
-    for (int c = threadIdx.x; c < NC; c += kThreads) {
-      int lane, j;
-      if (DIR == 0) { lane = c / SEG; j = c - lane * SEG; }
-      else { j = c / LANES; lane = c - j * LANES; }
-      const int ga = a0 + j, gl = l0 + lane;
-      if (ga >= n_along || gl >= n_lane) continue;
+    const int c = threadIdx.x;
+    int lane, j;
+    if (DIR == 0) { lane = c / SEG; j = c - lane * SEG; }
+    else { j = c / LANES; lane = c - j * LANES; }
+    const int ga = a0 + j, gl = l0 + lane;
+    if (ga < n_along && gl < n_lane) {
       const size_t o = offset(ga, gl);
 #pragma unroll
       for (int q = 0; q < 5; ++q) cp_async_ca<sizeof(F)>(sPr + q * NC + c, rhs_in + q * N + o);
@@ -266,6 +268,23 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
       }
     }
     cp_async_commit();
+  }
+
+  // whether a jet deposits into this tile (z sweep), decided once per block and
+  // read in phase 3 after the barriers of phases 1 and 2
+  __shared__ int sJetFlag;
+  int* sJet = &sJetFlag;
+  if (FINAL && threadIdx.x == 0) {
+    int here = 0;
+    for (int jn = 0; jn < jets.n; ++jn) {
+      const int* cl = jets.cell[jn];
+      if (cl[0] < 0) continue;
+      const int jal = DIR == 0 ? cl[0] : (DIR == 1 ? cl[1] : cl[2]);
+      const int jln = DIR == 0 ? cl[1] : cl[0];
+      const int jfx = DIR == 2 ? cl[1] : cl[2];
+      if (jfx == fixed && jal >= a0 && jal < a0 + SEG && jln >= l0 && jln < l0 + LANES) here = 1;
+    }
+    *sJet = here;
   }
 
   // ---------------- phase 1: stage cells, primitives, half fluxes, rho
@@ -423,7 +442,8 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   // the left faces of the tile's cells, all components, then the right face of
   // each line split into single-component tasks so that no thread does two
   // whole interfaces while the block waits at the barrier
-  for (int it = threadIdx.x; it < NC; it += kThreads) {
+  {
+    const int it = threadIdx.x;
     int lane, j;
     if (DIR == 0) { lane = it / SEG; j = it - lane * SEG; }
     else { j = it / LANES; lane = it - j * LANES; }
@@ -436,92 +456,84 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   __syncthreads();
 
   // ---------------- phase 3: flux difference, source, stage combination
-  bool jets_here = false;
-  if (FINAL) {
-    for (int jn = 0; jn < jets.n; ++jn) {
-      const int* cl = jets.cell[jn];
-      if (cl[0] < 0) continue;
-      const int jal = DIR == 0 ? cl[0] : (DIR == 1 ? cl[1] : cl[2]);
-      const int jln = DIR == 0 ? cl[1] : cl[0];
-      const int jfx = DIR == 2 ? cl[1] : cl[2];
-      if (jfx == fixed && jal >= a0 && jal < a0 + SEG && jln >= l0 && jln < l0 + LANES) jets_here = true;
-    }
-  }
+  const bool jets_here = FINAL && *sJet != 0;
   F* __restrict__ rhs = static_cast<F*>(a.rhs);
   const F inv_dx = kconst<F>(a.inv_dx, a.k.inv_dx_f);
   bool bad = false;
   if constexpr (PF::on) cp_async_wait_all();   // each thread reads only its own copies
-  for (int c = threadIdx.x; c < NC; c += kThreads) {
+  {
+    const int c = threadIdx.x;
     int lane, j;
     if (DIR == 0) { lane = c / SEG; j = c - lane * SEG; }
     else { j = c / LANES; lane = c - j * LANES; }
     const int ga = a0 + j, gl = l0 + lane;
-    if (ga >= n_along || gl >= n_lane) continue;
-    const size_t o = offset(ga, gl);
-    const int h0 = hidx(lane, j), h1 = hidx(lane, j + 1);
-    F L[5];
+    if (ga < n_along && gl < n_lane) {
+      const size_t o = offset(ga, gl);
+      const int h0 = hidx(lane, j), h1 = hidx(lane, j + 1);
+      F L[5];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) L[q] = -(sH[q * NIF + h1] - sH[q * NIF + h0]) * inv_dx;
-    if (!FINAL) {
-      if (DIR == 0) {
+      for (int q = 0; q < 5; ++q) L[q] = -(sH[q * NIF + h1] - sH[q * NIF + h0]) * inv_dx;
+      if (!FINAL) {
+        if (DIR == 0) {
 #pragma unroll
-        for (int q = 0; q < 5; ++q) rhs[q * N + o] = L[q];
-      } else {
-#pragma unroll
-        for (int q = 0; q < 5; ++q) rhs[q * N + o] = (PF::on ? sPr[q * NC + c] : rhs[q * N + o]) + L[q];
-      }
-    } else {
-      // the stage's right-hand side in the flux type
-      F Lq[5];
-#pragma unroll
-      for (int q = 0; q < 5; ++q) Lq[q] = (PF::on ? sPr[q * NC + c] : rhs[q * N + o]) + L[q];
-      if (jets_here) {
-        const int gx = DIR == 0 ? ga : gl;
-        const int gy = DIR == 1 ? ga : (DIR == 0 ? gl : fixed);
-        const int gz = DIR == 2 ? ga : fixed;
-        for (int jn = 0; jn < jets.n; ++jn) {
-          const int* cl = jets.cell[jn];
-          if (cl[0] != gx || cl[1] != gy || cl[2] != gz) continue;
-          // Eq. 3 at the temperature of this cell, deposited as in Eq. 2
-          double e, vx, vy, vz;
-          int hit = 0;
-          cons_to_prim<MathD>((double)U[o], (double)U[N + o], (double)U[2 * N + o], (double)U[3 * N + o],
-                               a.e_floor, e, vx, vy, vz, hit);
-          const double T = temperature(e, a.src.t4coef);
-          const double S0 = (a.src.rad * T * T * T * jets.ell[jn] + a.src.coll * T * T) * a.src.inv_vol;
-          Lq[0] += (F)S0;
-          Lq[1] += (F)(jets.dir[jn][0] * S0);
-          Lq[2] += (F)(jets.dir[jn][1] * S0);
-          Lq[3] += (F)(jets.dir[jn][2] * S0);
-          a.diag->dep[jn] += a.src.wdt_vol * S0;
-          a.diag->cell[jn][0] = gx;
-          a.diag->cell[jn][1] = gy;
-          a.diag->cell[jn][2] = gz;
-        }
-      }
-      // U0 and Uout alias at the last stage (in-place update of the step state)
-      const Store* U0 = static_cast<const Store*>(a.U0);
-      Store* Uout = static_cast<Store*>(a.Uout);
-      const Store dt = kconst<Store>(a.dt, a.k.dt_f), ca = kconst<Store>(a.a, a.k.a_f), cb = kconst<Store>(a.b, a.k.b_f);
-#pragma unroll
-      for (int q = 0; q < 5; ++q) {
-        Store out;
-        if constexpr (PREC == HYDRO_MIXED) {
-          // a U0 + b (u + dt L) = u + a (U0 - u) + b dt L (a + b = 1): the FP64
-          // state takes an FP32 increment, which carries the FP32 accuracy of L
-          // anyway; two FP64 additions per field instead of three operations
-          const double u = PF::on ? sP0[(5 + q) * NC + c] : U[q * N + o];
-          float inc = a.k.bdt_f * Lq[q];
-          if (!a.k.first) inc = fmaf(a.k.a_f, d2f_rn((PF::on ? sP0[q * NC + c] : U0[q * N + o]) - u), inc);
-          out = u + f2d(inc);
+          for (int q = 0; q < 5; ++q) rhs[q * N + o] = L[q];
         } else {
-          // the cell's own state is staged already
-          const Store u = IL ? (Store)sUF[q * NCS + sidx(lane, j + G)].x : (Store)sU[q * NCS + sidx(lane, j + G)];
-          const Store l = Lq[q];
-          out = a.k.first ? u + dt * l : ca * (PF::on ? sP0[q * NC + c] : U0[q * N + o]) + cb * (u + dt * l);
+#pragma unroll
+          for (int q = 0; q < 5; ++q) rhs[q * N + o] = (PF::on ? sPr[q * NC + c] : rhs[q * N + o]) + L[q];
         }
-        bad |= !finite_bits(out);
-        Uout[q * N + o] = out;
+      } else {
+        // the stage's right-hand side in the flux type
+        F Lq[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) Lq[q] = (PF::on ? sPr[q * NC + c] : rhs[q * N + o]) + L[q];
+        if (jets_here) {
+          const int gx = DIR == 0 ? ga : gl;
+          const int gy = DIR == 1 ? ga : (DIR == 0 ? gl : fixed);
+          const int gz = DIR == 2 ? ga : fixed;
+          for (int jn = 0; jn < jets.n; ++jn) {
+            const int* cl = jets.cell[jn];
+            if (cl[0] != gx || cl[1] != gy || cl[2] != gz) continue;
+            // Eq. 3 at the temperature of this cell, deposited as in Eq. 2
+            double e, vx, vy, vz;
+            int hit = 0;
+            cons_to_prim<MathD>((double)U[o], (double)U[N + o], (double)U[2 * N + o], (double)U[3 * N + o],
+                                 a.e_floor, e, vx, vy, vz, hit);
+            const double T = temperature(e, a.src.t4coef);
+            const double S0 = (a.src.rad * T * T * T * jets.ell[jn] + a.src.coll * T * T) * a.src.inv_vol;
+            Lq[0] += (F)S0;
+            Lq[1] += (F)(jets.dir[jn][0] * S0);
+            Lq[2] += (F)(jets.dir[jn][1] * S0);
+            Lq[3] += (F)(jets.dir[jn][2] * S0);
+            a.diag->dep[jn] += a.src.wdt_vol * S0;
+            a.diag->cell[jn][0] = gx;
+            a.diag->cell[jn][1] = gy;
+            a.diag->cell[jn][2] = gz;
+          }
+        }
+        // U0 and Uout alias at the last stage (in-place update of the step state)
+        const Store* U0 = static_cast<const Store*>(a.U0);
+        Store* Uout = static_cast<Store*>(a.Uout);
+        const Store dt = kconst<Store>(a.dt, a.k.dt_f), ca = kconst<Store>(a.a, a.k.a_f), cb = kconst<Store>(a.b, a.k.b_f);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          Store out;
+          if constexpr (PREC == HYDRO_MIXED) {
+            // a U0 + b (u + dt L) = u + a (U0 - u) + b dt L (a + b = 1): the FP64
+            // state takes an FP32 increment, which carries the FP32 accuracy of L
+            // anyway; two FP64 additions per field instead of three operations
+            const double u = PF::on ? sP0[(5 + q) * NC + c] : U[q * N + o];
+            float inc = a.k.bdt_f * Lq[q];
+            if (!a.k.first) inc = fmaf(a.k.a_f, d2f_rn((PF::on ? sP0[q * NC + c] : U0[q * N + o]) - u), inc);
+            out = u + f2d(inc);
+          } else {
+            // the cell's own state is staged already
+            const Store u = IL ? (Store)sUF[q * NCS + sidx(lane, j + G)].x : (Store)sU[q * NCS + sidx(lane, j + G)];
+            const Store l = Lq[q];
+            out = a.k.first ? u + dt * l : ca * (PF::on ? sP0[q * NC + c] : U0[q * N + o]) + cb * (u + dt * l);
+          }
+          bad |= !finite_bits(out);
+          Uout[q * N + o] = out;
+        }
       }
     }
   }
