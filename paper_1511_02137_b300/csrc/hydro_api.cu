@@ -77,7 +77,7 @@ struct hydro_ctx {
   double jt[kMaxJets];
   bool profiling = false;
   Prof prof;
-  CUtensorMap tmaps[3][3];   // [state buffer][sweep axis], valid when tma
+  SweepMaps tmaps[3][3];     // [stage][sweep axis], valid when tma
   bool tma = false;
   void* U(size_t off) { return ws + off; }
   DevDiag* diag() { return reinterpret_cast<DevDiag*>(ws + lay.diag); }
@@ -204,7 +204,8 @@ hydro_status hydro_create(const hydro_config* cfg, hydro_ctx** out) {
     return HYDRO_ECUDA;
   }
   void* bufs[3] = {c->U(c->lay.u0), c->U(c->lay.u1), c->U(c->lay.u2)};
-  c->tma = encode_sweep_tmaps(cfg->precision, cfg->weno_order, bufs, cfg->nx, cfg->ny, cfg->nz, c->tmaps);
+  c->tma = encode_sweep_tmaps(cfg->precision, cfg->weno_order, bufs, c->U(c->lay.rhs), cfg->nx, cfg->ny, cfg->nz,
+                              c->tmaps);
   *out = c;
   return HYDRO_OK;
 }

@@ -126,19 +126,31 @@ int batch_sweep_blocks_per_sm(int precision, int dir, int variant);
 // Zeroes the per-step maximum signal speed of n diagnostics blocks.
 cudaError_t launch_reset_vmax(DevDiag* diags, int n, cudaStream_t s);
 
+// Tensor maps of one sweep launch: `stage` boxes the staged cells of a tile in
+// the state the right-hand side is evaluated on (FP64 and FP32); `rhs`, `u0` and
+// `ust` box the tile's updated cells in the accumulator, the step state and the
+// stage state, the phase-3 operands that FP32-flux (FP32, mixed) y and z sweeps
+// fetch at the start of a tile.
+struct SweepMaps {
+  CUtensorMap stage, rhs, u0, ust;
+};
+
 // Launches one directional sweep (dir 0/1/2) for the given precision
 // (0 FP64, 1 FP32, 2 mixed) and WENO order (7 or 5).
-// tmap (may be NULL): tensor map of a.U for this sweep axis from encode_sweep_tmaps;
-// with it, tiles that need no ghost cells are staged by TMA.
+// maps (may be NULL): the tensor maps of this stage and sweep axis from
+// encode_sweep_tmaps; with them, tiles that need no ghost cells are staged by TMA
+// and the phase-3 operands arrive by TMA.
 cudaError_t launch_sweep(int precision, int order, int dir, const SweepArgs& a, cudaStream_t s,
-                         const CUtensorMap* tmap = nullptr);
+                         const SweepMaps* maps = nullptr);
 
-// Tensor maps of the three state buffers for the three sweep axes (maps[buffer][axis]),
-// for FP64 and FP32 storage with WENO7.  Returns false (and leaves maps unusable) when the
-// grid does not meet the TMA layout rules (row pitch a multiple of 16 bytes) or the
-// driver entry point is missing; callers then stage with plain loads.
-bool encode_sweep_tmaps(int precision, int order, void* const bufs[3], int nx, int ny, int nz,
-                        CUtensorMap maps[3][3]);
+// Tensor maps for the three RK stages and the three sweep axes (maps[stage][axis]);
+// bufs[st] is the state stage st evaluates its right-hand side on (bufs[0] is also
+// the step state U0), rhs the accumulator.  WENO7 only.  Returns false (and leaves
+// maps unusable) when the grid does not meet the TMA layout rules (row pitch a
+// multiple of 16 bytes) or the driver entry point is missing; callers then use
+// plain loads.
+bool encode_sweep_tmaps(int precision, int order, void* const bufs[3], void* rhs, int nx, int ny, int nz,
+                        SweepMaps maps[3][3]);
 
 // Initial state: staging (5N FP64, prim or cons) -> conserved state in storage precision.
 cudaError_t launch_init(int precision, int kind, const double* staging, void* U, size_t n, DevDiag* diag,

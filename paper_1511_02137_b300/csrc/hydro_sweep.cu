@@ -179,21 +179,30 @@ __host__ __device__ constexpr bool tma_staged() {
   return PREC != HYDRO_MIXED;
 }
 
-// Shared memory of one tile, in units of the flux type: U, F_d/2 (5 fields
-// each) and rho_d per staged cell, 5 numerical fluxes per interface, the
-// prefetched phase-3 operands per updated cell, and (FP32 with TMA staging)
-// the staging box of 5 fields per staged cell.
-template <int PREC, int ORDER, int DIR, int SEG, int LANES, bool STAGE = false>
-__host__ __device__ constexpr int tile_smem_words() {
+// Shared memory of one tile, in units of the flux type (word offsets): U, F_d/2
+// (5 fields each) and rho_d per staged cell, 5 numerical fluxes per interface,
+// the prefetched phase-3 operands per updated cell, (FP64 WENO7) the neighbour
+// differences, and (FP32 with TMA staging) the staging box of 5 fields per staged
+// cell.  Areas that a TMA copy writes start on 128-byte boundaries.
+template <int PREC, int ORDER, int DIR, int SEG, int LANES>
+struct TileLayout {
   using F = typename Types<PREC>::Flux;
   using Store = typename Types<PREC>::Store;
-  constexpr int G = (ORDER == 7) ? 4 : 3, NCS = LANES * (SEG + 2 * G), NIF = LANES * (SEG + 1), NC = LANES * SEG;
-  constexpr int delta = (sizeof(F) == 8 && ORDER == 7) ? 10 * NCS : 0;   // FP64 WENO7: neighbour differences
-  constexpr int body = 11 * NCS + 5 * NIF + Prefetch<PREC, DIR>::rhs * NC +
-                       Prefetch<PREC, DIR>::state * NC * (int)(sizeof(Store) / sizeof(F)) + delta;
-  // the staging box starts on a 128-byte boundary
-  constexpr int align = 128 / (int)sizeof(F);
-  return (STAGE && sizeof(F) == 4) ? (body + align - 1) / align * align + 5 * NCS : body;
+  static constexpr int G = (ORDER == 7) ? 4 : 3, NCS = LANES * (SEG + 2 * G), NIF = LANES * (SEG + 1),
+                       NC = LANES * SEG;
+  static constexpr int A = 128 / (int)sizeof(F);   // words per 128 bytes
+  __host__ __device__ static constexpr int up(int w) { return (w + A - 1) / A * A; }
+  static constexpr int pr = up(11 * NCS + 5 * NIF);                      // [5][NC] accumulator
+  static constexpr int p0 = pr + Prefetch<PREC, DIR>::rhs * NC;          // [5][NC] U0 (+ [5][NC] U), Store
+  static constexpr int delta = p0 + Prefetch<PREC, DIR>::state * NC * (int)(sizeof(Store) / sizeof(F));
+  static constexpr int body = delta + ((sizeof(F) == 8 && ORDER == 7) ? 10 * NCS : 0);
+  static constexpr int stage = up(body);
+  __host__ __device__ static constexpr int words(bool stage_box) { return (stage_box && sizeof(F) == 4) ? stage + 5 * NCS : body; }
+};
+
+template <int PREC, int ORDER, int DIR, int SEG, int LANES, bool STAGE = false>
+__host__ __device__ constexpr int tile_smem_words() {
+  return TileLayout<PREC, ORDER, DIR, SEG, LANES>::words(STAGE);
 }
 
 // One tile of a sweep: SEG cells along the sweep axis starting at a0, LANES
@@ -202,8 +211,8 @@ __host__ __device__ constexpr int tile_smem_words() {
 // again when it returns.
 template <int PREC, int ORDER, int DIR, bool FINAL, int SEG, int LANES, bool TMA = false>
 __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& jets, int a0, int l0, int fixed,
-                                           unsigned char* smem_raw, const CUtensorMap* tmap = nullptr,
-                                           uint64_t* bar = nullptr) {
+                                           unsigned char* smem_raw, const SweepMaps* maps = nullptr,
+                                           uint64_t* bar = nullptr, uint64_t* bar_pf = nullptr) {
   using Store = typename Types<PREC>::Store;
   using F = typename Types<PREC>::Flux;
   using Math = typename Types<PREC>::Math;
@@ -239,11 +248,27 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   // ---------------- phase-3 operands, fetched asynchronously
   const Store* __restrict__ U = static_cast<const Store*>(a.U);
   using PF = Prefetch<PREC, DIR>;
-  F* sPr = sH + 5 * NIF;                                 // [5][NC] accumulator
-  Store* sP0 = reinterpret_cast<Store*>(sPr + 5 * NC);   // [5][NC] U0, then (mixed) [5][NC] U
+  using TL = TileLayout<PREC, ORDER, DIR, SEG, LANES>;
+  F* sPr = reinterpret_cast<F*>(smem_raw) + TL::pr;                          // [5][NC] accumulator
+  Store* sP0 = reinterpret_cast<Store*>(reinterpret_cast<F*>(smem_raw) + TL::p0);   // [5][NC] U0, then (mixed) [5][NC] U
   // every tile shape updates one cell per thread (phase 3 and its operands)
   static_assert(NC == kThreads, "one updated cell per thread");
-  if constexpr (PF::on) {
+  if constexpr (PF::on && TMA) {
+    // one thread copies the tile's boxes of cells (the box of an edge tile reaches
+    // past the grid and is filled with zeros there, which phase 3 does not read)
+    if (threadIdx.x == 0) {
+      const bool need_u0 = FINAL && !a.k.first;
+      const unsigned bytes = (unsigned)(5 * NC * sizeof(F) +
+                                        (need_u0 ? 5 * NC * sizeof(Store) : 0) +
+                                        (FINAL && PREC == HYDRO_MIXED ? 5 * NC * sizeof(Store) : 0));
+      mbar_init(bar_pf, 1);
+      mbar_expect_tx(bar_pf, bytes);
+      const int c1 = DIR == 1 ? a0 : fixed, c2 = DIR == 1 ? fixed : a0;
+      tma_load_4d(sPr, &maps->rhs, l0, c1, c2, 0, bar_pf);
+      if (need_u0) tma_load_4d(sP0, &maps->u0, l0, c1, c2, 0, bar_pf);
+      if (FINAL && PREC == HYDRO_MIXED) tma_load_4d(sP0 + 5 * NC, &maps->ust, l0, c1, c2, 0, bar_pf);
+    }
+  } else if constexpr (PF::on) {
     const bool need_u0 = FINAL && !a.k.first;
     const F* rhs_in = static_cast<const F*>(a.rhs);
     const Store* U0_in = static_cast<const Store*>(a.U0);
@@ -290,18 +315,17 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   // ---------------- phase 1: stage cells, primitives, half fluxes, rho
   // a tile whose halo lies inside the grid needs no ghost cells: one TMA box of all 5 fields
   bool staged = false;
-  constexpr int kStageOff = tile_smem_words<PREC, ORDER, DIR, SEG, LANES, TMA>() - 5 * NCS;
-  F* sStage = IL ? reinterpret_cast<F*>(smem_raw) + kStageOff : sU;   // [5][NCS] U as copied
-  if constexpr (TMA) {
+  F* sStage = IL ? reinterpret_cast<F*>(smem_raw) + TL::stage : sU;   // [5][NCS] U as copied
+  if constexpr (TMA && PREC != HYDRO_MIXED) {
     static_assert(sizeof(Store) == sizeof(F), "TMA staging copies the stored type into the flux-type tile");
     if (a0 - G >= 0 && a0 + SEG + G <= n_along && l0 + LANES <= n_lane) {
       if (threadIdx.x == 0) mbar_init(bar, 1);
       __syncthreads();
       if (threadIdx.x == 0) {
         mbar_expect_tx(bar, (unsigned)(5 * NCS * sizeof(Store)));
-        if (DIR == 0) tma_load_4d(sStage, tmap, a0 - G, l0, fixed, 0, bar);
-        else if (DIR == 1) tma_load_4d(sStage, tmap, l0, a0 - G, fixed, 0, bar);
-        else tma_load_4d(sStage, tmap, l0, fixed, a0 - G, 0, bar);
+        if (DIR == 0) tma_load_4d(sStage, &maps->stage, a0 - G, l0, fixed, 0, bar);
+        else if (DIR == 1) tma_load_4d(sStage, &maps->stage, l0, a0 - G, fixed, 0, bar);
+        else tma_load_4d(sStage, &maps->stage, l0, fixed, a0 - G, 0, bar);
       }
       if (!mbar_wait_bounded(bar, 0)) atomicCAS(&a.diag->status, 0, (int)HYDRO_ETIMEOUT);
       staged = true;
@@ -369,8 +393,8 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   // per cell pair; each interface then forms its split-flux differences with one
   // FMA apiece instead of splitting 8 cells and differencing per interface.
   constexpr bool DELTA = sizeof(F) == 8 && ORDER == 7;
-  F* sDU = sH + 5 * NIF + PF::rhs * NC + PF::state * NC * (int)(sizeof(Store) / sizeof(F));   // [5][NCS] U(c+1) - U(c)
-  F* sDF = sDU + 5 * NCS;                                                                     // [5][NCS] F(c+1) - F(c)
+  F* sDU = reinterpret_cast<F*>(smem_raw) + TL::delta;   // [5][NCS] U(c+1) - U(c)
+  F* sDF = sDU + 5 * NCS;                                 // [5][NCS] F(c+1) - F(c)
   if constexpr (DELTA) {
     for (int c = threadIdx.x; c < NCS; c += kThreads) {
       int lane, s;
@@ -460,7 +484,11 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   F* __restrict__ rhs = static_cast<F*>(a.rhs);
   const F inv_dx = kconst<F>(a.inv_dx, a.k.inv_dx_f);
   bool bad = false;
-  if constexpr (PF::on) cp_async_wait_all();   // each thread reads only its own copies
+  if constexpr (PF::on && TMA) {
+    if (!mbar_wait_bounded(bar_pf, 0)) atomicCAS(&a.diag->status, 0, (int)HYDRO_ETIMEOUT);
+  } else if constexpr (PF::on) {
+    cp_async_wait_all();   // each thread reads only its own copies
+  }
   {
     const int c = threadIdx.x;
     int lane, j;
@@ -541,9 +569,9 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
 }
 
 template <int PREC, int ORDER, int DIR, bool FINAL, bool TMA>
-__global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a, const __grid_constant__ CUtensorMap tmap) {
+__global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a, const __grid_constant__ SweepMaps maps) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t bar, bar_pf;
   constexpr int SEG = Tile<PREC, DIR>::SEG, LANES = Tile<PREC, DIR>::LANES;
   int a0, l0;
   if (DIR == 0) {
@@ -551,7 +579,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a, cons
   } else {
     l0 = blockIdx.x * LANES; a0 = blockIdx.y * SEG;
   }
-  sweep_tile<PREC, ORDER, DIR, FINAL, SEG, LANES, TMA>(a, a.jets, a0, l0, blockIdx.z, smem_raw, &tmap, &bar);
+  sweep_tile<PREC, ORDER, DIR, FINAL, SEG, LANES, TMA>(a, a.jets, a0, l0, blockIdx.z, smem_raw, &maps, &bar, &bar_pf);
 }
 
 // Batched sweep: a persistent grid walks the tile list of all grids of the
@@ -595,34 +623,36 @@ __global__ void reset_vmax_kernel(DevDiag* d, int n) {
 }
 
 template <int PREC, int ORDER, int DIR>
-static cudaError_t launch_one(const SweepArgs& a, cudaStream_t s, const CUtensorMap* tmap) {
+static cudaError_t launch_one(const SweepArgs& a, cudaStream_t s, const SweepMaps* maps) {
   using F = typename Types<PREC>::Flux;
   constexpr int SEG = Tile<PREC, DIR>::SEG, LANES = Tile<PREC, DIR>::LANES;
-  constexpr bool kTmaCapable = ORDER == 7 && tma_staged<PREC>();
+  // tensor maps serve the staging copy (FP64, FP32) and the phase-3 operands (FP32, mixed y and z)
+  constexpr bool kStage = ORDER == 7 && tma_staged<PREC>();
+  constexpr bool kMapsUsed = kStage || (ORDER == 7 && Prefetch<PREC, DIR>::on);
   constexpr size_t smem = sizeof(F) * (size_t)tile_smem_words<PREC, ORDER, DIR, SEG, LANES>();
-  constexpr size_t smem_tma = sizeof(F) * (size_t)tile_smem_words<PREC, ORDER, DIR, SEG, LANES, kTmaCapable>();
+  constexpr size_t smem_tma = sizeof(F) * (size_t)tile_smem_words<PREC, ORDER, DIR, SEG, LANES, kStage>();
   dim3 grid;
   if (DIR == 0) grid = dim3((a.nx + SEG - 1) / SEG, (a.ny + LANES - 1) / LANES, a.nz);
   else if (DIR == 1) grid = dim3((a.nx + LANES - 1) / LANES, (a.ny + SEG - 1) / SEG, a.nz);
   else grid = dim3((a.nx + LANES - 1) / LANES, (a.nz + SEG - 1) / SEG, a.ny);
-  if (kTmaCapable && tmap) {
-    auto kern = sweep_kernel<PREC, ORDER, DIR, DIR == 2, kTmaCapable>;
+  if (kMapsUsed && maps) {
+    auto kern = sweep_kernel<PREC, ORDER, DIR, DIR == 2, kMapsUsed>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tma);
     if (err != cudaSuccess) return err;
-    kern<<<grid, kThreads, smem_tma, s>>>(a, *tmap);
+    kern<<<grid, kThreads, smem_tma, s>>>(a, *maps);
     return cudaGetLastError();
   }
   auto kern = sweep_kernel<PREC, ORDER, DIR, DIR == 2, false>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  CUtensorMap none;
+  SweepMaps none;
   memset(&none, 0, sizeof(none));
   kern<<<grid, kThreads, smem, s>>>(a, none);
   return cudaGetLastError();
 }
 
 template <int PREC, int ORDER>
-static cudaError_t launch_dir(int dir, const SweepArgs& a, cudaStream_t s, const CUtensorMap* t) {
+static cudaError_t launch_dir(int dir, const SweepArgs& a, cudaStream_t s, const SweepMaps* t) {
   switch (dir) {
     case 0: return launch_one<PREC, ORDER, 0>(a, s, t);
     case 1: return launch_one<PREC, ORDER, 1>(a, s, t);
@@ -631,7 +661,7 @@ static cudaError_t launch_dir(int dir, const SweepArgs& a, cudaStream_t s, const
 }
 
 template <int PREC>
-static cudaError_t launch_order(int order, int dir, const SweepArgs& a, cudaStream_t s, const CUtensorMap* t) {
+static cudaError_t launch_order(int order, int dir, const SweepArgs& a, cudaStream_t s, const SweepMaps* t) {
   return order == 5 ? launch_dir<PREC, 5>(dir, a, s, t) : launch_dir<PREC, 7>(dir, a, s, t);
 }
 
@@ -651,7 +681,7 @@ LaunchConst derive_constants(const GridArgs& g, int order) {
 }
 
 cudaError_t launch_sweep(int precision, int order, int dir, const SweepArgs& args, cudaStream_t s,
-                         const CUtensorMap* tmap) {
+                         const SweepMaps* tmap) {
   SweepArgs a = args;
   a.k = derive_constants(a, order);
   switch (precision) {
@@ -663,23 +693,12 @@ cudaError_t launch_sweep(int precision, int order, int dir, const SweepArgs& arg
 
 // ---------------------------------------------------------------- tensor maps
 
-template <int PREC, int DIR>
-static void tma_box(cuuint32_t box[4]) {
-  constexpr int SEG = Tile<PREC, DIR>::SEG, LANES = Tile<PREC, DIR>::LANES, W = SEG + 8;
-  box[3] = 5;
-  if (DIR == 0) { box[0] = W; box[1] = LANES; box[2] = 1; }
-  else if (DIR == 1) { box[0] = LANES; box[1] = W; box[2] = 1; }
-  else { box[0] = LANES; box[1] = 1; box[2] = W; }
-}
 
-bool encode_sweep_tmaps(int precision, int order, void* const bufs[3], int nx, int ny, int nz,
-                        CUtensorMap maps[3][3]) {
-  if (precision == HYDRO_MIXED || order != 7) return false;
-  const size_t es = precision == HYDRO_FP32 ? 4 : 8;
-  const cuuint64_t dim[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, 5};
-  const cuuint64_t stride[3] = {(cuuint64_t)nx * es, (cuuint64_t)nx * ny * es, (cuuint64_t)nx * ny * nz * es};
-  for (int k = 0; k < 3; ++k)
-    if (stride[k] % 16 != 0) return false;
+bool encode_sweep_tmaps(int precision, int order, void* const bufs[3], void* rhs, int nx, int ny, int nz,
+                        SweepMaps maps[3][3]) {
+  if (order != 7) return false;
+  const size_t es = precision == HYDRO_FP64 ? 8 : (precision == HYDRO_FP32 ? 4 : 8);   // stored type
+  const size_t fs = precision == HYDRO_FP64 ? 8 : 4;                                   // flux type
   void* fn = nullptr;
   cudaDriverEntryPointQueryResult q;
   if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
@@ -691,22 +710,45 @@ bool encode_sweep_tmaps(int precision, int order, void* const bufs[3], int nx, i
                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
   Encode encode = reinterpret_cast<Encode>(fn);
-  const CUtensorMapDataType dt = precision == HYDRO_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                                         : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
-  const cuuint32_t estr[4] = {1, 1, 1, 1};
-  for (int b = 0; b < 3; ++b)
+  // a 4-D (x, y, z, field) map of one 5-field array with elements of `size` bytes
+  auto enc = [&](CUtensorMap* m, void* base, size_t size, const cuuint32_t box[4]) {
+    const cuuint64_t dim[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, 5};
+    const cuuint64_t stride[3] = {(cuuint64_t)nx * size, (cuuint64_t)nx * ny * size, (cuuint64_t)nx * ny * nz * size};
+    for (int k = 0; k < 3; ++k)
+      if (stride[k] % 16 != 0) return false;
+    if ((box[0] * size) % 16 != 0) return false;
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUtensorMapDataType dt = size == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    return encode(m, dt, 4, base, dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  };
+  // box of a tile's staged cells (W = SEG + 8 along the axis) or updated cells (SEG)
+  auto box_of = [&](int d, int lanes, int along, cuuint32_t box[4]) {
+    box[3] = 5;
+    if (d == 0) { box[0] = along; box[1] = lanes; box[2] = 1; }
+    else if (d == 1) { box[0] = lanes; box[1] = along; box[2] = 1; }
+    else { box[0] = lanes; box[1] = 1; box[2] = along; }
+  };
+  std::memset(maps, 0, 9 * sizeof(SweepMaps));
+  for (int st = 0; st < 3; ++st)
     for (int d = 0; d < 3; ++d) {
+      // tile shapes: Tile<> (FP64 x tiles are 64 x 4, every other tile 32 x 8)
+      const bool wide = precision == HYDRO_FP64 && d == 0;
+      const int seg = wide ? Tile<HYDRO_FP64, 0>::SEG : Tile<HYDRO_FP32, 1>::SEG;
+      const int lanes = wide ? Tile<HYDRO_FP64, 0>::LANES : Tile<HYDRO_FP32, 1>::LANES;
       cuuint32_t box[4];
-      if (precision == HYDRO_FP32) {
-        if (d == 0) tma_box<HYDRO_FP32, 0>(box); else if (d == 1) tma_box<HYDRO_FP32, 1>(box); else tma_box<HYDRO_FP32, 2>(box);
-      } else {
-        if (d == 0) tma_box<HYDRO_FP64, 0>(box); else if (d == 1) tma_box<HYDRO_FP64, 1>(box); else tma_box<HYDRO_FP64, 2>(box);
+      if (precision != HYDRO_MIXED) {   // staging box of the stage state
+        box_of(d, lanes, seg + 8, box);
+        if (!enc(&maps[st][d].stage, bufs[st], es, box)) return false;
       }
-      if ((box[0] * es) % 16 != 0) return false;
-      if (encode(&maps[b][d], dt, 4, bufs[b], dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                 CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return false;
+      if (precision != HYDRO_FP64 && d != 0) {   // phase-3 operand boxes
+        box_of(d, lanes, seg, box);
+        if (!enc(&maps[st][d].rhs, rhs, fs, box)) return false;
+        if (d == 2) {
+          if (!enc(&maps[st][d].u0, bufs[0], es, box)) return false;
+          if (precision == HYDRO_MIXED && !enc(&maps[st][d].ust, bufs[st], es, box)) return false;
+        }
+      }
     }
   return true;
 }
