@@ -129,8 +129,8 @@ cudaError_t launch_reset_vmax(DevDiag* diags, int n, cudaStream_t s);
 // Tensor maps of one sweep launch: `stage` boxes the staged cells of a tile in
 // the state the right-hand side is evaluated on (FP64 and FP32); `rhs`, `u0` and
 // `ust` box the tile's updated cells in the accumulator, the step state and the
-// stage state, the phase-3 operands that FP32-flux (FP32, mixed) y and z sweeps
-// fetch at the start of a tile.
+// stage state.  FP32-flux (FP32, mixed) sweeps fetch their phase-3 operands
+// through them (y and z) and store their accumulator values through `rhs` (x, y).
 struct SweepMaps {
   CUtensorMap stage, rhs, u0, ust;
 };
