@@ -93,22 +93,24 @@ __device__ __forceinline__ void cons_to_prim(typename M::T E, typename M::T Mx, 
 //   1 - m v = (1 - v) + v om,  with s = sqrt(4 - 3m^2).
 // FP64 <-> FP32 conversions on the integer pipe, from the IEEE 754 binary64 and
 // binary32 layouts (B300 runs the hardware conversions at the FP64 rate, 1/64 of
-// FP32, and the mixed sweeps convert every staged value).  d2f_rn rounds to
+// FP32; the mixed z sweep, whose FP64 pipe also forms the stage combination, and
+// the adjoint's elementwise kernels convert with these).  d2f_rn rounds to
 // nearest even; results below the FP32 normal range flush to signed zero, above
 // it become infinity, NaN stays NaN.  f2d is exact for normal FP32 values and
 // zero; FP32 subnormals flush to signed zero.
 __device__ __forceinline__ float d2f_rn(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
-  const unsigned sign = hi & 0x80000000u;
-  const int ex = (int)((hi >> 20) & 0x7ffu) - 896;            // binary32 biased exponent
-  unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);             // top 23 of the 52 fraction bits
-  const unsigned rem = lo & 0x1fffffffu, half = 0x10000000u;    // the 29 bits dropped
-  m += (rem > half || (rem == half && (m & 1u))) ? 1u : 0u;     // a carry lands in the exponent
-  unsigned r = sign | (((unsigned)ex << 23) + m);
-  if (ex <= 0) r = sign;
-  if (ex >= 255) r = sign | 0x7f800000u | ((((hi & 0xfffffu) | lo) != 0u && ex == 1151) ? 0x400000u : 0u);
-  return __uint_as_float(r);
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned hb = hi & 0x7fffffffu;
+  // biased binary32 exponent and the top 23 fraction bits, then round to nearest
+  // even on the 29 dropped bits (a carry lands in the exponent, up to infinity)
+  unsigned t = __funnelshift_l(lo, hb - (896u << 20), 3);
+  t += ((lo & 0x1fffffffu) + (t & 1u) + 0x0fffffffu) >> 29;
+  if (hb - (897u << 20) >= (254u << 20)) {   // outside the binary32 normal range (rare)
+    if (hb < (897u << 20)) t = 0u;                                   // flush to zero
+    else if (hb > 0x7ff00000u || (hb == 0x7ff00000u && lo != 0u)) t = 0x7fc00000u;   // NaN
+    else t = 0x7f800000u;                                            // overflow, infinity
+  }
+  return __uint_as_float(t | (hi & 0x80000000u));
 }
 
 // Finite test of a double on the integer pipe (exponent field not all ones).

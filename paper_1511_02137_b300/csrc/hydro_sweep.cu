@@ -366,7 +366,14 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
     F e, vx, vy, vz, E, Mx, My, Mz, R;
     int hit = 0;
     if constexpr (PREC == HYDRO_MIXED) {
-      E = d2f_rn(Es); Mx = d2f_rn(Mxs); My = d2f_rn(Mys); Mz = d2f_rn(Mzs); R = d2f_rn(Rs);
+      // the x and y sweeps have FP64-pipe time to spare (E^2 - |M|^2 is their only
+      // FP64 arithmetic) and convert in hardware; the z sweep's FP64 pipe also
+      // carries the stage combination, so it converts on the integer pipe
+      if constexpr (DIR == 2) {
+        E = d2f_rn(Es); Mx = d2f_rn(Mxs); My = d2f_rn(Mys); Mz = d2f_rn(Mzs); R = d2f_rn(Rs);
+      } else {
+        E = (float)Es; Mx = (float)Mxs; My = (float)Mys; Mz = (float)Mzs; R = (float)Rs;
+      }
       cons_to_prim_mixed_f(Es, Mxs, Mys, Mzs, E, Mx, My, Mz, a.e_floor, e, vx, vy, vz, hit);
     } else {
       cons_to_prim<Math>(Es, Mxs, Mys, Mzs, kconst<F>(a.e_floor, a.k.e_floor_f), e, vx, vy, vz, hit);
