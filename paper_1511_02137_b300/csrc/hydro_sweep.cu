@@ -741,6 +741,19 @@ cudaError_t launch_sweep(int precision, int order, int dir, const SweepArgs& arg
 // ---------------------------------------------------------------- tensor maps
 
 
+// The tile shape of a single-grid sweep (Tile<PREC, DIR>) at run time.
+static void tile_shape(int precision, int d, int& seg, int& lanes) {
+  auto pick = [&](auto prec_tag) {
+    constexpr int P = decltype(prec_tag)::value;
+    if (d == 0) { seg = Tile<P, 0>::SEG; lanes = Tile<P, 0>::LANES; }
+    else if (d == 1) { seg = Tile<P, 1>::SEG; lanes = Tile<P, 1>::LANES; }
+    else { seg = Tile<P, 2>::SEG; lanes = Tile<P, 2>::LANES; }
+  };
+  if (precision == HYDRO_FP64) pick(std::integral_constant<int, HYDRO_FP64>());
+  else if (precision == HYDRO_FP32) pick(std::integral_constant<int, HYDRO_FP32>());
+  else pick(std::integral_constant<int, HYDRO_MIXED>());
+}
+
 bool encode_sweep_tmaps(int precision, int order, void* const bufs[3], void* rhs, int nx, int ny, int nz,
                         SweepMaps maps[3][3]) {
   if (order != 7) return false;
@@ -779,10 +792,8 @@ bool encode_sweep_tmaps(int precision, int order, void* const bufs[3], void* rhs
   std::memset(maps, 0, 9 * sizeof(SweepMaps));
   for (int st = 0; st < 3; ++st)
     for (int d = 0; d < 3; ++d) {
-      // tile shapes: Tile<> (FP64 x tiles are 64 x 4, every other tile 32 x 8)
-      const bool wide = precision == HYDRO_FP64 && d == 0;
-      const int seg = wide ? Tile<HYDRO_FP64, 0>::SEG : Tile<HYDRO_FP32, 1>::SEG;
-      const int lanes = wide ? Tile<HYDRO_FP64, 0>::LANES : Tile<HYDRO_FP32, 1>::LANES;
+      int seg, lanes;
+      tile_shape(precision, d, seg, lanes);
       cuuint32_t box[4];
       if (precision != HYDRO_MIXED) {   // staging box of the stage state
         box_of(d, lanes, seg + 8, box);
