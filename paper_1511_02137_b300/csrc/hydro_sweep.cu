@@ -628,37 +628,61 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a, cons
   sweep_tile<PREC, ORDER, DIR, FINAL, SEG, LANES, TMA>(a, a.jets, a0, l0, blockIdx.z, smem_raw, &maps, &bar, &bar_pf);
 }
 
+// Resident blocks per SM the batched kernels' register budget is held to: six
+// FP32-flux blocks (40 registers, as the single-grid sweeps), three FP64 blocks
+// (their shared memory admits no more).
+template <int PREC>
+__host__ __device__ constexpr int batch_min_blocks() { return PREC == HYDRO_FP64 ? 3 : 6; }
+
 // Batched sweep: a persistent grid walks the tile list of all grids of the
 // ensemble; each tile finds its grid's size and field offset in the event table.
 template <int PREC, int DIR, bool FINAL, int SEG, int LANES>
-__global__ void __launch_bounds__(kThreads) batch_sweep_kernel(const BatchArgs b) {
+__global__ void __launch_bounds__(kThreads, batch_min_blocks<PREC>()) batch_sweep_kernel(const BatchArgs b) {
   using Store = typename Types<PREC>::Store;
   using F = typename Types<PREC>::Flux;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
-    const int4 td = b.tiles[t];
-    const BatchEvent ev = b.events[td.x];
-    GridArgs g;
-    g.U = static_cast<const Store*>(b.U) + ev.off;
-    g.U0 = static_cast<const Store*>(b.U0) + ev.off;
-    g.Uout = static_cast<Store*>(b.Uout) + ev.off;
-    g.rhs = static_cast<F*>(b.rhs) + ev.off;
-    g.diag = b.diags + td.x;
-    g.nx = ev.nx;
-    g.ny = ev.ny;
-    g.nz = ev.nz;
-    g.periodic = b.periodic;
-    g.inv_dx = b.inv_dx;
-    g.dt = b.dt;
-    g.a = b.a;
-    g.b = b.b;
-    g.e_floor = b.e_floor;
-    g.eps = b.eps;
-    g.reduce_speed = b.reduce_speed;
-    g.count_floors = b.count_floors;
-    g.src = b.src;
-    g.k = b.k;
-    sweep_tile<PREC, 7, DIR, FINAL, SEG, LANES>(g, b.jets[td.x], td.y, td.z, td.w, smem_raw);
+  // the tile's grid arguments live in shared memory (one thread fills them): held in
+  // registers across the tile they would cost the persistent kernel occupancy
+  __shared__ GridArgs g;
+  __shared__ __align__(16) int4 tdq[2];   // this tile's descriptor and the next one's, copied ahead
+  __shared__ int4 td;
+  if (threadIdx.x == 0 && blockIdx.x < b.ntiles) {
+    cp_async_ca<16>(&tdq[0], &b.tiles[blockIdx.x]);
+    cp_async_commit();
+  }
+  int slot = 0;
+  for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x, slot ^= 1) {
+    if (threadIdx.x == 0) {
+      cp_async_wait_all();   // this tile's descriptor (copied during the previous tile)
+      if (t + (int)gridDim.x < b.ntiles) {
+        cp_async_ca<16>(&tdq[slot ^ 1], &b.tiles[t + gridDim.x]);
+        cp_async_commit();
+      }
+      td = tdq[slot];
+      const BatchEvent ev = b.events[td.x];
+      g.U = static_cast<const Store*>(b.U) + ev.off;
+      g.U0 = static_cast<const Store*>(b.U0) + ev.off;
+      g.Uout = static_cast<Store*>(b.Uout) + ev.off;
+      g.rhs = static_cast<F*>(b.rhs) + ev.off;
+      g.diag = b.diags + td.x;
+      g.nx = ev.nx;
+      g.ny = ev.ny;
+      g.nz = ev.nz;
+      g.periodic = b.periodic;
+      g.inv_dx = b.inv_dx;
+      g.dt = b.dt;
+      g.a = b.a;
+      g.b = b.b;
+      g.e_floor = b.e_floor;
+      g.eps = b.eps;
+      g.reduce_speed = b.reduce_speed;
+      g.count_floors = b.count_floors;
+      g.src = b.src;
+      g.k = b.k;
+    }
+    __syncthreads();
+    const int4 tile = td;
+    sweep_tile<PREC, 7, DIR, FINAL, SEG, LANES>(g, b.jets[tile.x], tile.y, tile.z, tile.w, smem_raw);
     __syncthreads();   // the next tile overwrites shared memory
   }
 }
