@@ -78,7 +78,7 @@ size_t max_tiles(int32_t nev, const int32_t* dims, int dir) {
 
 struct BLayout {
   size_t cells = 0;
-  size_t u0 = 0, u1 = 0, u2 = 0, rhs = 0, diags = 0, events = 0, tiles[3] = {0, 0, 0}, jets = 0, total = 0;
+  size_t u0 = 0, u1 = 0, u2 = 0, rhs = 0, diags = 0, events = 0, tiles[3] = {0, 0, 0}, jets = 0, maps = 0, total = 0;
   size_t tile_cap[3] = {0, 0, 0};
 };
 
@@ -100,6 +100,8 @@ BLayout layout_for(const hydro_config& c, int32_t nev, const int32_t* dims) {
   }
   L.jets = off;
   off += align_up((size_t)kJetChunk * 3 * nev * sizeof(JetStage));
+  L.maps = off;   // tensor maps [stage][axis][event]
+  off += align_up((size_t)9 * nev * sizeof(SweepMaps));
   L.total = off;
   return L;
 }
@@ -124,6 +126,7 @@ struct hydro_batch {
   int variant[3] = {0, 0, 0};
   int ntiles[3] = {0, 0, 0};
   int grid[3] = {0, 0, 0};
+  bool tma = false;   // tensor maps of the current tile shapes are uploaded
   std::vector<std::vector<HostJet>> jets;
   std::vector<char> initialized;
   int64_t steps = 0;
@@ -145,8 +148,20 @@ void drop_graph(hydro_batch* b) {
   b->exec_steps = 0;
 }
 
-// Uploads the tile list of the current variants and sizes the persistent grids.
+// Uploads the tile list and the tensor maps of the current variants and sizes the
+// persistent grids.
 hydro_status set_tiles(hydro_batch* b) {
+  {
+    std::vector<SweepMaps> maps((size_t)9 * b->nev);
+    void* bufs[3] = {b->at(b->lay.u0), b->at(b->lay.u1), b->at(b->lay.u2)};
+    b->tma = encode_batch_tmaps(b->cfg.precision, bufs, b->at(b->lay.rhs), b->nev, b->dims.data(), b->off.data(),
+                                b->variant, maps.data());
+    if (b->tma && cudaMemcpyAsync(b->at(b->lay.maps), maps.data(), maps.size() * sizeof(SweepMaps),
+                                  cudaMemcpyHostToDevice, b->cs) != cudaSuccess)
+      return HYDRO_ECUDA;
+    // the host copy must outlive the asynchronous copy
+    if (cudaStreamSynchronize(b->cs) != cudaSuccess) return HYDRO_ECUDA;
+  }
   for (int d = 0; d < 3; ++d) {
     std::vector<int4> t;
     for (int e = 0; e < b->nev; ++e)
@@ -156,7 +171,7 @@ hydro_status set_tiles(hydro_batch* b) {
         cudaSuccess)
       return HYDRO_ECUDA;
     b->ntiles[d] = (int)t.size();
-    const int per_sm = batch_sweep_blocks_per_sm(b->cfg.precision, d, b->variant[d]);
+    const int per_sm = batch_sweep_blocks_per_sm(b->cfg.precision, d, b->variant[d], b->tma);
     if (per_sm <= 0) return HYDRO_ECUDA;
     b->grid[d] = std::min<long long>((long long)per_sm * b->sms, (long long)b->ntiles[d]);
   }
@@ -232,6 +247,8 @@ cudaError_t issue_steps(hydro_batch* b, int n) {
       a.reduce_speed = st == 0;
       for (int d = 0; d < 3 && err == cudaSuccess; ++d) {
         a.tiles = reinterpret_cast<const int4*>(b->at(b->lay.tiles[d]));
+        a.maps = b->tma ? reinterpret_cast<const SweepMaps*>(b->at(b->lay.maps)) + (size_t)(st * 3 + d) * b->nev
+                        : nullptr;
         a.ntiles = b->ntiles[d];
         a.count_floors = d == 0;
         err = launch_batch_sweep(b->cfg.precision, d, b->variant[d], a, b->grid[d], b->cs);
@@ -394,6 +411,8 @@ hydro_status hydro_batch_autotune(hydro_batch* b, int32_t variant_out[3], double
       if (status != HYDRO_OK) break;
       a.tiles = reinterpret_cast<const int4*>(b->at(b->lay.tiles[d]));
       a.ntiles = b->ntiles[d];
+      // stage 1 of a step: the maps of stage 0 for this axis
+      a.maps = b->tma ? reinterpret_cast<const SweepMaps*>(b->at(b->lay.maps)) + (size_t)d * b->nev : nullptr;
       double ms_min = 1e300;
       for (int rep = 0; rep < 3; ++rep) {
         cudaEventRecord(e0, b->cs);

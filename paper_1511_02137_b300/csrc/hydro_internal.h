@@ -93,6 +93,8 @@ struct BatchEvent {
   size_t off;       // element offset of the grid's 5 fields in every state array
 };
 
+struct SweepMaps;
+
 // Arguments of a batched (persistent) sweep launch: one launch covers every
 // tile of every grid; tiles are (event, a0, l0, fixed).
 struct BatchArgs {
@@ -110,6 +112,7 @@ struct BatchArgs {
   int reduce_speed, count_floors;
   SourceCoef src;
   LaunchConst k;    // filled by launch_batch_sweep
+  const SweepMaps* maps;   // [nev] tensor maps of this launch's stage and axis, or NULL (plain loads)
 };
 
 // Tile shapes the batched sweeps can use (index = autotuner choice):
@@ -121,8 +124,16 @@ constexpr int kTileSegYZ[kBatchVariants] = {32, 16, 64};
 constexpr int kTileLanesYZ[kBatchVariants] = {8, 16, 4};
 
 cudaError_t launch_batch_sweep(int precision, int dir, int variant, const BatchArgs& a, int grid, cudaStream_t s);
-// Blocks per SM the batched sweep kernel reaches (0 on error).
-int batch_sweep_blocks_per_sm(int precision, int dir, int variant);
+// Blocks per SM the batched sweep kernel (with or without tensor maps) reaches (0 on error).
+int batch_sweep_blocks_per_sm(int precision, int dir, int variant, bool tma);
+
+// Tensor maps of a batched ensemble, maps[(stage * 3 + axis) * nev + event], for the tile
+// shapes variant[axis]; bufs[st] are the concatenated state arrays, rhs the accumulator,
+// off[e] the element offset of event e's fields.  False when a grid misses the TMA
+// layout rules (row pitch and field offset multiples of 16 bytes); callers then launch
+// the plain-load kernels.
+bool encode_batch_tmaps(int precision, void* const bufs[3], void* rhs, int nev, const int32_t* dims,
+                        const size_t* off, const int variant[3], SweepMaps* maps);
 // Zeroes the per-step maximum signal speed of n diagnostics blocks.
 cudaError_t launch_reset_vmax(DevDiag* diags, int n, cudaStream_t s);
 

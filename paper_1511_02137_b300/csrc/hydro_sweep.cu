@@ -225,10 +225,31 @@ __host__ __device__ constexpr int tile_smem_words() {
 // lines starting at l0, in plane `fixed` (z for the x and y sweeps, y for the z
 // sweep).  Must be reached by every thread of the block; shared memory is free
 // again when it returns.
+// The two mbarriers of a block's TMA copies (staging box, phase-3 operands),
+// initialised once per block, and the parity of the next phase of each; every
+// thread of the block keeps the same copy of the parities.
+struct TileBars {
+  uint64_t* stage;
+  uint64_t* pf;
+  unsigned ph_stage, ph_pf;
+};
+
+// Initialises the block's mbarriers (one arrival each: the thread that issues the
+// copies).  Must be reached by every thread of the block.
+__device__ __forceinline__ void init_tile_bars(TileBars& tb) {
+  if (threadIdx.x == 0) {
+    mbar_init(tb.stage, 1);
+    mbar_init(tb.pf, 1);
+  }
+  __syncthreads();
+  tb.ph_stage = 0;
+  tb.ph_pf = 0;
+}
+
 template <int PREC, int ORDER, int DIR, bool FINAL, int SEG, int LANES, bool TMA = false>
 __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& jets, int a0, int l0, int fixed,
                                            unsigned char* smem_raw, const SweepMaps* maps = nullptr,
-                                           uint64_t* bar = nullptr, uint64_t* bar_pf = nullptr) {
+                                           TileBars* tb = nullptr) {
   using Store = typename Types<PREC>::Store;
   using F = typename Types<PREC>::Flux;
   using Math = typename Types<PREC>::Math;
@@ -277,12 +298,11 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
       const unsigned bytes = (unsigned)(5 * NC * sizeof(F) +
                                         (need_u0 ? 5 * NC * sizeof(Store) : 0) +
                                         (FINAL && PREC == HYDRO_MIXED ? 5 * NC * sizeof(Store) : 0));
-      mbar_init(bar_pf, 1);
-      mbar_expect_tx(bar_pf, bytes);
+      mbar_expect_tx(tb->pf, bytes);
       const int c1 = DIR == 1 ? a0 : fixed, c2 = DIR == 1 ? fixed : a0;
-      tma_load_4d(sPr, &maps->rhs, l0, c1, c2, 0, bar_pf);
-      if (need_u0) tma_load_4d(sP0, &maps->u0, l0, c1, c2, 0, bar_pf);
-      if (FINAL && PREC == HYDRO_MIXED) tma_load_4d(sP0 + 5 * NC, &maps->ust, l0, c1, c2, 0, bar_pf);
+      tma_load_4d(sPr, &maps->rhs, l0, c1, c2, 0, tb->pf);
+      if (need_u0) tma_load_4d(sP0, &maps->u0, l0, c1, c2, 0, tb->pf);
+      if (FINAL && PREC == HYDRO_MIXED) tma_load_4d(sP0 + 5 * NC, &maps->ust, l0, c1, c2, 0, tb->pf);
     }
   } else if constexpr (PF::on) {
     const bool need_u0 = FINAL && !a.k.first;
@@ -335,15 +355,14 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   if constexpr (TMA && PREC != HYDRO_MIXED) {
     static_assert(sizeof(Store) == sizeof(F), "TMA staging copies the stored type into the flux-type tile");
     if (a0 - G >= 0 && a0 + SEG + G <= n_along && l0 + LANES <= n_lane) {
-      if (threadIdx.x == 0) mbar_init(bar, 1);
-      __syncthreads();
       if (threadIdx.x == 0) {
-        mbar_expect_tx(bar, (unsigned)(5 * NCS * sizeof(Store)));
-        if (DIR == 0) tma_load_4d(sStage, &maps->stage, a0 - G, l0, fixed, 0, bar);
-        else if (DIR == 1) tma_load_4d(sStage, &maps->stage, l0, a0 - G, fixed, 0, bar);
-        else tma_load_4d(sStage, &maps->stage, l0, fixed, a0 - G, 0, bar);
+        mbar_expect_tx(tb->stage, (unsigned)(5 * NCS * sizeof(Store)));
+        if (DIR == 0) tma_load_4d(sStage, &maps->stage, a0 - G, l0, fixed, 0, tb->stage);
+        else if (DIR == 1) tma_load_4d(sStage, &maps->stage, l0, a0 - G, fixed, 0, tb->stage);
+        else tma_load_4d(sStage, &maps->stage, l0, fixed, a0 - G, 0, tb->stage);
       }
-      if (!mbar_wait_bounded(bar, 0)) atomicCAS(&a.diag->status, 0, (int)HYDRO_ETIMEOUT);
+      if (!mbar_wait_bounded(tb->stage, tb->ph_stage)) atomicCAS(&a.diag->status, 0, (int)HYDRO_ETIMEOUT);
+      tb->ph_stage ^= 1u;
       staged = true;
     }
   }
@@ -515,7 +534,8 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   const F inv_dx = kconst<F>(a.inv_dx, a.k.inv_dx_f);
   bool bad = false;
   if constexpr (PF::on && TMA) {
-    if (!mbar_wait_bounded(bar_pf, 0)) atomicCAS(&a.diag->status, 0, (int)HYDRO_ETIMEOUT);
+    if (!mbar_wait_bounded(tb->pf, tb->ph_pf)) atomicCAS(&a.diag->status, 0, (int)HYDRO_ETIMEOUT);
+    tb->ph_pf ^= 1u;
   } else if constexpr (PF::on) {
     cp_async_wait_all();   // each thread reads only its own copies
   }
@@ -618,6 +638,8 @@ template <int PREC, int ORDER, int DIR, bool FINAL, bool TMA>
 __global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a, const __grid_constant__ SweepMaps maps) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar, bar_pf;
+  TileBars tb{&bar, &bar_pf, 0u, 0u};
+  if constexpr (TMA) init_tile_bars(tb);
   constexpr int SEG = Tile<PREC, DIR>::SEG, LANES = Tile<PREC, DIR>::LANES;
   int a0, l0;
   if (DIR == 0) {
@@ -625,7 +647,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a, cons
   } else {
     l0 = blockIdx.x * LANES; a0 = blockIdx.y * SEG;
   }
-  sweep_tile<PREC, ORDER, DIR, FINAL, SEG, LANES, TMA>(a, a.jets, a0, l0, blockIdx.z, smem_raw, &maps, &bar, &bar_pf);
+  sweep_tile<PREC, ORDER, DIR, FINAL, SEG, LANES, TMA>(a, a.jets, a0, l0, blockIdx.z, smem_raw, &maps, &tb);
 }
 
 // Resident blocks per SM the batched kernels' register budget is held to: six
@@ -636,7 +658,7 @@ __host__ __device__ constexpr int batch_min_blocks() { return PREC == HYDRO_FP64
 
 // Batched sweep: a persistent grid walks the tile list of all grids of the
 // ensemble; each tile finds its grid's size and field offset in the event table.
-template <int PREC, int DIR, bool FINAL, int SEG, int LANES>
+template <int PREC, int DIR, bool FINAL, int SEG, int LANES, bool TMA>
 __global__ void __launch_bounds__(kThreads, batch_min_blocks<PREC>()) batch_sweep_kernel(const BatchArgs b) {
   using Store = typename Types<PREC>::Store;
   using F = typename Types<PREC>::Flux;
@@ -646,6 +668,9 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<PREC>()) batch_swee
   __shared__ GridArgs g;
   __shared__ __align__(16) int4 tdq[2];   // this tile's descriptor and the next one's, copied ahead
   __shared__ int4 td;
+  __shared__ __align__(8) uint64_t bar, bar_pf;
+  TileBars tb{&bar, &bar_pf, 0u, 0u};
+  if constexpr (TMA) init_tile_bars(tb);
   if (threadIdx.x == 0 && blockIdx.x < b.ntiles) {
     cp_async_ca<16>(&tdq[0], &b.tiles[blockIdx.x]);
     cp_async_commit();
@@ -682,8 +707,12 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<PREC>()) batch_swee
     }
     __syncthreads();
     const int4 tile = td;
-    sweep_tile<PREC, 7, DIR, FINAL, SEG, LANES>(g, b.jets[tile.x], tile.y, tile.z, tile.w, smem_raw);
-    __syncthreads();   // the next tile overwrites shared memory
+    sweep_tile<PREC, 7, DIR, FINAL, SEG, LANES, TMA>(g, b.jets[tile.x], tile.y, tile.z, tile.w, smem_raw,
+                                                     TMA ? b.maps + tile.x : nullptr, &tb);
+    // the next tile overwrites shared memory, partly by TMA: order this tile's
+    // generic-proxy writes before the async proxy's
+    if constexpr (TMA) fence_proxy_async_smem();
+    __syncthreads();
   }
 }
 
@@ -778,53 +807,55 @@ static void tile_shape(int precision, int d, int& seg, int& lanes) {
   else pick(std::integral_constant<int, HYDRO_MIXED>());
 }
 
-bool encode_sweep_tmaps(int precision, int order, void* const bufs[3], void* rhs, int nx, int ny, int nz,
-                        SweepMaps maps[3][3]) {
-  if (order != 7) return false;
-  const size_t es = precision == HYDRO_FP64 ? 8 : (precision == HYDRO_FP32 ? 4 : 8);   // stored type
-  const size_t fs = precision == HYDRO_FP64 ? 8 : 4;                                   // flux type
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiled encode_entry() {
   void* fn = nullptr;
   cudaDriverEntryPointQueryResult q;
   if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
       q != cudaDriverEntryPointSuccess || !fn) {
     cudaGetLastError();
-    return false;
+    return nullptr;
   }
-  using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-  Encode encode = reinterpret_cast<Encode>(fn);
+  return reinterpret_cast<EncodeTiled>(fn);
+}
+
+// The maps of one grid for the three stages and axes, with tile shapes seg[d] x lanes[d].
+static bool encode_grid(EncodeTiled encode, int precision, void* const bufs[3], void* rhs, int nx, int ny, int nz,
+                        const int seg[3], const int lanes[3], SweepMaps maps[3][3]) {
+  const size_t es = precision == HYDRO_FP32 ? 4 : 8;   // stored type
+  const size_t fs = precision == HYDRO_FP64 ? 8 : 4;   // flux type
   // a 4-D (x, y, z, field) map of one 5-field array with elements of `size` bytes
   auto enc = [&](CUtensorMap* m, void* base, size_t size, const cuuint32_t box[4]) {
     const cuuint64_t dim[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, 5};
     const cuuint64_t stride[3] = {(cuuint64_t)nx * size, (cuuint64_t)nx * ny * size, (cuuint64_t)nx * ny * nz * size};
     for (int k = 0; k < 3; ++k)
       if (stride[k] % 16 != 0) return false;
-    if ((box[0] * size) % 16 != 0) return false;
+    if ((box[0] * size) % 16 != 0 || reinterpret_cast<uintptr_t>(base) % 16 != 0) return false;
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     const CUtensorMapDataType dt = size == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
     return encode(m, dt, 4, base, dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
   };
   // box of a tile's staged cells (W = SEG + 8 along the axis) or updated cells (SEG)
-  auto box_of = [&](int d, int lanes, int along, cuuint32_t box[4]) {
+  auto box_of = [&](int d, int ln, int along, cuuint32_t box[4]) {
     box[3] = 5;
-    if (d == 0) { box[0] = along; box[1] = lanes; box[2] = 1; }
-    else if (d == 1) { box[0] = lanes; box[1] = along; box[2] = 1; }
-    else { box[0] = lanes; box[1] = 1; box[2] = along; }
+    if (d == 0) { box[0] = along; box[1] = ln; box[2] = 1; }
+    else if (d == 1) { box[0] = ln; box[1] = along; box[2] = 1; }
+    else { box[0] = ln; box[1] = 1; box[2] = along; }
   };
   std::memset(maps, 0, 9 * sizeof(SweepMaps));
   for (int st = 0; st < 3; ++st)
     for (int d = 0; d < 3; ++d) {
-      int seg, lanes;
-      tile_shape(precision, d, seg, lanes);
       cuuint32_t box[4];
       if (precision != HYDRO_MIXED) {   // staging box of the stage state
-        box_of(d, lanes, seg + 8, box);
+        box_of(d, lanes[d], seg[d] + 8, box);
         if (!enc(&maps[st][d].stage, bufs[st], es, box)) return false;
       }
       if (precision != HYDRO_FP64) {   // phase-3 operand and result boxes
-        box_of(d, lanes, seg, box);
+        box_of(d, lanes[d], seg[d], box);
         if (!enc(&maps[st][d].rhs, rhs, fs, box)) return false;
         if (d == 2) {
           if (!enc(&maps[st][d].u0, bufs[0], es, box)) return false;
@@ -835,25 +866,61 @@ bool encode_sweep_tmaps(int precision, int order, void* const bufs[3], void* rhs
   return true;
 }
 
+bool encode_sweep_tmaps(int precision, int order, void* const bufs[3], void* rhs, int nx, int ny, int nz,
+                        SweepMaps maps[3][3]) {
+  if (order != 7) return false;
+  EncodeTiled encode = encode_entry();
+  if (!encode) return false;
+  int seg[3], lanes[3];
+  for (int d = 0; d < 3; ++d) tile_shape(precision, d, seg[d], lanes[d]);
+  return encode_grid(encode, precision, bufs, rhs, nx, ny, nz, seg, lanes, maps);
+}
+
+bool encode_batch_tmaps(int precision, void* const bufs[3], void* rhs, int nev, const int32_t* dims,
+                        const size_t* off, const int variant[3], SweepMaps* maps) {
+  EncodeTiled encode = encode_entry();
+  if (!encode) return false;
+  const size_t es = precision == HYDRO_FP32 ? 4 : 8, fs = precision == HYDRO_FP64 ? 8 : 4;
+  int seg[3], lanes[3];
+  seg[0] = kTileSegX[variant[0]];
+  lanes[0] = kTileLanesX[variant[0]];
+  for (int d = 1; d < 3; ++d) {
+    seg[d] = kTileSegYZ[variant[d]];
+    lanes[d] = kTileLanesYZ[variant[d]];
+  }
+  for (int e = 0; e < nev; ++e) {
+    void* eb[3];
+    for (int k = 0; k < 3; ++k) eb[k] = static_cast<char*>(bufs[k]) + off[e] * es;
+    SweepMaps m[3][3];
+    if (!encode_grid(encode, precision, eb, static_cast<char*>(rhs) + off[e] * fs, dims[3 * e], dims[3 * e + 1],
+                     dims[3 * e + 2], seg, lanes, m))
+      return false;
+    for (int st = 0; st < 3; ++st)
+      for (int d = 0; d < 3; ++d) maps[(size_t)(st * 3 + d) * nev + e] = m[st][d];
+  }
+  return true;
+}
+
 // ---------------------------------------------------------------- batched launches
 
-template <int PREC, int DIR, int SEG, int LANES>
+// Batched tiles with tensor maps take the same TMA paths as single-grid tiles.
+template <int PREC, int DIR, int SEG, int LANES, bool TMA>
 static constexpr size_t batch_smem() {
   using F = typename Types<PREC>::Flux;
-  return sizeof(F) * (size_t)tile_smem_words<PREC, 7, DIR, SEG, LANES>();
+  return sizeof(F) * (size_t)tile_smem_words<PREC, 7, DIR, SEG, LANES, TMA && tma_staged<PREC>()>();
 }
 
-template <int PREC, int DIR, int SEG, int LANES>
+template <int PREC, int DIR, int SEG, int LANES, bool TMA>
 static auto batch_kernel_ptr() {
-  return batch_sweep_kernel<PREC, DIR, DIR == 2, SEG, LANES>;
+  return batch_sweep_kernel<PREC, DIR, DIR == 2, SEG, LANES, TMA>;
 }
 
-template <int PREC, int DIR, int V>
-static cudaError_t batch_launch_v(const BatchArgs& a, int grid, cudaStream_t s) {
+template <int PREC, int DIR, int V, bool TMA>
+static cudaError_t batch_launch_vt(const BatchArgs& a, int grid, cudaStream_t s) {
   constexpr int SEG = DIR == 0 ? kTileSegX[V] : kTileSegYZ[V];
   constexpr int LANES = DIR == 0 ? kTileLanesX[V] : kTileLanesYZ[V];
-  constexpr size_t smem = batch_smem<PREC, DIR, SEG, LANES>();
-  auto kern = batch_kernel_ptr<PREC, DIR, SEG, LANES>();
+  constexpr size_t smem = batch_smem<PREC, DIR, SEG, LANES, TMA>();
+  auto kern = batch_kernel_ptr<PREC, DIR, SEG, LANES, TMA>();
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   kern<<<grid, kThreads, smem, s>>>(a);
@@ -861,15 +928,25 @@ static cudaError_t batch_launch_v(const BatchArgs& a, int grid, cudaStream_t s) 
 }
 
 template <int PREC, int DIR, int V>
-static int batch_occupancy_v() {
+static cudaError_t batch_launch_v(const BatchArgs& a, int grid, cudaStream_t s) {
+  return a.maps ? batch_launch_vt<PREC, DIR, V, true>(a, grid, s) : batch_launch_vt<PREC, DIR, V, false>(a, grid, s);
+}
+
+template <int PREC, int DIR, int V, bool TMA>
+static int batch_occupancy_vt() {
   constexpr int SEG = DIR == 0 ? kTileSegX[V] : kTileSegYZ[V];
   constexpr int LANES = DIR == 0 ? kTileLanesX[V] : kTileLanesYZ[V];
-  constexpr size_t smem = batch_smem<PREC, DIR, SEG, LANES>();
-  auto kern = batch_kernel_ptr<PREC, DIR, SEG, LANES>();
+  constexpr size_t smem = batch_smem<PREC, DIR, SEG, LANES, TMA>();
+  auto kern = batch_kernel_ptr<PREC, DIR, SEG, LANES, TMA>();
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kThreads, smem) != cudaSuccess) return 0;
   return n;
+}
+
+template <int PREC, int DIR, int V>
+static int batch_occupancy_v(bool tma) {
+  return tma ? batch_occupancy_vt<PREC, DIR, V, true>() : batch_occupancy_vt<PREC, DIR, V, false>();
 }
 
 template <int PREC, int DIR>
@@ -882,11 +959,11 @@ static cudaError_t batch_launch_dir(int variant, const BatchArgs& a, int grid, c
 }
 
 template <int PREC, int DIR>
-static int batch_occupancy_dir(int variant) {
+static int batch_occupancy_dir(int variant, bool tma) {
   switch (variant) {
-    case 0: return batch_occupancy_v<PREC, DIR, 0>();
-    case 1: return batch_occupancy_v<PREC, DIR, 1>();
-    default: return batch_occupancy_v<PREC, DIR, 2>();
+    case 0: return batch_occupancy_v<PREC, DIR, 0>(tma);
+    case 1: return batch_occupancy_v<PREC, DIR, 1>(tma);
+    default: return batch_occupancy_v<PREC, DIR, 2>(tma);
   }
 }
 
@@ -900,11 +977,11 @@ static cudaError_t batch_launch_prec(int dir, int variant, const BatchArgs& a, i
 }
 
 template <int PREC>
-static int batch_occupancy_prec(int dir, int variant) {
+static int batch_occupancy_prec(int dir, int variant, bool tma) {
   switch (dir) {
-    case 0: return batch_occupancy_dir<PREC, 0>(variant);
-    case 1: return batch_occupancy_dir<PREC, 1>(variant);
-    default: return batch_occupancy_dir<PREC, 2>(variant);
+    case 0: return batch_occupancy_dir<PREC, 0>(variant, tma);
+    case 1: return batch_occupancy_dir<PREC, 1>(variant, tma);
+    default: return batch_occupancy_dir<PREC, 2>(variant, tma);
   }
 }
 
@@ -926,11 +1003,11 @@ cudaError_t launch_batch_sweep(int precision, int dir, int variant, const BatchA
   }
 }
 
-int batch_sweep_blocks_per_sm(int precision, int dir, int variant) {
+int batch_sweep_blocks_per_sm(int precision, int dir, int variant, bool tma) {
   switch (precision) {
-    case HYDRO_FP64: return batch_occupancy_prec<HYDRO_FP64>(dir, variant);
-    case HYDRO_FP32: return batch_occupancy_prec<HYDRO_FP32>(dir, variant);
-    default: return batch_occupancy_prec<HYDRO_MIXED>(dir, variant);
+    case HYDRO_FP64: return batch_occupancy_prec<HYDRO_FP64>(dir, variant, tma);
+    case HYDRO_FP32: return batch_occupancy_prec<HYDRO_FP32>(dir, variant, tma);
+    default: return batch_occupancy_prec<HYDRO_MIXED>(dir, variant, tma);
   }
 }
 
