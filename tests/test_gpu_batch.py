@@ -97,6 +97,29 @@ def test_reduced_precision_batch_is_bitwise_single_grid(hy, W, precision):
         assert np.array_equal(got, want), e
 
 
+@pytest.mark.parametrize("precision,variants", [("fp64", (0, 0, 0)), ("fp32", (1, 0, 0)), ("fp32", (2, 1, 2)),
+                                                ("mixed", (1, 2, 0))])
+def test_batch_with_tensor_maps_is_bitwise_single_grid(hy, W, precision, variants):
+    """Every row pitch and field offset a multiple of 16 bytes: the persistent
+    kernels stage, fetch and store through per-grid tensor maps (and carry their
+    mbarrier phases across tiles of different grids) and still match the grids
+    stepped alone bit for bit."""
+    shapes = [(16, 20, 12), (24, 16, 18), (36, 17, 9), (8, 40, 20), (72, 5, 6), (40, 40, 40)]
+    events = []
+    for k, n in enumerate(shapes):
+        jets = W.seeded_jets(200 + k, 1 + k % 3, 0.5, 1.0)
+        events.append(replace(W.ELLIPSOIDAL_32, n=n, sigma=(0.7 + 0.1 * k, 0.9, 1.1), e0=20.0 + 5 * k, jets=jets))
+    steps = 3
+    b = _batch(hy, W, events, precision, variants)
+    hy.hydro_batch_step(b, steps)
+    for e, w in enumerate(events):
+        got = hy.hydro_batch_read_fields(b, e)
+        want, d = _single(hy, w, precision, steps)
+        assert np.array_equal(got, want), e
+        assert hy.hydro_batch_get_diag(b, e)["jet_cells"] == d["jet_cells"]
+    hy.hydro_batch_destroy(b)
+
+
 def test_autotune_picks_a_shape_and_leaves_the_state_alone(hy, W):
     events = _small_ensemble(W)
     b = _batch(hy, W, events, "fp32")
