@@ -38,11 +38,17 @@ __device__ __forceinline__ double rcp_nr(double d) {
   return fma(y, e, y);
 }
 
+// gt_nonneg(a, b) = a > b for a >= 0 or NaN and b >= 0: FP64 compares the bit
+// patterns on the integer pipe (non-negative doubles order like them; a NaN with
+// the sign bit clear compares greater), FP32 compares the values.
 struct MathD {
   using T = double;
   static constexpr double m_max = 1.0 - 1e-12;   // cap on |M|/E (|M| -> E as v -> 1)
   static __device__ __forceinline__ double rcp(double x) { return rcp_nr(x); }
   static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
+  static __device__ __forceinline__ bool gt_nonneg(double a, double b) {
+    return __double_as_longlong(a) > __double_as_longlong(b);
+  }
 };
 
 struct MathF {
@@ -50,35 +56,38 @@ struct MathF {
   static constexpr float m_max = 1.0f - 1.0f / 1048576.0f;
   static __device__ __forceinline__ float rcp(float x) { return rcp_approx(x); }
   static __device__ __forceinline__ float sqrt(float x) { return sqrt_approx(x); }
+  static __device__ __forceinline__ bool gt_nonneg(float a, float b) { return !(a <= b); }
 };
 
 // Closed-form conserved -> primitive recovery for p = e/3.
 // With m = |M|/E the EOS gives m = 4v/(3+v^2), so v = 3m/(2 + sqrt(4-3m^2)),
 // e = E (1 - m v), p = e/3 and v^i = v M^i/|M| = 3 (m/|M|) M^i / (2 + sqrt(4-3m^2)).
-// E below e_floor is raised to e_floor and m is capped below 1; either floor
-// sets hit.  The stored state is never modified.
+// Everything but the cap test needs m^2 = |M|^2/E^2 only (m v = 3 m^2 r and
+// m/|M| = 1/E, r = 1/(2 + sqrt(4 - 3m^2))), so |M| itself, one square root, is
+// formed only when the cap acts.  E below e_floor is raised to e_floor and m is
+// capped below 1; either floor sets hit.  The stored state is never modified.
 template <class M>
 __device__ __forceinline__ void cons_to_prim(typename M::T E, typename M::T Mx, typename M::T My,
                                              typename M::T Mz, typename M::T e_floor, typename M::T& e,
                                              typename M::T& vx, typename M::T& vy, typename M::T& vz, int& hit) {
   using P = typename M::T;
-  const P Mabs = M::sqrt(Mx * Mx + My * My + Mz * Mz);
+  const P M2 = Mx * Mx + My * My + Mz * Mz;
   P Ee = E;
   if (!(Ee >= e_floor)) {
     Ee = e_floor;
     hit = 1;
   }
   const P invE = M::rcp(Ee);
-  P m = Mabs * invE;
+  P m2 = M2 * invE * invE;
   P m_over_M = invE;   // m / |M|, so that v / |M| = 3 r m / |M| stays finite for M = 0
-  if (!(m <= M::m_max)) {
-    m = M::m_max;
-    m_over_M = m / Mabs;
+  constexpr P m_max2 = M::m_max * M::m_max;
+  if (M::gt_nonneg(m2, m_max2)) {   // m2 >= 0 or NaN (a NaN state takes the cap branch and stays NaN)
+    m2 = m_max2;
+    m_over_M = M::m_max / M::sqrt(M2);
     hit = 1;
   }
-  const P r = M::rcp(P(2) + M::sqrt(P(4) - P(3) * m * m));
-  const P v = P(3) * m * r;
-  e = Ee * (P(1) - m * v);
+  const P r = M::rcp(P(2) + M::sqrt(P(4) - P(3) * m2));
+  e = Ee * (P(1) - P(3) * m2 * r);
   const P vs = P(3) * m_over_M * r;   // v / |M|
   vx = Mx * vs;
   vy = My * vs;
@@ -198,7 +207,7 @@ __device__ __forceinline__ typename M::T spectral_radius(typename M::T vd, typen
   const P third = P(1) / P(3);
   const P vd2 = vd * vd;
   P disc = (P(1) - v2) * (P(1) - vd2 - (v2 - vd2) * third);
-  disc = disc > P(0) ? disc : P(0);
+  disc = M::gt_nonneg(disc, P(0)) ? disc : P(0);   // (against +0 the bit compare also orders negatives)
   return (fabs(vd) * (P(2) * third) + M::sqrt(disc * third)) * M::rcp(P(1) - v2 * third);
 }
 
