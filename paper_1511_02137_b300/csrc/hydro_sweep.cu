@@ -383,6 +383,7 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
       Es = U[o]; Mxs = U[N + o]; Mys = U[2 * N + o]; Mzs = U[3 * N + o]; Rs = U[4 * N + o];
     }
     F e, vx, vy, vz, E, Mx, My, Mz, R;
+    F v2, rden;   // v^2 and 1/(1 - v^2/3) from the recovery (FP64, FP32)
     int hit = 0;
     if constexpr (PREC == HYDRO_MIXED) {
       // the x and y sweeps have FP64-pipe time to spare (E^2 - |M|^2 is their only
@@ -395,12 +396,14 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
       }
       cons_to_prim_mixed_f(Es, Mxs, Mys, Mzs, E, Mx, My, Mz, a.e_floor, e, vx, vy, vz, hit);
     } else {
-      cons_to_prim<Math>(Es, Mxs, Mys, Mzs, kconst<F>(a.e_floor, a.k.e_floor_f), e, vx, vy, vz, hit);
+      cons_to_prim_rho<Math>(Es, Mxs, Mys, Mzs, kconst<F>(a.e_floor, a.k.e_floor_f), e, vx, vy, vz, v2, rden, hit);
       E = (F)Es; Mx = (F)Mxs; My = (F)Mys; Mz = (F)Mzs; R = (F)Rs;
     }
     const F p = e * F(1.0 / 3.0);
     const F vd = DIR == 0 ? vx : (DIR == 1 ? vy : vz);
-    const F rho = spectral_radius<Math>(vd, vx * vx + vy * vy + vz * vz);
+    F rho;
+    if constexpr (PREC == HYDRO_MIXED) rho = spectral_radius<Math>(vd, vx * vx + vy * vy + vz * vz);
+    else rho = spectral_radius_r<Math>(vd, v2, rden);
     const F Md = DIR == 0 ? Mx : (DIR == 1 ? My : Mz);
     const F Fh[5] = {F(0.5) * Md, F(0.5) * (Mx * vd + (DIR == 0 ? p : F(0))),
                      F(0.5) * (My * vd + (DIR == 1 ? p : F(0))), F(0.5) * (Mz * vd + (DIR == 2 ? p : F(0))),
