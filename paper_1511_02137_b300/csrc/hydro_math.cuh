@@ -68,6 +68,14 @@ struct MathD {
   static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
   // x^(1/2) and x^(-1/2) for x >= 1
   static __device__ __forceinline__ void sqrt_rsqrt(double x, double& s, double& y) { sqrt_rsqrt_nr(x, s, y); }
+  // x^(1/2) for x >= 0 where a result of 1.5e-154 in place of 0 is immaterial:
+  // the argument is raised to the smallest normal double
+  static __device__ __forceinline__ double sqrt_nonneg(double x) {
+    const long long b = __double_as_longlong(x), lo = 0x0010000000000000LL;   // 2^-1022
+    double s, y;
+    sqrt_rsqrt_nr(__longlong_as_double(b > lo ? b : lo), s, y);
+    return s;
+  }
   static __device__ __forceinline__ bool gt_nonneg(double a, double b) {
     return __double_as_longlong(a) > __double_as_longlong(b);
   }
@@ -82,6 +90,7 @@ struct MathF {
     y = rsqrt_approx(x);
     s = x * y;
   }
+  static __device__ __forceinline__ float sqrt_nonneg(float x) { return sqrt_approx(x); }
   static __device__ __forceinline__ bool gt_nonneg(float a, float b) { return !(a <= b); }
 };
 
@@ -166,7 +175,7 @@ __device__ __forceinline__ typename M::T spectral_radius_r(typename M::T vd, typ
   const P vd2 = vd * vd;
   P disc = (P(1) - v2) * (P(1) - vd2 - (v2 - vd2) * third);
   disc = M::gt_nonneg(disc, P(0)) ? disc : P(0);
-  return (fabs(vd) * (P(2) * third) + M::sqrt(disc * third)) * rden;
+  return (fabs(vd) * (P(2) * third) + M::sqrt_nonneg(disc * third)) * rden;
 }
 
 // Mixed-precision recovery: only the cancelling combination E^2 - |M|^2 (tiny
