@@ -269,7 +269,8 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   F* sH = sR + NCS;                         // [5][NIF] numerical flux
 
   const int nx = a.nx, ny = a.ny, nz = a.nz;
-  const size_t N = (size_t)nx * ny * nz;
+  const size_t N64 = (size_t)nx * ny * nz;
+  const size_t N = N64;
   const int n_along = DIR == 0 ? nx : (DIR == 1 ? ny : nz);
   const int n_lane = DIR == 0 ? ny : nx;
   auto offset = [&](int along, int lane) -> size_t {
@@ -549,7 +550,10 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
     else { j = c / LANES; lane = c - j * LANES; }
     const int ga = a0 + j, gl = l0 + lane;
     if (ga < n_along && gl < n_lane) {
-      const size_t o = offset(ga, gl);
+      // 32-bit element indices (a grid holds at most 4e8 cells, 5 fields < 2^32)
+      const unsigned o = DIR == 0 ? ((unsigned)fixed * ny + gl) * nx + ga
+                       : (DIR == 1 ? ((unsigned)fixed * ny + ga) * nx + gl : ((unsigned)ga * ny + fixed) * nx + gl);
+      const unsigned N = (unsigned)N64;
       const int h0 = hidx(lane, j), h1 = hidx(lane, j + 1);
       F L[5];
 #pragma unroll
