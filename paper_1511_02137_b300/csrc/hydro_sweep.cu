@@ -269,14 +269,14 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   F* sH = sR + NCS;                         // [5][NIF] numerical flux
 
   const int nx = a.nx, ny = a.ny, nz = a.nz;
-  const size_t N64 = (size_t)nx * ny * nz;
-  const size_t N = N64;
+  // 32-bit element indices: a grid holds at most 4e8 cells, so 5 fields stay below 2^32
+  const unsigned N = (unsigned)nx * ny * nz;
   const int n_along = DIR == 0 ? nx : (DIR == 1 ? ny : nz);
   const int n_lane = DIR == 0 ? ny : nx;
-  auto offset = [&](int along, int lane) -> size_t {
-    if (DIR == 0) return ((size_t)fixed * ny + lane) * nx + along;
-    if (DIR == 1) return ((size_t)fixed * ny + along) * nx + lane;
-    return ((size_t)along * ny + fixed) * nx + lane;
+  auto offset = [&](int along, int lane) -> unsigned {
+    if (DIR == 0) return ((unsigned)fixed * ny + lane) * nx + along;
+    if (DIR == 1) return ((unsigned)fixed * ny + along) * nx + lane;
+    return ((unsigned)along * ny + fixed) * nx + lane;
   };
   // staged cell (lane, s) and interface/cell (lane, j) index maps; consecutive
   // threads walk the contiguous (x) direction in every phase
@@ -315,7 +315,7 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
     else { j = c / LANES; lane = c - j * LANES; }
     const int ga = a0 + j, gl = l0 + lane;
     if (ga < n_along && gl < n_lane) {
-      const size_t o = offset(ga, gl);
+      const unsigned o = offset(ga, gl);
 #pragma unroll
       for (int q = 0; q < 5; ++q) cp_async_ca<sizeof(F)>(sPr + q * NC + c, rhs_in + q * N + o);
       if constexpr (FINAL) {
@@ -380,7 +380,7 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
       Es = (Store)sStage[c]; Mxs = (Store)sStage[NCS + c]; Mys = (Store)sStage[2 * NCS + c];
       Mzs = (Store)sStage[3 * NCS + c]; Rs = (Store)sStage[4 * NCS + c];
     } else {
-      const size_t o = offset(map_along(ga, n_along, a.periodic), gl < n_lane ? gl : n_lane - 1);
+      const unsigned o = offset(map_along(ga, n_along, a.periodic), gl < n_lane ? gl : n_lane - 1);
       Es = U[o]; Mxs = U[N + o]; Mys = U[2 * N + o]; Mzs = U[3 * N + o]; Rs = U[4 * N + o];
     }
     F e, vx, vy, vz, E, Mx, My, Mz, R;
@@ -550,10 +550,7 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
     else { j = c / LANES; lane = c - j * LANES; }
     const int ga = a0 + j, gl = l0 + lane;
     if (ga < n_along && gl < n_lane) {
-      // 32-bit element indices (a grid holds at most 4e8 cells, 5 fields < 2^32)
-      const unsigned o = DIR == 0 ? ((unsigned)fixed * ny + gl) * nx + ga
-                       : (DIR == 1 ? ((unsigned)fixed * ny + ga) * nx + gl : ((unsigned)ga * ny + fixed) * nx + gl);
-      const unsigned N = (unsigned)N64;
+      const unsigned o = offset(ga, gl);
       const int h0 = hidx(lane, j), h1 = hidx(lane, j + 1);
       F L[5];
 #pragma unroll
