@@ -602,6 +602,9 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
         const Store* U0 = static_cast<const Store*>(a.U0);
         Store* Uout = static_cast<Store*>(a.Uout);
         const Store dt = kconst<Store>(a.dt, a.k.dt_f), ca = kconst<Store>(a.a, a.k.a_f), cb = kconst<Store>(a.b, a.k.b_f);
+        // FP32: the finite test runs once on the sum of the five results (NaN and
+        // infinities propagate into it; a finite sum of physical values cannot overflow)
+        float chk = 0.0f;
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
           Store out;
@@ -619,9 +622,11 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
             const Store l = Lq[q];
             out = a.k.first ? u + dt * l : ca * (PF::on ? sP0[q * NC + c] : U0[q * N + o]) + cb * (u + dt * l);
           }
-          bad |= !finite_bits(out);
+          if constexpr (sizeof(Store) == 4) chk += out;
+          else bad |= !finite_bits(out);
           Uout[q * N + o] = out;
         }
+        if constexpr (sizeof(Store) == 4) bad |= !finite_bits(chk);
       }
     }
   }
