@@ -51,7 +51,8 @@ enum { HYDRO_PRIMITIVE = 0, HYDRO_CONSERVED = 1 };           /* field kinds */
 
 /* Run configuration.  hydro_config_default() fills the paper's values. */
 typedef struct {
-  int32_t nx, ny, nz;   /* cells per axis, each >= 1 */
+  int32_t nx, ny, nz;   /* cells per axis, each >= 1; ny, nz <= 65535 and nx ny nz <= 4e8
+                           (32-bit element indices in the kernels) */
   int32_t precision;    /* HYDRO_FP64: everything in FP64.
                            HYDRO_FP32: storage and arithmetic in FP32.
                            HYDRO_MIXED: FP64 storage, FP64 conserved-to-primitive recovery
@@ -229,8 +230,9 @@ typedef struct hydro_adjoint hydro_adjoint;
 
 /* Sets up an adjoint run (allocates checkpoint, segment and adjoint buffers
  * with cudaMalloc).  HYDRO_EINVAL unless precision is HYDRO_FP64 or
- * HYDRO_MIXED, boundary = HYDRO_OUTFLOW and weno_order = 7, or for
- * non-positive sizes or cone. */
+ * HYDRO_MIXED, boundary = HYDRO_OUTFLOW and weno_order = 7, for grids of more
+ * than 4e8 cells (the kernels index with 32 bits), or for non-positive sizes or
+ * cone. */
 hydro_status hydro_adjoint_create(const hydro_config* cfg, int32_t nsteps, int32_t checkpoint_every,
                                   const double apex[3], const double axis[3], double half_angle_deg, double rmax,
                                   hydro_adjoint** out);

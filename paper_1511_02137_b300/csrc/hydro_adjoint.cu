@@ -109,17 +109,18 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
   P* r_out = static_cast<P*>(p.r);
 
   const int nx = p.nx, ny = p.ny, nz = p.nz;
-  const size_t N = (size_t)nx * ny * nz;
+  // 32-bit element indices: hydro_adjoint_create admits at most 4e8 cells (7 shadow fields < 2^32)
+  const unsigned N = (unsigned)nx * ny * nz;
   const int n_along = DIR == 0 ? nx : (DIR == 1 ? ny : nz);
   const int n_lane = DIR == 0 ? ny : nx;
   int a0, l0;
   if (DIR == 0) { a0 = blockIdx.x * SEG; l0 = blockIdx.y * LANES; }
   else { l0 = blockIdx.x * LANES; a0 = blockIdx.y * SEG; }
   const int fixed = blockIdx.z;
-  auto offset = [&](int along, int lane) -> size_t {
-    if (DIR == 0) return ((size_t)fixed * ny + lane) * nx + along;
-    if (DIR == 1) return ((size_t)fixed * ny + along) * nx + lane;
-    return ((size_t)along * ny + fixed) * nx + lane;
+  auto offset = [&](int along, int lane) -> unsigned {
+    if (DIR == 0) return ((unsigned)fixed * ny + lane) * nx + along;
+    if (DIR == 1) return ((unsigned)fixed * ny + along) * nx + lane;
+    return ((unsigned)along * ny + fixed) * nx + lane;
   };
   auto sidx = [&](int lane, int s) { return DIR == 0 ? lane * W + s : s * LANES + lane; };
   auto iidx = [&](int lane, int ii) { return DIR == 0 ? lane * NI + ii : ii * LANES + lane; };
@@ -138,7 +139,7 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
     const int ga = a0 - 8 + s;
     const int gl = l0 + lane;
     const bool inside = ga >= 0 && ga < n_along && gl < n_lane;
-    const size_t oa = offset(inside ? ga : 0, gl < n_lane ? gl : 0);
+    const unsigned oa = offset(inside ? ga : 0, gl < n_lane ? gl : 0);
     for (int q = 0; q < 5; ++q) {
       P aq;
       if constexpr (MIXED) aq = inside ? p.lamf[q * N + oa] : P(0);
@@ -154,7 +155,7 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
         lane = c / SEG;
         j = c - lane * SEG;
         if (a0 + j >= n_along || l0 + lane >= n_lane) continue;
-        const size_t o = offset(a0 + j, l0 + lane);
+        const unsigned o = offset(a0 + j, l0 + lane);
         for (int k = 0; k < 5; ++k) r_out[k * N + o] = P(0);
       }
     }
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
     else { s = c / LANES; lane = c - s * LANES; }
     const int ga = a0 - 8 + s;
     const int gl = l0 + lane;
-    const size_t o = offset(clampi(ga, n_along), gl < n_lane ? gl : n_lane - 1);
+    const unsigned o = offset(clampi(ga, n_along), gl < n_lane ? gl : n_lane - 1);
     P e, vx, vy, vz, E, Mx, My, Mz, R;
     int hit = 0;
     if constexpr (MIXED) {
@@ -327,7 +328,7 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
       if (own) rhob += P(0.5) * (P)own * sAhb[x] / (P)__popc(mask);
     }
     const int sc = sidx(lane, j + 8);
-    const size_t o = offset(gcell, gl);
+    const unsigned o = offset(gcell, gl);
     const P Mx = sU[NCS + sc], My = sU[2 * NCS + sc], Mz = sU[3 * NCS + sc], R = sU[4 * NCS + sc];
     P e, vx, vy, vz;
     C2PTape<P> tape;
@@ -379,7 +380,7 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
           continue;
         const int j = cl[2] - a0, lane = cl[0] - l0;
         const int sc = sidx(lane, j + 8);
-        const size_t o = offset(cl[2], cl[0]);
+        const unsigned o = offset(cl[2], cl[0]);
         const double Ed = p.U[o], Mxd = p.U[N + o], Myd = p.U[2 * N + o], Mzd = p.U[3 * N + o];
         // S0 = inv_vol (k_rad C T^3 l / hc^2 + k_coll C T^2 / hc), T = (e t4)^(1/4): S = (S0, n S0, 0).
         // The source runs in FP64 in both precisions (FP64 recovery at the jet cell).
@@ -706,6 +707,7 @@ hydro_status hydro_adjoint_create(const hydro_config* cfg, int32_t nsteps, int32
     return HYDRO_EINVAL;
   if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1 || nsteps < 1 || checkpoint_every < 1 || !apex || !axis)
     return HYDRO_EINVAL;
+  if ((double)cfg->nx * cfg->ny * cfg->nz > 4.0e8) return HYDRO_EINVAL;   // 32-bit indices, as the forward
   if (!(cfg->dx > 0.0) || !(cfg->dt > 0.0) || !(cfg->e_floor > 0.0) || !weno_eps_ok(cfg->precision, cfg->weno_eps)) return HYDRO_EINVAL;
   const double al = std::sqrt(axis[0] * axis[0] + axis[1] * axis[1] + axis[2] * axis[2]);
   if (!(al > 0.0) || !(rmax > 0.0) || !(half_angle_deg > 0.0 && half_angle_deg < 180.0)) return HYDRO_EINVAL;
