@@ -554,6 +554,12 @@ struct hydro_adjoint {
   std::vector<double*> seg;      // (every + 1) step states for the recomputed segment
   double* rhs = nullptr;
   std::vector<double*> stages;   // every x 2 stage states (U1, U2) of the segment
+  // a second segment buffer set, refilled on a side stream while the main stream
+  // reverses the other one (set of segment k: (nckpt - 1 - k) & 1)
+  std::vector<double*> seg_b, stages_b;
+  double* rhs_b = nullptr;
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_ready[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr}, ev_start = nullptr;
   double *lamA = nullptr, *lamB = nullptr, *lam0 = nullptr, *r = nullptr, *prim = nullptr;
   float* sh = nullptr;           // mixed: FP32 shadow of the stage state under reverse [7][n]
   float* lamf = nullptr;         // mixed: FP32 scaled adjoint input of the next reverse sweep [5][n]
@@ -618,8 +624,10 @@ SweepArgs sweep_base(const hydro_adjoint* a) {
 
 // One forward step from `in` (step index n) to `out`; the two intermediate stage
 // states go to s1, s2.
-cudaError_t forward_step(hydro_adjoint* a, int64_t n, const double* in, double* s1, double* s2, double* out) {
+cudaError_t forward_step(hydro_adjoint* a, int64_t n, const double* in, double* s1, double* s2, double* out,
+                         cudaStream_t stream, double* rhs) {
   SweepArgs s = sweep_base(a);
+  s.rhs = rhs;
   s.U0 = in;
   const double vol = a->cfg.dx * a->cfg.dx * a->cfg.dx;
   const double* Us[3] = {in, s1, s2};
@@ -632,7 +640,7 @@ cudaError_t forward_step(hydro_adjoint* a, int64_t n, const double* in, double* 
     s.Uout = Uo[st];
     s.a = kA[st];
     s.b = kB[st];
-    for (int d = 0; d < 3 && err == cudaSuccess; ++d) err = launch_sweep(a->cfg.precision, 7, d, s, a->stream);
+    for (int d = 0; d < 3 && err == cudaSuccess; ++d) err = launch_sweep(a->cfg.precision, 7, d, s, stream);
   }
   return err;
 }
@@ -732,7 +740,7 @@ hydro_status hydro_adjoint_create(const hydro_config* cfg, int32_t nsteps, int32
   a->cone.nz = cfg->nz;
   // buffers: checkpoints, the segment's step states and stage states, adjoints, scratch
   const size_t f5 = 5 * a->n * sizeof(double);
-  const size_t nbuf = (size_t)a->nckpt + (size_t)(a->every + 1) + 2 * (size_t)a->every + 1 + 4 + 1;
+  const size_t nbuf = (size_t)a->nckpt + 2 * ((size_t)(a->every + 1) + 2 * (size_t)a->every + 1) + 4 + 1;
   const size_t shadow = cfg->precision == HYDRO_MIXED ? 12 * a->n * sizeof(float) + 512 : 0;
   const size_t bytes = nbuf * f5 + a->n * sizeof(double) + 2 * kMaxJets * sizeof(double) +
                        kConeBlocks * sizeof(double) + sizeof(DevDiag) + shadow + 4096;
@@ -751,6 +759,9 @@ hydro_status hydro_adjoint_create(const hydro_config* cfg, int32_t nsteps, int32
   for (int k = 0; k <= a->every; ++k) a->seg.push_back(reinterpret_cast<double*>(take(f5)));
   for (int k = 0; k < 2 * a->every; ++k) a->stages.push_back(reinterpret_cast<double*>(take(f5)));
   a->rhs = reinterpret_cast<double*>(take(f5));
+  for (int k = 0; k <= a->every; ++k) a->seg_b.push_back(reinterpret_cast<double*>(take(f5)));
+  for (int k = 0; k < 2 * a->every; ++k) a->stages_b.push_back(reinterpret_cast<double*>(take(f5)));
+  a->rhs_b = reinterpret_cast<double*>(take(f5));
   a->lamA = reinterpret_cast<double*>(take(f5));
   a->lamB = reinterpret_cast<double*>(take(f5));
   a->lam0 = reinterpret_cast<double*>(take(f5));
@@ -763,6 +774,16 @@ hydro_status hydro_adjoint_create(const hydro_config* cfg, int32_t nsteps, int32
   a->kbar = reinterpret_cast<double*>(take(2 * kMaxJets * sizeof(double)));
   a->partial = reinterpret_cast<double*>(take(kConeBlocks * sizeof(double)));
   a->diag = reinterpret_cast<DevDiag*>(take(sizeof(DevDiag)));
+  bool ok = cudaStreamCreateWithFlags(&a->side, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&a->ev_start, cudaEventDisableTiming) == cudaSuccess;
+  for (int k = 0; k < 2 && ok; ++k)
+    ok = cudaEventCreateWithFlags(&a->ev_ready[k], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&a->ev_free[k], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    hydro_adjoint_destroy(a);
+    return HYDRO_ECUDA;
+  }
   *out = a;
   return HYDRO_OK;
 }
@@ -804,7 +825,8 @@ hydro_status hydro_adjoint_forward(hydro_adjoint* a, const double* d_prim5, doub
     if (s >= s_last) {
       const int i = s - s_last;
       if (i == 0) err = cudaMemcpyAsync(a->seg[0], cur, 5 * a->n * sizeof(double), cudaMemcpyDeviceToDevice, a->stream);
-      if (err == cudaSuccess) err = forward_step(a, s, a->seg[i], a->stages[2 * i], a->stages[2 * i + 1], a->seg[i + 1]);
+      if (err == cudaSuccess)
+        err = forward_step(a, s, a->seg[i], a->stages[2 * i], a->stages[2 * i + 1], a->seg[i + 1], a->stream, a->rhs);
       cur = a->seg[i + 1];
       continue;
     }
@@ -816,7 +838,7 @@ hydro_status hydro_adjoint_forward(hydro_adjoint* a, const double* d_prim5, doub
       next = a->seg[pp];
       pp ^= 1;
     }
-    err = forward_step(a, s, cur, a->stages[0], a->stages[1], next);
+    err = forward_step(a, s, cur, a->stages[0], a->stages[1], next, a->stream, a->rhs);
     cur = next;
   }
   if (err == cudaSuccess) cone_energy_kernel<<<kConeBlocks, 256, 0, a->stream>>>(cur, a->cone, a->partial);
@@ -852,21 +874,43 @@ hydro_status hydro_adjoint_backward(hydro_adjoint* a, double dJ, double* grad_k_
       err = cudaGetLastError();
     }
   }
-  // segments in reverse: recompute the step states of the segment from its
-  // checkpoint, then walk its steps backwards
-  for (int k = a->nckpt - 1; k >= 0 && err == cudaSuccess; --k) {
-    const int s0 = k * a->every;
-    const int s1 = std::min(a->nsteps, s0 + a->every);
-    const int len = s1 - s0;
-    if (!(k == a->nckpt - 1 && a->last_kept)) {
-      err = cudaMemcpyAsync(a->seg[0], a->ckpt[k], 5 * a->n * sizeof(double), cudaMemcpyDeviceToDevice, a->stream);
-      for (int s = 0; s < len && err == cudaSuccess; ++s)
-        err = forward_step(a, s0 + s, a->seg[s], a->stages[2 * s], a->stages[2 * s + 1], a->seg[s + 1]);
+  // segments in reverse: the step and stage states of a segment are recomputed
+  // from its checkpoint into one of two buffer sets on the side stream while the
+  // main stream walks the previous segment's steps backwards in the other set
+  // (the reverse sweeps leave most issue slots idle; the forward sweeps fill them)
+  auto set_of = [&](int k) { return (a->nckpt - 1 - k) & 1; };
+  auto recompute = [&](int k, cudaStream_t st) {
+    const int s0 = k * a->every, len = std::min(a->nsteps, s0 + a->every) - s0;
+    std::vector<double*>& sg = set_of(k) ? a->seg_b : a->seg;
+    std::vector<double*>& sta = set_of(k) ? a->stages_b : a->stages;
+    double* rhs = set_of(k) ? a->rhs_b : a->rhs;
+    cudaError_t e = cudaMemcpyAsync(sg[0], a->ckpt[k], 5 * a->n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    for (int s = 0; s < len && e == cudaSuccess; ++s)
+      e = forward_step(a, s0 + s, sg[s], sta[2 * s], sta[2 * s + 1], sg[s + 1], st, rhs);
+    return e;
+  };
+  const int last = a->nckpt - 1;
+  if (err == cudaSuccess && !a->last_kept) err = recompute(last, a->stream);   // set 0
+  a->last_kept = false;   // the replays below overwrite the segment buffers
+  // the side stream starts after everything issued so far (checkpoints, seeds); set 1 is free
+  if (err == cudaSuccess) err = cudaEventRecord(a->ev_start, a->stream);
+  if (err == cudaSuccess) err = cudaStreamWaitEvent(a->side, a->ev_start, 0);
+  if (err == cudaSuccess) err = cudaEventRecord(a->ev_free[1], a->stream);
+  for (int k = last; k >= 0 && err == cudaSuccess; --k) {
+    if (k >= 1) {   // refill the other set with segment k - 1 once its previous reader is done
+      const int o = set_of(k - 1);
+      err = cudaStreamWaitEvent(a->side, a->ev_free[o], 0);
+      if (err == cudaSuccess) err = recompute(k - 1, a->side);
+      if (err == cudaSuccess) err = cudaEventRecord(a->ev_ready[o], a->side);
     }
-    a->last_kept = false;   // the replays below overwrite the segment buffers
+    if (err == cudaSuccess && k < last) err = cudaStreamWaitEvent(a->stream, a->ev_ready[set_of(k)], 0);
+    const int s0 = k * a->every;
+    const int len = std::min(a->nsteps, s0 + a->every) - s0;
+    const std::vector<double*>& sg = set_of(k) ? a->seg_b : a->seg;
+    const std::vector<double*>& sta = set_of(k) ? a->stages_b : a->stages;
     for (int s = len - 1; s >= 0 && err == cudaSuccess; --s) {
       const int64_t n = s0 + s;
-      const double* Us[3] = {a->seg[s], a->stages[2 * s], a->stages[2 * s + 1]};
+      const double* Us[3] = {sg[s], sta[2 * s], sta[2 * s + 1]};
       // stage 3: U = 1/3 U0 + 2/3 (U2 + dt L(U2))
       err = vjp(a, n, 2, Us[2], a->lamA, kB[2] * a->cfg.dt);
       if (err == cudaSuccess) err = combine(a, 0, 2);
@@ -878,6 +922,7 @@ hydro_status hydro_adjoint_backward(hydro_adjoint* a, double dJ, double* grad_k_
       if (err == cudaSuccess) err = combine(a, 2, 0);
       std::swap(a->lamA, a->lam0);   // adjoint of the step's input becomes the next output adjoint
     }
+    if (err == cudaSuccess) err = cudaEventRecord(a->ev_free[set_of(k)], a->stream);
   }
   if (err == cudaSuccess) {
     grad_e_kernel<<<grid_1d(a->n), 256, 0, a->stream>>>(a->prim, a->lamA, d_grad_e, a->n);
@@ -900,6 +945,12 @@ hydro_status hydro_adjoint_backward(hydro_adjoint* a, double dJ, double* grad_k_
 void hydro_adjoint_destroy(hydro_adjoint* a) {
   if (!a) return;
   if (a->stream || a->ws) cudaStreamSynchronize(a->stream);
+  if (a->side) {
+    cudaStreamSynchronize(a->side);
+    cudaStreamDestroy(a->side);
+  }
+  for (cudaEvent_t e : {a->ev_start, a->ev_ready[0], a->ev_ready[1], a->ev_free[0], a->ev_free[1]})
+    if (e) cudaEventDestroy(e);
   if (a->ws) cudaFree(a->ws);
   delete a;
 }
