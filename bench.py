@@ -52,9 +52,9 @@ FIELD_ACCESSES_PER_CELL_STEP = 40
 # (dram__bytes_read.sum + dram__bytes_write.sum, mean over the three stages of a step),
 # taken with the kernels as built; a kernel change makes them stale.
 TRAFFIC_B_PER_CELL = {
-    ("fp64", "sweep_x"): 77.5, ("fp64", "sweep_y"): 117.7, ("fp64", "sweep_z"): 145.4,
-    ("fp32", "sweep_x"): 37.5, ("fp32", "sweep_y"): 57.7, ("fp32", "sweep_z"): 71.9,
-    ("mixed", "sweep_x"): 58.3, ("mixed", "sweep_y"): 78.4, ("mixed", "sweep_z"): 124.9,
+    ("fp64", "sweep_x"): 77.4, ("fp64", "sweep_y"): 117.6, ("fp64", "sweep_z"): 145.3,
+    ("fp32", "sweep_x"): 37.5, ("fp32", "sweep_y"): 57.7, ("fp32", "sweep_z"): 72.0,
+    ("mixed", "sweep_x"): 58.3, ("mixed", "sweep_y"): 78.3, ("mixed", "sweep_z"): 124.8,
 }
 
 # Peaks for an ALU-bound path, derived from unit counts and clocks: 148 SMs x

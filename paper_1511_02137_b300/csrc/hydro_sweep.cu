@@ -643,8 +643,9 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   }
 }
 
+// One single-grid sweep tile per block.
 template <int PREC, int ORDER, int DIR, bool FINAL, bool TMA>
-__global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a, const __grid_constant__ SweepMaps maps) {
+__device__ __forceinline__ void sweep_block(const SweepArgs& a, const SweepMaps& maps) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar, bar_pf;
   TileBars tb{&bar, &bar_pf, 0u, 0u};
@@ -657,6 +658,19 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a, cons
     l0 = blockIdx.x * LANES; a0 = blockIdx.y * SEG;
   }
   sweep_tile<PREC, ORDER, DIR, FINAL, SEG, LANES, TMA>(a, a.jets, a0, l0, blockIdx.z, smem_raw, &maps, &tb);
+}
+
+template <int PREC, int ORDER, int DIR, bool FINAL, bool TMA>
+__global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a, const __grid_constant__ SweepMaps maps) {
+  sweep_block<PREC, ORDER, DIR, FINAL, TMA>(a, maps);
+}
+
+// The FP32 z sweep held to 40 registers (six blocks of 256 threads per SM); left
+// alone it takes 46 and five blocks.  The other sweeps stay at or below 40 by
+// themselves; FP64 and mixed tiles are limited by shared memory first.
+template <int ORDER, bool TMA>
+__global__ void __launch_bounds__(kThreads, 6) sweep_kernel_z32(const SweepArgs a, const __grid_constant__ SweepMaps maps) {
+  sweep_block<HYDRO_FP32, ORDER, 2, true, TMA>(a, maps);
 }
 
 // Resident blocks per SM the batched kernels' register budget is held to: six
@@ -730,6 +744,12 @@ __global__ void reset_vmax_kernel(DevDiag* d, int n) {
   if (i < n) d[i].vmax_bits = 0ull;
 }
 
+template <int PREC, int ORDER, int DIR, bool TMA>
+static auto pick_sweep_kernel() {
+  if constexpr (PREC == HYDRO_FP32 && DIR == 2) return sweep_kernel_z32<ORDER, TMA>;
+  else return sweep_kernel<PREC, ORDER, DIR, DIR == 2, TMA>;
+}
+
 template <int PREC, int ORDER, int DIR>
 static cudaError_t launch_one(const SweepArgs& a, cudaStream_t s, const SweepMaps* maps) {
   using F = typename Types<PREC>::Flux;
@@ -745,13 +765,13 @@ static cudaError_t launch_one(const SweepArgs& a, cudaStream_t s, const SweepMap
   else if (DIR == 1) grid = dim3((a.nx + LANES - 1) / LANES, (a.ny + SEG - 1) / SEG, a.nz);
   else grid = dim3((a.nx + LANES - 1) / LANES, (a.nz + SEG - 1) / SEG, a.ny);
   if (kMapsUsed && maps) {
-    auto kern = sweep_kernel<PREC, ORDER, DIR, DIR == 2, kMapsUsed>;
+    auto kern = pick_sweep_kernel<PREC, ORDER, DIR, kMapsUsed>();
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tma);
     if (err != cudaSuccess) return err;
     kern<<<grid, kThreads, smem_tma, s>>>(a, *maps);
     return cudaGetLastError();
   }
-  auto kern = sweep_kernel<PREC, ORDER, DIR, DIR == 2, false>;
+  auto kern = pick_sweep_kernel<PREC, ORDER, DIR, false>();
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   SweepMaps none;
