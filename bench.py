@@ -38,11 +38,17 @@ METRIC = "cell-updates/s per RK3 step at 256^3 (FP64 vs FP32); % of HBM roofline
 UNIT = "cell-updates/s"
 
 # Algorithmic work per cell of one directional sweep of one RK3 stage (FLOPs
-# with FMA = 2, division and square root = 1; breakdown in the design notes):
-# one interface (LLF split 141 + 10 WENO7 reconstructions x 122 + 5) = 1366,
-# the flux difference, and the per-cell terms the sweep carries (x: primitive
-# recovery, |v|^2, rho_x and F_x; y, z: rho_d and F_d; z: stage combination).
-FLOP_PER_CELL = {"sweep_x": 1428, "sweep_y": 1405, "sweep_z": 1425}
+# with FMA = 2, division and square root = 1), counted on the textbook
+# evaluation: one interface is the LLF split (5 x 14 FMAs + alpha/2 = 141), 10
+# WENO7 reconstructions of 122 (candidates 28, differences 15, A 20, B 4,
+# beta 32, weights 23) and the 5 flux sums, 1366 in all; the x sweep adds the
+# flux difference (10), the primitive recovery (23), |v|^2 (5), rho_x (14) and
+# F_x (10); y and z add difference and accumulation (15), rho_d and F_d; z adds
+# the stage combination (20, averaged over the three stages).
+FLOP_PER_INTERFACE = 141 + 10 * 122 + 5
+FLOP_PER_CELL = {"sweep_x": FLOP_PER_INTERFACE + 10 + 23 + 5 + 14 + 10,
+                 "sweep_y": FLOP_PER_INTERFACE + 15 + 14 + 10,
+                 "sweep_z": FLOP_PER_INTERFACE + 15 + 14 + 10 + 20}
 FLOP_PER_CELL_STEP = 3 * sum(FLOP_PER_CELL.values())
 # Algorithmic HBM bytes per cell per step: 40 field accesses (stage 1 reads 5 and
 # writes 5; stages 2 and 3 read 10 and write 5) in storage precision.

@@ -16,7 +16,7 @@
  * only over independent cells; the one cross-thread reduction is a max (exact),
  * so results do not depend on the thread count.
  *
- * Readings of points the paper leaves open (all listed in the design notes):
+ * Readings of points the paper leaves open:
  *  R1  Conserved vector U = (E, M^x, M^y, M^z, R) with E = T^00, M^i = T^0i and
  *      a passive charge R = n*gamma with flux R*v^j (Sec. 1 names "energy,
  *      momentum and charge densities"; no EOS uses n).

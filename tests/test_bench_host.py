@@ -71,3 +71,21 @@ def test_roofline_arithmetic():
     assert abs(r["frac"] - round(want / bench.PEAK_FP64_TFLOPS, 4)) < 1e-9
     assert abs(sum(r["share"].values()) - 1.0) < 1e-3
     assert abs(bench.PEAK_FP32_TFLOPS - 76.98815) < 1e-3
+
+
+def test_algorithmic_counts_and_traffic_table():
+    """The FLOP counts behind roofline.achieved (122 per WENO7 reconstruction,
+    1366 per interface; 1428 / 1405 / 1425 per cell for the x / y / z sweeps,
+    12774 per cell and RK3 step) and a DRAM figure for every sweep of every
+    precision."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.FLOP_PER_INTERFACE == 1366
+    assert bench.FLOP_PER_CELL == {"sweep_x": 1428, "sweep_y": 1405, "sweep_z": 1425}
+    assert bench.FLOP_PER_CELL_STEP == 12774
+    for p in ("fp64", "fp32", "mixed"):
+        for k in ("sweep_x", "sweep_y", "sweep_z"):
+            assert bench.TRAFFIC_B_PER_CELL[(p, k)] > 0
+    # the stored-state traffic of a sweep is at least its own algorithmic field accesses
+    assert bench.TRAFFIC_B_PER_CELL[("fp64", "sweep_x")] >= 8 * 10 * 0.95
+    assert bench.TRAFFIC_B_PER_CELL[("fp32", "sweep_x")] >= 4 * 10 * 0.9
