@@ -2,26 +2,32 @@
 //
 // A stage evaluates L(U) = -sum_d (Fhat_{i+1/2} - Fhat_{i-1/2})/dx + S and
 // combines it with the step's start state.  It runs as three sweeps, one per
-// axis, each a tiled kernel:
+// axis, each a tiled kernel with one updated cell per thread:
 //
-//   phase 1  stage a halo-padded tile of cells into shared memory: load the
-//            5 conserved fields (coalesced along x), recover primitives in
-//            closed form, and keep U, the half physical flux F_d/2 and the
-//            spectral radius rho_d of every cell;
+//   phase 0  (FP32-flux y and z sweeps) start copying the tile's phase-3
+//            operands (accumulator, step state, mixed: stage state) into
+//            shared memory: one TMA box each, or per-thread cp.async copies;
+//   phase 1  stage a halo-padded tile of cells into shared memory (interior
+//            tiles as one TMA box, edge tiles through clamped or wrapped
+//            coalesced loads), recover primitives in closed form, and keep U,
+//            the half physical flux F_d/2 and the spectral radius rho_d of
+//            every cell;
 //   phase 2  one thread per interface: alpha = max rho_d over the interface's
 //            stencil, local Lax-Friedrichs split f_pm = F/2 +- alpha U/2, and
 //            component-wise WENO reconstruction of f+ (left-biased) and f-
 //            (right-biased, mirrored); Fhat = f+ + f-;
 //   phase 3  one thread per cell: the flux difference goes into the
-//            right-hand-side accumulator (x: write, y: add); the z sweep adds
-//            the jet source at the jet cells and writes the stage combination
-//            a U0 + b (U + dt L) in storage precision.
+//            right-hand-side accumulator (x: write, y: add; FP32-flux tiles
+//            store the box by TMA); the z sweep adds the jet source at the jet
+//            cells and writes the stage combination a U0 + b (U + dt L) in
+//            storage precision.
 //
 // Ghost cells are never stored: halo loads clamp the index (outflow,
 // zero-gradient) or wrap it (periodic).  The x sweep of each stage counts
 // primitive-recovery floors; at the first stage of a step every sweep folds
-// its spectral radii into the step's maximum signal speed with a warp-shuffle
-// reduction and one atomic per block.
+// its spectral radii into the step's maximum signal speed with a warp
+// reduction and one atomic per block.  Element indices are 32-bit (a grid
+// holds at most 4e8 cells).
 #include <cstdint>
 #include <cstring>
 
