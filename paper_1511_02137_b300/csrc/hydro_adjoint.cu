@@ -16,7 +16,9 @@
 // split equally among the stencil cells that tie for the maximum (to 1e-12
 // relative), the symmetric subgradient.  The z sweep adds the adjoint of the jet
 // source of Eqs. 2-3 and accumulates dJ/dk_rad and dJ/dk_coll.  Outflow
-// boundaries only: a clamped ghost hands its adjoint to the edge cell.
+// boundaries only: a clamped ghost hands its adjoint to the edge cell.  The
+// backward recomputes the next segment's states from its checkpoint on a side
+// stream while the main stream reverses the current segment (two buffer sets).
 #include <cmath>
 #include <cstring>
 #include <new>

@@ -8,6 +8,9 @@
 // of every grid, step and stage precomputed on the host in FP64 and uploaded
 // before the replay.  hydro_batch_autotune times the tile shapes each sweep
 // kernel is compiled for on the ensemble itself and keeps the fastest per axis.
+// When every grid meets the TMA layout rules, each grid's tensor maps for the
+// chosen tile shapes sit in the workspace and the persistent kernels stage,
+// fetch and store through them as the single-grid sweeps do.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
