@@ -162,7 +162,10 @@ hydro_status set_tiles(hydro_batch* b) {
     if (b->tma && cudaMemcpyAsync(b->at(b->lay.maps), maps.data(), maps.size() * sizeof(SweepMaps),
                                   cudaMemcpyHostToDevice, b->cs) != cudaSuccess)
       return HYDRO_ECUDA;
-    // the host copy must outlive the asynchronous copy
+    // the host copy must outlive the asynchronous copy.  No launch of this batch is
+    // in flight while the maps are rewritten (every entry point synchronizes the
+    // stream before it returns), and the upload completes before the next launch,
+    // whose TMA copies read the maps after that launch boundary.
     if (cudaStreamSynchronize(b->cs) != cudaSuccess) return HYDRO_ECUDA;
   }
   for (int d = 0; d < 3; ++d) {
