@@ -91,6 +91,20 @@ def test_weno_eps_range_depends_on_the_precision_of_the_weights(hy, precision, e
         assert rc == hy.HYDRO_EINVAL and not h.value
 
 
+@pytest.mark.parametrize("dims", [(1000, 1000, 401), (4, 70000, 4), (4, 4, 70000)])
+def test_grids_beyond_the_32_bit_index_and_launch_limits_are_rejected(hy, dims):
+    """nx ny nz <= 4e8 (32-bit element indices over 5 fields) and ny, nz <= 65535."""
+    c = hy.hydro_config_default(*dims)
+    size = ctypes.c_size_t()
+    assert hy._lib().hydro_workspace_size(ctypes.byref(c), ctypes.byref(size)) == hy.HYDRO_EINVAL
+    if dims[0] * dims[1] * dims[2] > 4e8:   # the adjoint holds the same limit, before allocating
+        h = ctypes.c_void_p()
+        d3 = ctypes.c_double * 3
+        rc = hy._lib().hydro_adjoint_create(ctypes.byref(c), 4, 2, d3(0, 0, 0), d3(1, 0, 0), 30.0, 3.0,
+                                            ctypes.byref(h))
+        assert rc == hy.HYDRO_EINVAL and not h.value
+
+
 def test_misaligned_workspace_is_rejected(hy):
     c = hy.hydro_config_default(8, 8, 8)
     c.workspace = 0x1000 + 8
