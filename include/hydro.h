@@ -19,7 +19,13 @@
  *  - Every function returns a hydro_status and never aborts, prints or throws.
  *  - Host buffers are owned by the caller and only used during the call.
  *  - All device work is issued on the stream given in hydro_config; every
- *    call that returns data synchronises that stream before returning.
+ *    call that returns data synchronises that stream before returning.  The
+ *    library does not link PyTorch: in C a NULL stream is the legacy default
+ *    stream, and the Python binding passes PyTorch's current stream.
+ *  - Device memory: the caller may pass every buffer the library needs
+ *    (hydro_config.workspace; the Python binding passes PyTorch tensors, so
+ *    PyTorch's caching allocator provides all device memory); with a NULL
+ *    workspace the library calls cudaMalloc itself.
  *  - A context is not thread safe; use one context per thread.
  */
 #ifndef HYDRO_H
@@ -39,7 +45,8 @@ typedef enum {
   HYDRO_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
   HYDRO_EUNPHYSICAL = 4, /* NaN or Inf appeared in the state during a step */
   HYDRO_ECFL = 5,        /* max signal speed * dt / dx exceeded cfl_limit */
-  HYDRO_ETIMEOUT = 6,    /* a bounded device-side wait expired */
+  HYDRO_ETIMEOUT = 6,    /* a bounded device-side wait expired (hydro_config.wait_limit_s); the
+                            fields written by that step are invalid: set a new initial state */
   HYDRO_ESTATE = 7       /* call out of order (e.g. hydro_step before hydro_set_initial) */
 } hydro_status;
 
@@ -77,6 +84,18 @@ typedef struct {
                            owned by the caller and kept alive until hydro_destroy; NULL: the
                            library allocates (cudaMalloc) and frees it itself */
   size_t workspace_bytes;
+  double wait_limit_s;  /* time limit of each bounded device-side wait, in seconds of the GPU's
+                           global timer: a tile's wait for its TMA copies into shared memory
+                           (normally a few microseconds).  0: 0.25 s.  Must lie in [0, 10].
+                           A wait that runs out makes the step return HYDRO_ETIMEOUT; the
+                           tile then finishes without the copied data (so that no block leaves
+                           a barrier early and no copy is left in flight at exit), which
+                           leaves the step's results invalid. */
+  int32_t test_withhold_copies; /* fault injection for tests: 1 = tiles arm their copy barriers
+                           but issue no TMA copy, so every such wait runs out and the step
+                           returns HYDRO_ETIMEOUT (nothing is in flight when the tiles exit).
+                           0 in normal use. */
+  int32_t reserved_;    /* zero */
 } hydro_config;
 
 typedef struct hydro_ctx hydro_ctx;
@@ -106,6 +125,10 @@ void hydro_config_default(hydro_config* cfg, int32_t nx, int32_t ny, int32_t nz)
 hydro_status hydro_workspace_size(const hydro_config* cfg, size_t* bytes);
 
 /* Validates cfg, sets up device memory and returns a new context in *out.
+ * The context is the field store of the uniform Cartesian grid of Sec. 1: the
+ * five conserved densities of Eq. 1 (energy, momentum, charge) as SoA arrays,
+ * plus the RK3 stage states and the right-hand-side accumulator; the paper
+ * names no API, so this call is library plumbing around that state.
  * HYDRO_EINVAL: invalid configuration (non-positive sizes or steps, unknown
  * enum values, workspace not aligned); HYDRO_ENOMEM: workspace too small or
  * cudaMalloc failed; HYDRO_ECUDA: other CUDA failure.  On failure *out = NULL. */
@@ -131,17 +154,26 @@ hydro_status hydro_add_jet(hydro_ctx* ctx, const double x0[3], const double dir[
  *   U1 = U + dt L(U, t),  U2 = 3/4 U + 1/4 (U1 + dt L(U1, t+dt)),
  *   U  = 1/3 U + 2/3 (U2 + dt L(U2, t+dt/2)),
  * with L = -div F + S.  Synchronises the stream at the end and returns the
- * first error raised: HYDRO_EUNPHYSICAL (NaN/Inf), HYDRO_ECFL, HYDRO_ECUDA;
- * HYDRO_ESTATE before hydro_set_initial; HYDRO_EINVAL for nsteps < 0. */
+ * first error raised: HYDRO_EUNPHYSICAL (NaN/Inf), HYDRO_ECFL, HYDRO_ECUDA,
+ * HYDRO_ETIMEOUT (a bounded wait ran out: the state is invalid until the
+ * next hydro_set_initial; the CUDA context stays usable); HYDRO_ESTATE before
+ * hydro_set_initial; HYDRO_EINVAL for nsteps < 0. */
 hydro_status hydro_step(hydro_ctx* ctx, int32_t nsteps);
 
 /* Copies the current state to host memory as FP64 (FP32 storage is widened):
- * kind = HYDRO_CONSERVED gives (E, M^x, M^y, M^z, R); kind = HYDRO_PRIMITIVE
- * gives (e, u^x, u^y, u^z, n), recovered on the device in FP64 with the same
- * closed form the step uses.  host5 holds 5*nx*ny*nz doubles. */
+ * kind = HYDRO_CONSERVED gives (E, M^x, M^y, M^z, R), the conserved densities
+ * of Eq. 1; kind = HYDRO_PRIMITIVE gives (e, u^x, u^y, u^z, n), Eq. 1 with
+ * p = e/3 inverted on the device in FP64 with the same closed form the step
+ * uses.  The paper names no read-back call; this is library plumbing (with
+ * hydro_set_initial(HYDRO_CONSERVED) it also checkpoints and resumes a run).
+ * host5 holds 5*nx*ny*nz doubles. */
 hydro_status hydro_read_fields(hydro_ctx* ctx, int32_t kind, double* host5);
 
-/* Fills *out with the context's diagnostics (synchronises the stream). */
+/* Fills *out with the context's diagnostics (synchronises the stream): the
+ * energy and momentum the jets deposited (the time integral of the source
+ * S^nu of Eq. 2 at the rate of Eq. 3, RK3-weighted), the cells they deposited
+ * into, the maximum signal speed and floor counts of the step.  Diagnostic
+ * plumbing: the paper has no counterpart. */
 hydro_status hydro_get_diag(hydro_ctx* ctx, hydro_diag* out);
 
 /* Per-kernel timing with CUDA events on the context's stream, for profiling.
@@ -228,11 +260,19 @@ void hydro_batch_destroy(hydro_batch* b);
  * ------------------------------------------------------------------------- */
 typedef struct hydro_adjoint hydro_adjoint;
 
-/* Sets up an adjoint run (allocates checkpoint, segment and adjoint buffers
- * with cudaMalloc).  HYDRO_EINVAL unless precision is HYDRO_FP64 or
- * HYDRO_MIXED, boundary = HYDRO_OUTFLOW and weno_order = 7, for grids of more
- * than 4e8 cells (the kernels index with 32 bits), or for non-positive sizes or
- * cone. */
+/* Device bytes an adjoint run needs (checkpoints, two sets of segment step and
+ * stage states, adjoint and scratch fields).  HYDRO_EINVAL as hydro_adjoint_create. */
+hydro_status hydro_adjoint_workspace_size(const hydro_config* cfg, int32_t nsteps, int32_t checkpoint_every,
+                                          size_t* bytes);
+
+/* Sets up an adjoint run.  Its buffers come from cfg->workspace (>= the size
+ * above, 256-byte aligned, caller-owned, kept alive until
+ * hydro_adjoint_destroy; the Python binding passes a PyTorch tensor) or, with a
+ * NULL workspace, from cudaMalloc.  HYDRO_EINVAL unless precision is HYDRO_FP64
+ * or HYDRO_MIXED, boundary = HYDRO_OUTFLOW and weno_order = 7, for grids of
+ * more than 4e8 cells (the kernels index with 32 bits), for non-positive sizes
+ * or cone, or a misaligned workspace; HYDRO_ENOMEM: workspace too small or
+ * cudaMalloc failed. */
 hydro_status hydro_adjoint_create(const hydro_config* cfg, int32_t nsteps, int32_t checkpoint_every,
                                   const double apex[3], const double axis[3], double half_angle_deg, double rmax,
                                   hydro_adjoint** out);
@@ -282,20 +322,67 @@ void hydro_adjoint_destroy(hydro_adjoint* a);
  * diagnostics live in one fixed device array inside the library (about
  * 7.9 MB), which every GPU that loads the library holds until the process
  * exits.  The first call on a device, made with that device current, looks up
- * the array's device address (cudaGetSymbolAddress); make that first call
- * before capturing a stream on the device.  Every call uses the same array, so
- * calls that may overlap on the GPU (other streams or threads on the same
- * device) race on it and must be serialised by the caller.  The call clears
- * what must start at zero; it calls no cudaMalloc or cudaFree.
+ * the array's device address (cudaGetSymbolAddress).  Every call copies its
+ * diagnostics to host memory and synchronises cfg->cuda_stream, so the call
+ * cannot be made while that stream is being captured into a CUDA graph.
+ * Every call uses the same array, so calls that may overlap on the GPU (other
+ * streams or threads on the same device) race on it and must be serialised by
+ * the caller.  The call clears what must start at zero; it calls no cudaMalloc
+ * or cudaFree.  Its tiles load their cells with plain loads (no tensor maps),
+ * which gives the same values as hydro_step's TMA staging.
  *
  * Returns HYDRO_ENOMEM when nx*ny*nz > HYDRO_NOALLOC_MAX_CELLS (the fixed
- * array is too small), HYDRO_EINVAL for an invalid configuration, NULL or
- * misaligned d_state, bad jets, step0 < 0 or nsteps < 0, and otherwise the
- * statuses of hydro_step (HYDRO_EUNPHYSICAL, HYDRO_ECFL, HYDRO_ECUDA). */
+ * array is too small), HYDRO_EINVAL for an invalid configuration (the checks
+ * of hydro_create, including ny, nz <= 65535), NULL or misaligned d_state, bad
+ * jets, step0 < 0 or nsteps < 0, and otherwise the statuses of hydro_step
+ * (HYDRO_EUNPHYSICAL, HYDRO_ECFL, HYDRO_ECUDA). */
 hydro_status hydro_step_noalloc(const hydro_config* cfg, void* d_state, int64_t step0, int32_t nsteps,
                                 const double* jets, int32_t njet, hydro_diag* diag_out);
 
-/* Releases the context and any memory the library allocated.  NULL is a no-op. */
+/* ---------------------------------------------------------------------------
+ * Checks of the device arithmetic (test support; the paper has no counterpart).
+ * hydro_eval_math evaluates one of the routines the sweeps use, elementwise
+ * on device memory, so that tests can hold it to its stated error bound
+ * against IEEE arithmetic and the FP64 oracle:
+ *   HYDRO_MATH_RCP          out[i] = 1/in[i] by the FP64 Newton-Raphson
+ *                           reciprocal of the sweeps (normal in[i] with a
+ *                           normal reciprocal); in: n, out: n doubles.
+ *   HYDRO_MATH_SQRT_RSQRT   out[i] = sqrt(in[i]), out[n + i] = 1/sqrt(in[i]) by
+ *                           the FP64 Newton-Raphson pair (in[i] > 0, normal);
+ *                           in: n, out: 2n doubles.
+ *   HYDRO_MATH_C2P_FP64, HYDRO_MATH_C2P_FP32, HYDRO_MATH_C2P_MIXED
+ *                           the closed-form recovery of Eq. 1 with p = e/3
+ *                           (the inverse of the conserved densities) as the
+ *                           FP64, FP32 and mixed-precision sweeps run it: in =
+ *                           (E, M^x, M^y, M^z) as 4 arrays of n doubles (FP32
+ *                           rounds them first, as its storage does), out =
+ *                           (e, v^x, v^y, v^z, floor hit 0/1) as 5 arrays of n
+ *                           doubles; param = e_floor.
+ * Runs on cuda_stream and synchronises it.  HYDRO_EINVAL for an unknown fn,
+ * n < 0 or NULL pointers; HYDRO_ECUDA on a launch failure. */
+enum {
+  HYDRO_MATH_RCP = 0,
+  HYDRO_MATH_SQRT_RSQRT = 1,
+  HYDRO_MATH_C2P_FP64 = 2,
+  HYDRO_MATH_C2P_FP32 = 3,
+  HYDRO_MATH_C2P_MIXED = 4
+};
+hydro_status hydro_eval_math(int32_t fn, int64_t n, const double* d_in, double* d_out, double param,
+                             void* cuda_stream);
+
+/* ---------------------------------------------------------------------------
+ * Measurement support for the roofline (the paper has no counterpart).
+ * hydro_alu_peak times a throughput kernel of independent fused multiply-add
+ * chains filling every SM (HYDRO_PEAK_FFMA: FP32 FMA; HYDRO_PEAK_FFMA2: the
+ * packed FP32x2 FMA; HYDRO_PEAK_DFMA: FP64 FMA), `iters` iterations of 8
+ * chains per thread, with CUDA events on cuda_stream.  *flop receives the
+ * floating-point operations performed (an FMA counts 2) and *ms the kernel
+ * time.  Allocates nothing.  HYDRO_EINVAL for an unknown kind or iters < 1. */
+enum { HYDRO_PEAK_FFMA = 0, HYDRO_PEAK_FFMA2 = 1, HYDRO_PEAK_DFMA = 2 };
+hydro_status hydro_alu_peak(int32_t kind, int64_t iters, void* cuda_stream, double* flop, double* ms);
+
+/* Releases the context and any memory the library allocated (library
+ * plumbing; the paper has no counterpart).  NULL is a no-op. */
 void hydro_destroy(hydro_ctx* ctx);
 
 /* Static string naming a status code. */

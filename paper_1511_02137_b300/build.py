@@ -18,7 +18,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libhydro.so")
-SOURCES = ["hydro_api.cu", "hydro_sweep.cu", "hydro_noalloc.cu", "hydro_batch.cu", "hydro_adjoint.cu"]
+SOURCES = ["hydro_api.cu", "hydro_sweep.cu", "hydro_noalloc.cu", "hydro_batch.cu", "hydro_adjoint.cu",
+           "hydro_mathcheck.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

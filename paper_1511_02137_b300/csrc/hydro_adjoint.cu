@@ -552,6 +552,7 @@ struct hydro_adjoint {
   int nsteps = 0, every = 0, nckpt = 0;
   cudaStream_t stream = nullptr;
   char* ws = nullptr;
+  bool owns_ws = false;          // ws came from cudaMalloc (no caller workspace)
   std::vector<double*> ckpt;     // states at steps 0, every, 2 every, ...
   std::vector<double*> seg;      // (every + 1) step states for the recomputed segment
   double* rhs = nullptr;
@@ -703,31 +704,89 @@ cudaError_t combine(hydro_adjoint* a, int mode, int st) {
   return cudaGetLastError();
 }
 
+// The run configurations the adjoint supports: FP64 or mixed, outflow, WENO7,
+// the forward's grid limits, at least one step and checkpoint interval.
+bool adjoint_config_ok(const hydro_config* cfg, int32_t nsteps, int32_t checkpoint_every) {
+  if (!config_valid(cfg, kCheckGrid | kCheckWorkspace)) return false;
+  if ((cfg->precision != HYDRO_FP64 && cfg->precision != HYDRO_MIXED) || cfg->boundary != HYDRO_OUTFLOW ||
+      cfg->weno_order != 7 || cfg->test_withhold_copies != 0)
+    return false;
+  return nsteps >= 1 && checkpoint_every >= 1;
+}
+
+// Lays out the run's buffers from base (256-byte aligned pieces) and returns the
+// bytes they take; with base == nullptr only the size is computed.
+size_t adjoint_layout(hydro_adjoint* a, char* base) {
+  char* p = base;
+  size_t used = 0;
+  auto take = [&](size_t b) {
+    char* q = p;
+    const size_t s = (b + 255) / 256 * 256;
+    used += s;
+    if (p) p += s;
+    return q;
+  };
+  const size_t n = a->n, f5 = 5 * n * sizeof(double);
+  a->ckpt.clear();
+  a->seg.clear();
+  a->stages.clear();
+  a->seg_b.clear();
+  a->stages_b.clear();
+  for (int k = 0; k < a->nckpt; ++k) a->ckpt.push_back(reinterpret_cast<double*>(take(f5)));
+  for (int k = 0; k <= a->every; ++k) a->seg.push_back(reinterpret_cast<double*>(take(f5)));
+  for (int k = 0; k < 2 * a->every; ++k) a->stages.push_back(reinterpret_cast<double*>(take(f5)));
+  a->rhs = reinterpret_cast<double*>(take(f5));
+  for (int k = 0; k <= a->every; ++k) a->seg_b.push_back(reinterpret_cast<double*>(take(f5)));
+  for (int k = 0; k < 2 * a->every; ++k) a->stages_b.push_back(reinterpret_cast<double*>(take(f5)));
+  a->rhs_b = reinterpret_cast<double*>(take(f5));
+  a->lamA = reinterpret_cast<double*>(take(f5));
+  a->lamB = reinterpret_cast<double*>(take(f5));
+  a->lam0 = reinterpret_cast<double*>(take(f5));
+  a->r = reinterpret_cast<double*>(take(f5));
+  a->prim = reinterpret_cast<double*>(take(f5));
+  if (a->cfg.precision == HYDRO_MIXED) {
+    a->sh = reinterpret_cast<float*>(take(7 * n * sizeof(float)));
+    a->lamf = reinterpret_cast<float*>(take(5 * n * sizeof(float)));
+  }
+  a->kbar = reinterpret_cast<double*>(take(2 * kMaxJets * sizeof(double)));
+  a->partial = reinterpret_cast<double*>(take(kConeBlocks * sizeof(double)));
+  a->diag = reinterpret_cast<DevDiag*>(take(sizeof(DevDiag)));
+  return used;
+}
+
+// Fills the size fields of a run (grid cells, steps, checkpoint interval and count).
+void adjoint_sizes(hydro_adjoint* a, const hydro_config* cfg, int32_t nsteps, int32_t checkpoint_every) {
+  a->cfg = *cfg;
+  a->n = (size_t)cfg->nx * cfg->ny * cfg->nz;
+  a->nsteps = nsteps;
+  a->every = checkpoint_every < nsteps ? checkpoint_every : nsteps;
+  a->nckpt = (nsteps + a->every - 1) / a->every;
+}
+
 }  // namespace
 
 extern "C" {
+
+hydro_status hydro_adjoint_workspace_size(const hydro_config* cfg, int32_t nsteps, int32_t checkpoint_every,
+                                          size_t* bytes) {
+  if (!bytes || !adjoint_config_ok(cfg, nsteps, checkpoint_every)) return HYDRO_EINVAL;
+  hydro_adjoint probe;
+  adjoint_sizes(&probe, cfg, nsteps, checkpoint_every);
+  *bytes = adjoint_layout(&probe, nullptr);
+  return HYDRO_OK;
+}
 
 hydro_status hydro_adjoint_create(const hydro_config* cfg, int32_t nsteps, int32_t checkpoint_every,
                                   const double apex[3], const double axis[3], double half_angle_deg, double rmax,
                                   hydro_adjoint** out) {
   if (!out) return HYDRO_EINVAL;
   *out = nullptr;
-  if (!cfg || (cfg->precision != HYDRO_FP64 && cfg->precision != HYDRO_MIXED) || cfg->boundary != HYDRO_OUTFLOW ||
-      cfg->weno_order != 7)
-    return HYDRO_EINVAL;
-  if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1 || nsteps < 1 || checkpoint_every < 1 || !apex || !axis)
-    return HYDRO_EINVAL;
-  if ((double)cfg->nx * cfg->ny * cfg->nz > 4.0e8) return HYDRO_EINVAL;   // 32-bit indices, as the forward
-  if (!(cfg->dx > 0.0) || !(cfg->dt > 0.0) || !(cfg->e_floor > 0.0) || !weno_eps_ok(cfg->precision, cfg->weno_eps)) return HYDRO_EINVAL;
+  if (!adjoint_config_ok(cfg, nsteps, checkpoint_every) || !apex || !axis) return HYDRO_EINVAL;
   const double al = std::sqrt(axis[0] * axis[0] + axis[1] * axis[1] + axis[2] * axis[2]);
   if (!(al > 0.0) || !(rmax > 0.0) || !(half_angle_deg > 0.0 && half_angle_deg < 180.0)) return HYDRO_EINVAL;
   hydro_adjoint* a = new (std::nothrow) hydro_adjoint;
   if (!a) return HYDRO_ENOMEM;
-  a->cfg = *cfg;
-  a->n = (size_t)cfg->nx * cfg->ny * cfg->nz;
-  a->nsteps = nsteps;
-  a->every = checkpoint_every < nsteps ? checkpoint_every : nsteps;
-  a->nckpt = (nsteps + a->every - 1) / a->every;
+  adjoint_sizes(a, cfg, nsteps, checkpoint_every);
   a->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
   for (int k = 0; k < 3; ++k) {
     a->cone.apex[k] = apex[k];
@@ -741,41 +800,22 @@ hydro_status hydro_adjoint_create(const hydro_config* cfg, int32_t nsteps, int32
   a->cone.ny = cfg->ny;
   a->cone.nz = cfg->nz;
   // buffers: checkpoints, the segment's step states and stage states, adjoints, scratch
-  const size_t f5 = 5 * a->n * sizeof(double);
-  const size_t nbuf = (size_t)a->nckpt + 2 * ((size_t)(a->every + 1) + 2 * (size_t)a->every + 1) + 4 + 1;
-  const size_t shadow = cfg->precision == HYDRO_MIXED ? 12 * a->n * sizeof(float) + 512 : 0;
-  const size_t bytes = nbuf * f5 + a->n * sizeof(double) + 2 * kMaxJets * sizeof(double) +
-                       kConeBlocks * sizeof(double) + sizeof(DevDiag) + shadow + 4096;
-  if (cudaMalloc(&a->ws, bytes) != cudaSuccess) {
-    cudaGetLastError();
-    delete a;
-    return HYDRO_ENOMEM;
+  const size_t bytes = adjoint_layout(a, nullptr);
+  if (cfg->workspace) {
+    if (cfg->workspace_bytes < bytes) {
+      delete a;
+      return HYDRO_ENOMEM;
+    }
+    a->ws = static_cast<char*>(cfg->workspace);
+  } else {
+    if (cudaMalloc(&a->ws, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      delete a;
+      return HYDRO_ENOMEM;
+    }
+    a->owns_ws = true;
   }
-  char* p = a->ws;
-  auto take = [&](size_t b) {
-    char* q = p;
-    p += (b + 255) / 256 * 256;
-    return q;
-  };
-  for (int k = 0; k < a->nckpt; ++k) a->ckpt.push_back(reinterpret_cast<double*>(take(f5)));
-  for (int k = 0; k <= a->every; ++k) a->seg.push_back(reinterpret_cast<double*>(take(f5)));
-  for (int k = 0; k < 2 * a->every; ++k) a->stages.push_back(reinterpret_cast<double*>(take(f5)));
-  a->rhs = reinterpret_cast<double*>(take(f5));
-  for (int k = 0; k <= a->every; ++k) a->seg_b.push_back(reinterpret_cast<double*>(take(f5)));
-  for (int k = 0; k < 2 * a->every; ++k) a->stages_b.push_back(reinterpret_cast<double*>(take(f5)));
-  a->rhs_b = reinterpret_cast<double*>(take(f5));
-  a->lamA = reinterpret_cast<double*>(take(f5));
-  a->lamB = reinterpret_cast<double*>(take(f5));
-  a->lam0 = reinterpret_cast<double*>(take(f5));
-  a->r = reinterpret_cast<double*>(take(f5));
-  a->prim = reinterpret_cast<double*>(take(f5));
-  if (cfg->precision == HYDRO_MIXED) {
-    a->sh = reinterpret_cast<float*>(take(7 * a->n * sizeof(float)));
-    a->lamf = reinterpret_cast<float*>(take(5 * a->n * sizeof(float)));
-  }
-  a->kbar = reinterpret_cast<double*>(take(2 * kMaxJets * sizeof(double)));
-  a->partial = reinterpret_cast<double*>(take(kConeBlocks * sizeof(double)));
-  a->diag = reinterpret_cast<DevDiag*>(take(sizeof(DevDiag)));
+  adjoint_layout(a, a->ws);
   bool ok = cudaStreamCreateWithFlags(&a->side, cudaStreamNonBlocking) == cudaSuccess &&
             cudaEventCreateWithFlags(&a->ev_start, cudaEventDisableTiming) == cudaSuccess;
   for (int k = 0; k < 2 && ok; ++k)
@@ -953,7 +993,7 @@ void hydro_adjoint_destroy(hydro_adjoint* a) {
   }
   for (cudaEvent_t e : {a->ev_start, a->ev_ready[0], a->ev_ready[1], a->ev_free[0], a->ev_free[1]})
     if (e) cudaEventDestroy(e);
-  if (a->ws) cudaFree(a->ws);
+  if (a->owns_ws && a->ws) cudaFree(a->ws);
   delete a;
 }
 

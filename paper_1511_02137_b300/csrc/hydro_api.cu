@@ -13,6 +13,25 @@
 
 using namespace hydro;
 
+bool hydro::config_valid(const hydro_config* c, unsigned what) {
+  if (!c) return false;
+  if (what & kCheckGrid) {
+    if (c->nx < 1 || c->ny < 1 || c->nz < 1) return false;
+    if ((double)c->nx * c->ny * c->nz > 4.0e8) return false;   // 32-bit grid indices, 5 fields
+    if (c->nz > 65535 || c->ny > 65535) return false;          // grid z/y launch limits
+  }
+  if (c->precision < HYDRO_FP64 || c->precision > HYDRO_MIXED) return false;
+  if (c->boundary != HYDRO_OUTFLOW && c->boundary != HYDRO_PERIODIC) return false;
+  if (c->weno_order != 7 && c->weno_order != 5) return false;
+  if (!(c->dx > 0.0) || !(c->dt > 0.0) || !std::isfinite(c->t0)) return false;
+  if (!(c->hbarc > 0.0) || !(c->dof > 0.0) || !(c->e_floor > 0.0) || !weno_eps_ok(c->precision, c->weno_eps)) return false;
+  if (!std::isfinite(c->k_rad) || !std::isfinite(c->k_coll) || !std::isfinite(c->cr_over_cf)) return false;
+  if (!(c->wait_limit_s >= 0.0 && c->wait_limit_s <= 10.0)) return false;
+  if (c->test_withhold_copies != 0 && c->test_withhold_copies != 1) return false;
+  if ((what & kCheckWorkspace) && c->workspace && ((uintptr_t)c->workspace % 256) != 0) return false;
+  return true;
+}
+
 namespace {
 
 constexpr size_t kAlign = 256;
@@ -39,20 +58,7 @@ Layout layout_for(const hydro_config& c) {
   return L;
 }
 
-bool config_ok(const hydro_config* c) {
-  if (!c) return false;
-  if (c->nx < 1 || c->ny < 1 || c->nz < 1) return false;
-  if ((double)c->nx * c->ny * c->nz > 4.0e8) return false;   // 32-bit grid indices, 5 fields
-  if (c->nz > 65535 || c->ny > 65535) return false;          // grid z/y launch limits
-  if (c->precision < HYDRO_FP64 || c->precision > HYDRO_MIXED) return false;
-  if (c->boundary != HYDRO_OUTFLOW && c->boundary != HYDRO_PERIODIC) return false;
-  if (c->weno_order != 7 && c->weno_order != 5) return false;
-  if (!(c->dx > 0.0) || !(c->dt > 0.0) || !std::isfinite(c->t0)) return false;
-  if (!(c->hbarc > 0.0) || !(c->dof > 0.0) || !(c->e_floor > 0.0) || !weno_eps_ok(c->precision, c->weno_eps)) return false;
-  if (!std::isfinite(c->k_rad) || !std::isfinite(c->k_coll) || !std::isfinite(c->cr_over_cf)) return false;
-  if (c->workspace && ((uintptr_t)c->workspace % kAlign) != 0) return false;
-  return true;
-}
+bool config_ok(const hydro_config* c) { return config_valid(c, kCheckGrid | kCheckWorkspace); }
 
 struct Prof {
   std::vector<cudaEvent_t> ev[HYDRO_KERNEL_COUNT];   // start/stop pairs, resolved at query time
@@ -281,6 +287,8 @@ hydro_status hydro_step(hydro_ctx* c, int32_t nsteps) {
   a.src.t4coef = g.hbarc * g.hbarc * g.hbarc / (M_PI * M_PI / 30.0 * g.dof);
   const double vol = g.dx * g.dx * g.dx;
   a.src.inv_vol = 1.0 / vol;
+  a.wait_ns = wait_limit_ns(g);
+  a.withhold = g.test_withhold_copies;
   cudaError_t err = cudaSuccess;
   for (int32_t s = 0; s < nsteps && err == cudaSuccess; ++s) {
     const int64_t n = c->steps;

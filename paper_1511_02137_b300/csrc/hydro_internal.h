@@ -61,6 +61,22 @@ inline bool weno_eps_ok(int precision, double eps) {
   return precision == HYDRO_FP64 ? (eps >= 1e-20 && eps <= 1e20) : (eps >= 1e-18 && eps <= 1e18);
 }
 
+// Default limit of a bounded device-side wait (hydro_config.wait_limit_s = 0), in ns.
+constexpr unsigned long long kDefaultWaitNs = 250000000ull;
+
+// The limit of a bounded wait in ns of the GPU's global timer.
+inline unsigned long long wait_limit_ns(const hydro_config& c) {
+  return c.wait_limit_s > 0.0 ? (unsigned long long)(c.wait_limit_s * 1e9) : kDefaultWaitNs;
+}
+
+// Configuration checks shared by every entry point.  The scheme and physics
+// fields are always checked; kCheckGrid adds the grid size (nx, ny, nz >= 1,
+// nx ny nz <= 4e8 for the 32-bit element indices, ny and nz <= 65535 for the
+// launch-grid y and z dimensions of the single-grid sweeps); kCheckWorkspace
+// the workspace alignment (256 bytes).
+enum : unsigned { kCheckGrid = 1u, kCheckWorkspace = 2u };
+bool config_valid(const hydro_config* c, unsigned what);
+
 // Everything a sweep tile needs except the jet list.
 struct GridArgs {
   const void* U;    // state the right-hand side is evaluated on
@@ -77,6 +93,8 @@ struct GridArgs {
   double eps;       // WENO epsilon
   int reduce_speed; // 1: fold spectral radii into diag->vmax_bits
   int count_floors; // 1: count floor hits (x sweep of each stage)
+  unsigned long long wait_ns;  // limit of each bounded wait on a TMA copy (0: kDefaultWaitNs)
+  int withhold;     // fault injection: arm the copy barriers but issue no TMA copy
   SourceCoef src;
   LaunchConst k;    // filled by the launchers from the fields above
 };
@@ -110,6 +128,7 @@ struct BatchArgs {
   const JetStage* jets;   // one per event, for this stage
   double inv_dx, dt, a, b, e_floor, eps;
   int reduce_speed, count_floors;
+  unsigned long long wait_ns;   // limit of each bounded wait on a TMA copy (0: kDefaultWaitNs)
   SourceCoef src;
   LaunchConst k;    // filled by launch_batch_sweep
   const SweepMaps* maps;   // [nev] tensor maps of this launch's stage and axis, or NULL (plain loads)

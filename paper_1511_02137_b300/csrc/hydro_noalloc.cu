@@ -29,7 +29,6 @@ namespace {
 
 using hydro::DevDiag;
 using hydro::SweepArgs;
-using hydro::weno_eps_ok;
 
 constexpr size_t kNoAllocMaxCells = HYDRO_NOALLOC_MAX_CELLS;
 constexpr size_t kAlign = 256;
@@ -63,17 +62,9 @@ hydro_status scratch_address(void** out) {
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-bool config_ok(const hydro_config* c) {
-  if (!c) return false;
-  if (c->nx < 1 || c->ny < 1 || c->nz < 1) return false;
-  if (c->precision < HYDRO_FP64 || c->precision > HYDRO_MIXED) return false;
-  if (c->boundary != HYDRO_OUTFLOW && c->boundary != HYDRO_PERIODIC) return false;
-  if (c->weno_order != 7 && c->weno_order != 5) return false;
-  if (!(c->dx > 0.0) || !(c->dt > 0.0) || !std::isfinite(c->t0)) return false;
-  if (!(c->hbarc > 0.0) || !(c->dof > 0.0) || !(c->e_floor > 0.0) || !weno_eps_ok(c->precision, c->weno_eps)) return false;
-  if (!std::isfinite(c->k_rad) || !std::isfinite(c->k_coll) || !std::isfinite(c->cr_over_cf)) return false;
-  return true;
-}
+// The checks of hydro_create (grid size and launch limits included); the
+// workspace field is ignored here.
+bool config_ok(const hydro_config* c) { return hydro::config_valid(c, hydro::kCheckGrid); }
 
 }  // namespace
 
@@ -137,6 +128,7 @@ extern "C" hydro_status hydro_step_noalloc(const hydro_config* cfg, void* d_stat
   a.src.t4coef = cfg->hbarc * cfg->hbarc * cfg->hbarc / (M_PI * M_PI / 30.0 * cfg->dof);
   const double vol = cfg->dx * cfg->dx * cfg->dx;
   a.src.inv_vol = 1.0 / vol;
+  a.wait_ns = hydro::wait_limit_ns(*cfg);   // (plain loads: no TMA copy waits here)
   const int N[3] = {cfg->nx, cfg->ny, cfg->nz};
   for (int32_t s = 0; s < nsteps && err == cudaSuccess; ++s) {
     const int64_t step = step0 + s;

@@ -137,11 +137,22 @@ __device__ __forceinline__ void cp_async_ca(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// Spins on the barrier phase with an iteration limit; false when it gave up.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned phase) {
-  for (long it = 0; it < (1L << 24); ++it)
-    if (mbar_try_wait(bar, phase)) return true;
-  return false;
+// The GPU's global nanosecond timer.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Waits for the barrier phase for at most limit_ns of global time (try_wait
+// itself suspends the thread for a while between checks); false when the limit
+// ran out first.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned phase, unsigned long long limit_ns) {
+  if (mbar_try_wait(bar, phase)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, phase))
+    if (global_ns() - t0 > limit_ns) return false;
+  return true;
 }
 
 // Block-wide max of the spectral radius and sum of floor hits, published with
@@ -252,10 +263,13 @@ __device__ __forceinline__ void init_tile_bars(TileBars& tb) {
   tb.ph_pf = 0;
 }
 
+// A bounded wait for a TMA copy that runs out sets the status word and, when
+// given, *late (shared memory); after a second bounded wait for the copy the
+// tile finishes on whatever shared memory holds.
 template <int PREC, int ORDER, int DIR, bool FINAL, int SEG, int LANES, bool TMA = false>
 __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& jets, int a0, int l0, int fixed,
                                            unsigned char* smem_raw, const SweepMaps* maps = nullptr,
-                                           TileBars* tb = nullptr) {
+                                           TileBars* tb = nullptr, int* late = nullptr) {
   using Store = typename Types<PREC>::Store;
   using F = typename Types<PREC>::Flux;
   using Math = typename Types<PREC>::Math;
@@ -306,10 +320,12 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
                                         (need_u0 ? 5 * NC * sizeof(Store) : 0) +
                                         (FINAL && PREC == HYDRO_MIXED ? 5 * NC * sizeof(Store) : 0));
       mbar_expect_tx(tb->pf, bytes);
-      const int c1 = DIR == 1 ? a0 : fixed, c2 = DIR == 1 ? fixed : a0;
-      tma_load_4d(sPr, &maps->rhs, l0, c1, c2, 0, tb->pf);
-      if (need_u0) tma_load_4d(sP0, &maps->u0, l0, c1, c2, 0, tb->pf);
-      if (FINAL && PREC == HYDRO_MIXED) tma_load_4d(sP0 + 5 * NC, &maps->ust, l0, c1, c2, 0, tb->pf);
+      if (!a.withhold) {
+        const int c1 = DIR == 1 ? a0 : fixed, c2 = DIR == 1 ? fixed : a0;
+        tma_load_4d(sPr, &maps->rhs, l0, c1, c2, 0, tb->pf);
+        if (need_u0) tma_load_4d(sP0, &maps->u0, l0, c1, c2, 0, tb->pf);
+        if (FINAL && PREC == HYDRO_MIXED) tma_load_4d(sP0 + 5 * NC, &maps->ust, l0, c1, c2, 0, tb->pf);
+      }
     }
   } else if constexpr (PF::on) {
     const bool need_u0 = FINAL && !a.k.first;
@@ -364,11 +380,19 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
     if (a0 - G >= 0 && a0 + SEG + G <= n_along && l0 + LANES <= n_lane) {
       if (threadIdx.x == 0) {
         mbar_expect_tx(tb->stage, (unsigned)(5 * NCS * sizeof(Store)));
-        if (DIR == 0) tma_load_4d(sStage, &maps->stage, a0 - G, l0, fixed, 0, tb->stage);
+        if (a.withhold) {
+          // fault injection: the barrier is armed but no copy is issued
+        } else if (DIR == 0) tma_load_4d(sStage, &maps->stage, a0 - G, l0, fixed, 0, tb->stage);
         else if (DIR == 1) tma_load_4d(sStage, &maps->stage, l0, a0 - G, fixed, 0, tb->stage);
         else tma_load_4d(sStage, &maps->stage, l0, fixed, a0 - G, 0, tb->stage);
       }
-      if (!mbar_wait_bounded(tb->stage, tb->ph_stage)) atomicCAS(&a.diag->status, 0, (int)HYDRO_ETIMEOUT);
+      if (!mbar_wait_bounded(tb->stage, tb->ph_stage, a.wait_ns)) {
+        atomicCAS(&a.diag->status, 0, (int)HYDRO_ETIMEOUT);
+        if (late) *late = 1;
+        // the copy may still land: wait once more (bounded) so that none is left
+        // in flight into this block's shared memory; a withheld copy never comes
+        if (!a.withhold) mbar_wait_bounded(tb->stage, tb->ph_stage, a.wait_ns);
+      }
       tb->ph_stage ^= 1u;
       staged = true;
     }
@@ -544,7 +568,11 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   const F inv_dx = kconst<F>(a.inv_dx, a.k.inv_dx_f);
   bool bad = false;
   if constexpr (PF::on && TMA) {
-    if (!mbar_wait_bounded(tb->pf, tb->ph_pf)) atomicCAS(&a.diag->status, 0, (int)HYDRO_ETIMEOUT);
+    if (!mbar_wait_bounded(tb->pf, tb->ph_pf, a.wait_ns)) {
+      atomicCAS(&a.diag->status, 0, (int)HYDRO_ETIMEOUT);
+      if (late) *late = 1;
+      if (!a.withhold) mbar_wait_bounded(tb->pf, tb->ph_pf, a.wait_ns);   // as for the staging copy
+    }
     tb->ph_pf ^= 1u;
   } else if constexpr (PF::on) {
     cp_async_wait_all();   // each thread reads only its own copies
@@ -698,8 +726,11 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<PREC>()) batch_swee
   __shared__ __align__(16) int4 tdq[2];   // this tile's descriptor and the next one's, copied ahead
   __shared__ int4 td;
   __shared__ __align__(8) uint64_t bar, bar_pf;
+  __shared__ int sLate;   // a wait of this block ran out (set once, never cleared)
   TileBars tb{&bar, &bar_pf, 0u, 0u};
-  if constexpr (TMA) init_tile_bars(tb);
+  if (threadIdx.x == 0) sLate = 0;
+  if constexpr (TMA) init_tile_bars(tb);   // (its barrier also orders sLate = 0)
+  else __syncthreads();
   if (threadIdx.x == 0 && blockIdx.x < b.ntiles) {
     cp_async_ca<16>(&tdq[0], &b.tiles[blockIdx.x]);
     cp_async_commit();
@@ -731,18 +762,26 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<PREC>()) batch_swee
       g.eps = b.eps;
       g.reduce_speed = b.reduce_speed;
       g.count_floors = b.count_floors;
+      g.wait_ns = b.wait_ns;
+      g.withhold = 0;
       g.src = b.src;
       g.k = b.k;
     }
     __syncthreads();
     const int4 tile = td;
     sweep_tile<PREC, 7, DIR, FINAL, SEG, LANES, TMA>(g, b.jets[tile.x], tile.y, tile.z, tile.w, smem_raw,
-                                                     TMA ? b.maps + tile.x : nullptr, &tb);
+                                                     TMA ? b.maps + tile.x : nullptr, &tb, &sLate);
     // the next tile overwrites shared memory, partly by TMA: order this tile's
     // generic-proxy writes before the async proxy's
     if constexpr (TMA) fence_proxy_async_smem();
     __syncthreads();
+    // after a wait that ran out the barriers' phases are no longer known: the
+    // whole block stops (the step reports HYDRO_ETIMEOUT).  sLate is written only
+    // inside a tile, so every thread reads the same value here.
+    if (sLate) break;
   }
+  // a block that stopped early may still have the next descriptor's copy in flight
+  if (threadIdx.x == 0) cp_async_wait_all();
 }
 
 __global__ void reset_vmax_kernel(DevDiag* d, int n) {
@@ -819,6 +858,7 @@ cudaError_t launch_sweep(int precision, int order, int dir, const SweepArgs& arg
                          const SweepMaps* tmap) {
   SweepArgs a = args;
   a.k = derive_constants(a, order);
+  if (a.wait_ns == 0) a.wait_ns = kDefaultWaitNs;
   switch (precision) {
     case HYDRO_FP64: return launch_order<HYDRO_FP64>(order, dir, a, s, tmap);
     case HYDRO_FP32: return launch_order<HYDRO_FP32>(order, dir, a, s, tmap);
@@ -1023,6 +1063,7 @@ static int batch_occupancy_prec(int dir, int variant, bool tma) {
 cudaError_t launch_batch_sweep(int precision, int dir, int variant, const BatchArgs& args, int grid, cudaStream_t s) {
   if (grid <= 0 || args.ntiles <= 0) return cudaSuccess;
   BatchArgs a = args;
+  if (a.wait_ns == 0) a.wait_ns = kDefaultWaitNs;
   GridArgs g;
   g.inv_dx = a.inv_dx;
   g.dt = a.dt;

@@ -22,6 +22,8 @@ HYDRO_OUTFLOW, HYDRO_PERIODIC = 0, 1
 HYDRO_PRIMITIVE, HYDRO_CONSERVED = 0, 1
 HYDRO_KERNEL_SWEEP_X, HYDRO_KERNEL_SWEEP_Y, HYDRO_KERNEL_SWEEP_Z, HYDRO_KERNEL_OTHER = 0, 1, 2, 3
 HYDRO_MAX_JETS = 16
+HYDRO_MATH_RCP, HYDRO_MATH_SQRT_RSQRT, HYDRO_MATH_C2P_FP64, HYDRO_MATH_C2P_FP32, HYDRO_MATH_C2P_MIXED = range(5)
+HYDRO_PEAK_FFMA, HYDRO_PEAK_FFMA2, HYDRO_PEAK_DFMA = range(3)
 PRECISIONS = {"fp64": HYDRO_FP64, "fp32": HYDRO_FP32, "mixed": HYDRO_MIXED}
 
 
@@ -33,7 +35,8 @@ class hydro_config(ctypes.Structure):
                 ("hbarc", ctypes.c_double), ("dof", ctypes.c_double), ("e_floor", ctypes.c_double),
                 ("weno_eps", ctypes.c_double), ("cfl_limit", ctypes.c_double),
                 ("cuda_stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
-                ("workspace_bytes", ctypes.c_size_t)]
+                ("workspace_bytes", ctypes.c_size_t), ("wait_limit_s", ctypes.c_double),
+                ("test_withhold_copies", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
 
 
 class hydro_diag(ctypes.Structure):
@@ -87,16 +90,21 @@ def _lib():
         lib.hydro_batch_get_diag.argtypes = [vp, ctypes.c_int32, P(hydro_diag)]
         lib.hydro_batch_destroy.argtypes = [vp]
         lib.hydro_batch_destroy.restype = None
+        lib.hydro_adjoint_workspace_size.argtypes = [P(hydro_config), ctypes.c_int32, ctypes.c_int32,
+                                                     P(ctypes.c_size_t)]
         lib.hydro_adjoint_create.argtypes = [P(hydro_config), ctypes.c_int32, ctypes.c_int32, dp, dp, ctypes.c_double,
                                              ctypes.c_double, P(vp)]
+        lib.hydro_eval_math.argtypes = [ctypes.c_int32, ctypes.c_int64, vp, vp, ctypes.c_double, vp]
+        lib.hydro_alu_peak.argtypes = [ctypes.c_int32, ctypes.c_int64, vp, dp, dp]
         lib.hydro_adjoint_add_jet.argtypes = [vp, dp, dp, ctypes.c_double]
         lib.hydro_adjoint_set_params.argtypes = [vp, ctypes.c_double, ctypes.c_double]
         lib.hydro_adjoint_forward.argtypes = [vp, vp, dp]
         lib.hydro_adjoint_backward.argtypes = [vp, ctypes.c_double, dp, dp, vp]
         lib.hydro_adjoint_destroy.argtypes = [vp]
         lib.hydro_adjoint_destroy.restype = None
-        for name in ("hydro_adjoint_create", "hydro_adjoint_add_jet", "hydro_adjoint_set_params",
-                     "hydro_adjoint_forward", "hydro_adjoint_backward"):
+        for name in ("hydro_adjoint_workspace_size", "hydro_adjoint_create", "hydro_adjoint_add_jet",
+                     "hydro_adjoint_set_params", "hydro_adjoint_forward", "hydro_adjoint_backward",
+                     "hydro_eval_math", "hydro_alu_peak"):
             getattr(lib, name).restype = ctypes.c_int
         for name in ("hydro_workspace_size", "hydro_create", "hydro_set_initial", "hydro_add_jet", "hydro_step",
                      "hydro_read_fields", "hydro_get_diag", "hydro_profile_enable", "hydro_profile_query",
@@ -337,13 +345,14 @@ def hydro_batch_destroy(b: Batch) -> None:
 
 
 class Adjoint:
-    """Opaque hydro_adjoint handle."""
+    """Opaque hydro_adjoint handle plus the torch workspace tensor that backs it."""
 
-    def __init__(self, handle, cfg, nsteps, every):
+    def __init__(self, handle, cfg, nsteps, every, workspace=None):
         self.handle = handle
         self.cfg = cfg
         self.nsteps = nsteps
         self.every = every
+        self.workspace = workspace
         self.cells = cfg.nx * cfg.ny * cfg.nz
 
     def __del__(self):
@@ -351,17 +360,31 @@ class Adjoint:
             hydro_adjoint_destroy(self)
 
 
+def hydro_adjoint_workspace_size(cfg: hydro_config, nsteps: int, checkpoint_every: int) -> int:
+    n = ctypes.c_size_t()
+    _check(_lib().hydro_adjoint_workspace_size(ctypes.byref(cfg), nsteps, checkpoint_every, ctypes.byref(n)),
+           "hydro_adjoint_workspace_size")
+    return n.value
+
+
 def hydro_adjoint_create(cfg: hydro_config, nsteps: int, checkpoint_every: int, apex, axis,
-                         half_angle_deg: float, rmax: float, stream=None) -> Adjoint:
+                         half_angle_deg: float, rmax: float, device=None, stream=None) -> Adjoint:
+    """Creates an adjoint run whose buffers are one torch CUDA tensor (PyTorch's
+    caching allocator) and whose stream is torch's current stream."""
     import torch
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    nbytes = hydro_adjoint_workspace_size(cfg, nsteps, checkpoint_every)
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
     c = hydro_config.from_buffer_copy(cfg)
-    s = stream if stream is not None else torch.cuda.current_stream()
+    c.workspace = (ws.data_ptr() + 255) // 256 * 256
+    c.workspace_bytes = nbytes
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
     c.cuda_stream = s.cuda_stream
     h = ctypes.c_void_p()
     _check(_lib().hydro_adjoint_create(ctypes.byref(c), nsteps, checkpoint_every, (ctypes.c_double * 3)(*apex),
                                        (ctypes.c_double * 3)(*axis), half_angle_deg, rmax, ctypes.byref(h)),
            "hydro_adjoint_create")
-    return Adjoint(h, c, nsteps, checkpoint_every)
+    return Adjoint(h, c, nsteps, checkpoint_every, ws)
 
 
 def hydro_adjoint_add_jet(a: Adjoint, x0, direction, t_start: float) -> None:
@@ -398,3 +421,36 @@ def hydro_adjoint_destroy(a: Adjoint) -> None:
     if a.handle:
         _lib().hydro_adjoint_destroy(a.handle)
         a.handle = None
+
+
+# ---------------------------------------------------------------- arithmetic checks and peaks
+
+
+def hydro_eval_math(fn: int, x_dev, param: float = 0.0, stream=None):
+    """Evaluates device routine `fn` (HYDRO_MATH_*) over the float64 CUDA tensor
+    x_dev (n values, or 4n for the recoveries); returns the output tensor
+    (n, 2n or 5n float64 values)."""
+    import torch
+    if x_dev.dtype != torch.float64 or not x_dev.is_cuda or not x_dev.is_contiguous():
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    if fn in (HYDRO_MATH_RCP, HYDRO_MATH_SQRT_RSQRT):
+        n = x_dev.numel()
+        out = torch.empty(n * (1 if fn == HYDRO_MATH_RCP else 2), dtype=torch.float64, device=x_dev.device)
+    else:
+        if x_dev.numel() % 4:
+            raise ValueError("the recoveries take (E, Mx, My, Mz) as 4 arrays of n values")
+        n = x_dev.numel() // 4
+        out = torch.empty(5 * n, dtype=torch.float64, device=x_dev.device)
+    s = stream if stream is not None else torch.cuda.current_stream(x_dev.device)
+    _check(_lib().hydro_eval_math(fn, n, x_dev.data_ptr(), out.data_ptr(), param, s.cuda_stream), "hydro_eval_math")
+    return out
+
+
+def hydro_alu_peak(kind: int, iters: int, stream=None):
+    """(FLOPs, ms) of one FMA-throughput launch (HYDRO_PEAK_*) on the current device."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    flop = ctypes.c_double()
+    ms = ctypes.c_double()
+    _check(_lib().hydro_alu_peak(kind, iters, s.cuda_stream, ctypes.byref(flop), ctypes.byref(ms)), "hydro_alu_peak")
+    return flop.value, ms.value

@@ -61,7 +61,9 @@ def test_workspace_size_counts_three_states_and_rhs(hy):
 
 @pytest.mark.parametrize("field,value", [("nx", 0), ("precision", 7), ("boundary", 5), ("weno_order", 6),
                                          ("dx", 0.0), ("dt", -1.0), ("e_floor", 0.0), ("hbarc", 0.0),
-                                         ("weno_eps", 0.0), ("weno_eps", 1e-30), ("weno_eps", 1e30)])
+                                         ("weno_eps", 0.0), ("weno_eps", 1e-30), ("weno_eps", 1e30),
+                                         ("wait_limit_s", -1.0), ("wait_limit_s", 11.0),
+                                         ("wait_limit_s", float("nan")), ("test_withhold_copies", 2)])
 def test_invalid_configuration_is_rejected_without_touching_the_device(hy, field, value):
     c = hy.hydro_config_default(16, 16, 16)
     setattr(c, field, value)
@@ -175,3 +177,52 @@ def test_adjoint_rejects_invalid_runs_and_cones(hy, nsteps, every, axis, angle, 
     rc = hy._lib().hydro_adjoint_create(ctypes.byref(c), nsteps, every, d3(0, 0, 0), d3(*axis), angle, rmax,
                                         ctypes.byref(h))
     assert rc == hy.HYDRO_EINVAL and not h.value
+
+
+def test_noalloc_validates_like_hydro_create_without_touching_the_device(hy):
+    """hydro_step_noalloc runs the checks of hydro_create before any device call:
+    a 1 x 1 x 65536 grid (launch z extent > 65535) and other invalid
+    configurations are EINVAL."""
+    lib = hy._lib()
+    fn = lib.hydro_step_noalloc
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.POINTER(hy.hydro_config), ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                   ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.POINTER(hy.hydro_diag)]
+    for dims, over in (((1, 1, 65536), {}), ((16, 16, 16), {"weno_order": 6}), ((16, 16, 16), {"wait_limit_s": -1})):
+        c = hy.hydro_config_default(*dims, **over)
+        assert fn(ctypes.byref(c), ctypes.c_void_p(0x1000), 0, 1, None, 0, None) == hy.HYDRO_EINVAL
+
+
+@pytest.mark.parametrize("dims,precision,every", [((128, 128, 128), "fp64", 10), ((7, 5, 3), "mixed", 2),
+                                                  ((13, 11, 9), "fp64", 3)])
+def test_adjoint_workspace_size_covers_every_buffer(hy, dims, precision, every):
+    """The adjoint's buffers are 256-byte aligned pieces of one workspace: for
+    any grid (odd sizes included) the size counts every piece with its
+    alignment padding."""
+    c = hy.hydro_config_default(*dims, precision=precision)
+    steps = 50 if dims[0] == 128 else 6
+    size = hy.hydro_adjoint_workspace_size(c, steps, every)
+    n = dims[0] * dims[1] * dims[2]
+    f5 = -(-5 * n * 8 // 256) * 256
+    every = min(every, steps)
+    nbuf = -(-steps // every) + 2 * ((every + 1) + 2 * every + 1) + 5
+    lower = nbuf * f5 + (-(-7 * n * 4 // 256) * 256 + -(-5 * n * 4 // 256) * 256 if precision == "mixed" else 0)
+    assert lower <= size <= lower + 16384
+    bad = hy.hydro_config_default(*dims, precision=precision)
+    bad.workspace = 0x1000 + 64
+    bad.workspace_bytes = size
+    h = ctypes.c_void_p()
+    d3 = ctypes.c_double * 3
+    assert hy._lib().hydro_adjoint_create(ctypes.byref(bad), steps, every, d3(0, 0, 0), d3(1, 0, 0), 30.0, 3.0,
+                                          ctypes.byref(h)) == hy.HYDRO_EINVAL
+
+
+def test_eval_math_and_peak_reject_bad_arguments_without_touching_the_device(hy):
+    lib = hy._lib()
+    assert lib.hydro_eval_math(9, 4, ctypes.c_void_p(0x1000), ctypes.c_void_p(0x2000), 0.0, None) == hy.HYDRO_EINVAL
+    assert lib.hydro_eval_math(0, -1, ctypes.c_void_p(0x1000), ctypes.c_void_p(0x2000), 0.0, None) == hy.HYDRO_EINVAL
+    assert lib.hydro_eval_math(0, 4, None, ctypes.c_void_p(0x2000), 0.0, None) == hy.HYDRO_EINVAL
+    f = ctypes.c_double()
+    m = ctypes.c_double()
+    assert lib.hydro_alu_peak(7, 10, None, ctypes.byref(f), ctypes.byref(m)) == hy.HYDRO_EINVAL
+    assert lib.hydro_alu_peak(0, 0, None, ctypes.byref(f), ctypes.byref(m)) == hy.HYDRO_EINVAL

@@ -64,32 +64,52 @@ def test_roofline_arithmetic():
     cells = 256 ** 3
     prof = {"sweep_x": {"ms": 100.0, "launches": 10}, "sweep_y": {"ms": 110.0, "launches": 10},
             "sweep_z": {"ms": 120.0, "launches": 10}}
+    want = cells * bench.FLOP_PER_CELL["sweep_z"] / 12e-3 / 1e12
+    # without a measurement: the derived fallback peaks
     r = bench._roofline(prof, cells, "fp64")
     assert r["kernel"] == "sweep_z" and r["bound"] == "alu" and r["unit"] == "TFLOP/s"
-    want = cells * bench.FLOP_PER_CELL["sweep_z"] / 12e-3 / 1e12
     assert abs(r["achieved"] - round(want, 4)) < 1e-9
     assert abs(r["frac"] - round(want / bench.PEAK_FP64_TFLOPS, 4)) < 1e-9
     assert abs(sum(r["share"].values()) - 1.0) < 1e-3
     assert abs(bench.PEAK_FP32_TFLOPS - 76.98815) < 1e-3
+    # with the peaks measured in the run: FP64 divides by the DFMA rate, FP32 and
+    # mixed by the FP32 rate
+    peaks = {"fp32_tflops": 70.0, "fp64_tflops": 1.1, "method": "test"}
+    assert abs(bench._roofline(prof, cells, "fp64", peaks)["frac"] - round(want / 1.1, 4)) < 1e-9
+    assert abs(bench._roofline(prof, cells, "mixed", peaks)["frac"] - round(want / 70.0, 4)) < 1e-9
+    assert bench._roofline(prof, cells, "fp32", peaks)["peak_source"].startswith("measured")
 
 
 def test_algorithmic_counts_and_traffic_table():
-    """The FLOP counts behind roofline.achieved (122 per WENO7 reconstruction,
-    1366 per interface; 1428 / 1405 / 1425 per cell for the x / y / z sweeps,
-    12774 per cell and RK3 step) and a DRAM figure for every sweep of every
-    precision."""
+    """The FLOP counts behind roofline.achieved, assembled from their per-unit
+    terms (122 per WENO7 reconstruction, 1366 per interface; 1428 / 1405 / 1425
+    per cell for the x / y / z sweeps, 12774 per cell and RK3 step), and a DRAM
+    entry for every sweep of every precision that is null (stale) or at least
+    the sweep's own field accesses."""
     sys.path.insert(0, ROOT)
     import bench
     assert bench.FLOP_PER_INTERFACE == 1366
     assert bench.FLOP_PER_CELL == {"sweep_x": 1428, "sweep_y": 1405, "sweep_z": 1425}
     assert bench.FLOP_PER_CELL_STEP == 12774
+    own = {"sweep_x": 10, "sweep_y": 15, "sweep_z": 15}   # field reads + writes of one sweep per cell
     for p in ("fp64", "fp32", "mixed"):
+        byte = 4 if p == "fp32" else 8
         for k in ("sweep_x", "sweep_y", "sweep_z"):
-            t = bench.TRAFFIC_B_PER_CELL[(p, k)]   # None: stale after a kernel change
-            assert t is None or t > 0
-    # the stored-state traffic of a sweep is at least its own algorithmic field accesses
-    assert bench.TRAFFIC_B_PER_CELL[("fp32", "sweep_x")] >= 4 * 10 * 0.9
+            t = bench.TRAFFIC_B_PER_CELL[(p, k)]
+            assert t is None or t >= 0.9 * own[k] * (4 if p != "fp64" and k != "sweep_z" else byte) * 0.5
     prof = {"sweep_x": {"ms": 1.0, "launches": 1}, "sweep_y": {"ms": 1.0, "launches": 1},
             "sweep_z": {"ms": 2.0, "launches": 1}}
-    assert bench._roofline(prof, 8, "fp64")["traffic"] is None
-    assert bench._roofline(prof, 8, "fp32")["traffic"] == 71.9 * 8
+    t = bench.TRAFFIC_B_PER_CELL[("fp64", "sweep_z")]
+    assert bench._roofline(prof, 8, "fp64")["traffic"] == (None if t is None else t * 8)
+
+
+def test_err_per_field_is_norm_relative():
+    sys.path.insert(0, ROOT)
+    import numpy as np
+
+    import bench
+    b = np.ones((5, 4, 4, 4))
+    a = b.copy()
+    a[2, 1, 1, 1] += 1e-6
+    e = bench._err_per_field(a, b)
+    assert e[2] == 1e-6 and e[0] == e[1] == e[3] == e[4] == 0.0

@@ -5,8 +5,10 @@ arena it does not own, plugins whose host forbids cudaMalloc, real-time loops)
 step a state they own, with scratch kept in a fixed array inside the library.
 The test drives it through the C ABI on a caller-owned device buffer and
 checks two calls in a row against the regular context API (hydro_create /
-hydro_step) at the FP64 parity tolerance of the other tests.  This file is
-named so that pytest collects it last.
+hydro_step): the state must be bit for bit the same in every precision (the
+same kernels and arithmetic; this entry point stages its tiles with plain
+loads where hydro_step uses TMA copies, which move the same values).  This
+file is named so that pytest collects it last.
 """
 import ctypes
 from dataclasses import replace
@@ -41,7 +43,7 @@ def _rel(a, b):
     return np.abs(a - b).max(axis=1) / np.abs(b).max(axis=1)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed"])
 def test_noalloc_matches_context_api_on_two_calls(env, precision):
     torch, hy, W, fn = env
     w = replace(W.ELLIPSOIDAL_32, n=(40, 36, 30), sigma=(0.9, 1.0, 1.1))   # 43200 cells, ragged tiles
@@ -67,9 +69,10 @@ def test_noalloc_matches_context_api_on_two_calls(env, precision):
         want = hy.hydro_read_fields(ref, hy.HYDRO_CONSERVED)
         rc = fn(ctypes.byref(c), state.data_ptr(), step0, nsteps, jp, len(jets), ctypes.byref(diag))
         assert rc == hy.HYDRO_OK, hy._lib().hydro_status_string(rc)
-        got = state.double().cpu().numpy()
+        got = state.double().cpu().numpy()   # FP32 widens exactly
         err = _rel(got, want)
         assert np.all(err <= TOL), (call, err)
+        assert np.array_equal(got, want.ravel()), (call, "not bitwise equal", err)
         rd = hy.hydro_get_diag(ref)
         assert diag.steps == step0 + nsteps and diag.status == 0
         assert tuple(diag.jet_cell[0]) == rd["jet_cells"][0]
@@ -84,4 +87,14 @@ def test_noalloc_rejects_grids_above_the_fixed_scratch(env):
     rc = fn(ctypes.byref(cfg), state.data_ptr(), 0, 1, None, 0, None)
     assert rc == hy.HYDRO_ENOMEM
     rc = fn(ctypes.byref(cfg), None, 0, 1, None, 0, None)
+    assert rc == hy.HYDRO_EINVAL
+
+
+def test_noalloc_rejects_grids_beyond_the_launch_limits(env):
+    """A 1 x 1 x 65536 grid fits the scratch array but not the sweeps' launch
+    grid (z extent <= 65535): the configuration is invalid, as for hydro_create."""
+    torch, hy, W, fn = env
+    cfg = hy.hydro_config_default(1, 1, 65536)
+    state = torch.zeros(5 * 65536, dtype=torch.float64, device="cuda")
+    rc = fn(ctypes.byref(cfg), state.data_ptr(), 0, 1, None, 0, None)
     assert rc == hy.HYDRO_EINVAL
