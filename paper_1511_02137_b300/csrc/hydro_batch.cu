@@ -77,6 +77,7 @@ struct BLayout {
   size_t cells = 0;
   size_t u0 = 0, u1 = 0, u2 = 0, rhs = 0, diags = 0, events = 0, tiles[3] = {0, 0, 0}, jets = 0, maps = 0, total = 0;
   size_t tile_cap[3] = {0, 0, 0};
+  size_t s[3] = {0, 0, 0};   // mixed precision: the FP32 shadows [6][cells] of the three stage states
 };
 
 BLayout layout_for(const hydro_config& c, int32_t nev, const int32_t* dims) {
@@ -99,6 +100,10 @@ BLayout layout_for(const hydro_config& c, int32_t nev, const int32_t* dims) {
   off += align_up((size_t)kJetChunk * 3 * nev * sizeof(JetStage));
   L.maps = off;   // tensor maps [stage][axis][event]
   off += align_up((size_t)9 * nev * sizeof(SweepMaps));
+  for (int k = 0; k < 3; ++k) {
+    L.s[k] = off;
+    if (c.precision == HYDRO_MIXED) off += align_up(6 * L.cells * sizeof(float));
+  }
   L.total = off;
   return L;
 }
@@ -134,6 +139,7 @@ struct hydro_batch {
   char* at(size_t o) { return ws + o; }
   DevDiag* diags() { return reinterpret_cast<DevDiag*>(ws + lay.diags); }
   size_t store() const { return cfg.precision == HYDRO_FP32 ? 4 : 8; }
+  float* shadow(int k) { return cfg.precision == HYDRO_MIXED ? reinterpret_cast<float*>(ws + lay.s[k]) : nullptr; }
   size_t flux() const { return cfg.precision == HYDRO_FP64 ? 8 : 4; }
 };
 
@@ -151,8 +157,9 @@ hydro_status set_tiles(hydro_batch* b) {
   {
     std::vector<SweepMaps> maps((size_t)9 * b->nev);
     void* bufs[3] = {b->at(b->lay.u0), b->at(b->lay.u1), b->at(b->lay.u2)};
+    void* shadows[3] = {b->shadow(0), b->shadow(1), b->shadow(2)};
     b->tma = encode_batch_tmaps(b->cfg.precision, bufs, b->at(b->lay.rhs), b->nev, b->dims.data(), b->off.data(),
-                                b->variant, maps.data());
+                                b->variant, maps.data(), b->cfg.precision == HYDRO_MIXED ? shadows : nullptr);
     if (b->tma && cudaMemcpyAsync(b->at(b->lay.maps), maps.data(), maps.size() * sizeof(SweepMaps),
                                   cudaMemcpyHostToDevice, b->cs) != cudaSuccess)
       return HYDRO_ECUDA;
@@ -241,6 +248,13 @@ cudaError_t issue_steps(hydro_batch* b, int n) {
     for (int st = 0; st < 3 && err == cudaSuccess; ++st) {
       a.U = U[st];
       a.Uout = st == 2 ? U[0] : U[st + 1];
+      if (b->cfg.precision == HYDRO_MIXED) {
+        // stage states as FP32 increments over U0 in the accumulator (see hydro_step)
+        a.U = U[0];
+        a.Uout = st == 2 ? U[0] : nullptr;
+        a.S = b->shadow(st);
+        a.Sout = b->shadow(st == 2 ? 0 : st + 1);
+      }
       a.a = kA[st];
       a.b = kB[st];
       a.src.wdt_vol = b->cfg.dt * kStageW[st] * vol;
@@ -349,6 +363,9 @@ hydro_status hydro_batch_set_initial(hydro_batch* b, int32_t event, int32_t kind
   if (e == cudaSuccess) e = cudaMemcpyAsync(staging, host5, 5 * n * sizeof(double), cudaMemcpyHostToDevice, b->cs);
   if (e == cudaSuccess)
     e = launch_init(b->cfg.precision, kind, staging, b->at(b->lay.u0) + b->off[event] * b->store(), n, d, b->cs);
+  if (e == cudaSuccess && b->cfg.precision == HYDRO_MIXED)
+    e = launch_shadow(reinterpret_cast<const double*>(b->at(b->lay.u0)) + b->off[event],
+                      b->shadow(0) + b->off[event] / 5 * 6, n, b->cfg.e_floor, b->cs);
   int bad = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, &d->bad_input, sizeof(int), cudaMemcpyDeviceToHost, b->cs);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->cs);
@@ -397,6 +414,11 @@ hydro_status hydro_batch_autotune(hydro_batch* b, int32_t variant_out[3], double
   BatchArgs a = base_args(b);
   a.U = a.U0 = b->at(b->lay.u0);
   a.Uout = b->at(b->lay.u1);
+  if (b->cfg.precision == HYDRO_MIXED) {   // stage 1 writes the increment and the shadow of U1 only
+    a.Uout = nullptr;
+    a.S = b->shadow(0);
+    a.Sout = b->shadow(1);
+  }
   a.a = 0.0;
   a.b = 1.0;
   a.jets = jt;

@@ -83,6 +83,10 @@ struct GridArgs {
   const void* U0;   // state at the start of the step (stage combination)
   void* Uout;       // combined stage result (z sweep only)
   void* rhs;        // right-hand-side accumulator
+  const float* S;   // mixed precision: FP32 shadow of U ([6][n], mixed_shadow), or NULL.  With
+                    // it the accumulator holds delta_k = U_k - U0 between stages and the z
+                    // sweep writes U (into Uout = U0) only at the last stage (Uout != NULL)
+  float* Sout;      // mixed precision: shadow of the stage result, written by the z sweep (with S)
   DevDiag* diag;
   int nx, ny, nz;
   int periodic;
@@ -122,8 +126,10 @@ struct BatchArgs {
   int periodic;
   const void* U;    // base of the concatenated state arrays
   const void* U0;
-  void* Uout;
+  void* Uout;       // mixed precision: NULL except at the last stage (see GridArgs::S)
   void* rhs;
+  const float* S;   // mixed precision: bases of the concatenated shadows (event e's [6][n_e] block
+  float* Sout;      // starts at 6/5 of its state offset); NULL otherwise
   DevDiag* diags;   // one per event
   const JetStage* jets;   // one per event, for this stage
   double inv_dx, dt, a, b, e_floor, eps;
@@ -148,11 +154,11 @@ int batch_sweep_blocks_per_sm(int precision, int dir, int variant, bool tma);
 
 // Tensor maps of a batched ensemble, maps[(stage * 3 + axis) * nev + event], for the tile
 // shapes variant[axis]; bufs[st] are the concatenated state arrays, rhs the accumulator,
-// off[e] the element offset of event e's fields.  False when a grid misses the TMA
-// layout rules (row pitch and field offset multiples of 16 bytes); callers then launch
-// the plain-load kernels.
+// off[e] the element offset of event e's fields, shadows[st] (mixed precision) the
+// concatenated shadows.  False when a grid misses the TMA layout rules (row pitch and
+// field offset multiples of 16 bytes); callers then launch the plain-load kernels.
 bool encode_batch_tmaps(int precision, void* const bufs[3], void* rhs, int nev, const int32_t* dims,
-                        const size_t* off, const int variant[3], SweepMaps* maps);
+                        const size_t* off, const int variant[3], SweepMaps* maps, void* const shadows[3] = nullptr);
 // Zeroes the per-step maximum signal speed of n diagnostics blocks.
 cudaError_t launch_reset_vmax(DevDiag* diags, int n, cudaStream_t s);
 
@@ -179,8 +185,14 @@ cudaError_t launch_sweep(int precision, int order, int dir, const SweepArgs& a, 
 // maps unusable) when the grid does not meet the TMA layout rules (row pitch a
 // multiple of 16 bytes) or the driver entry point is missing; callers then use
 // plain loads.
+// shadows (may be NULL): for mixed precision, the FP32 shadows [6][n] of the three
+// stage states, whose staging boxes then go into the maps' `stage` entries.
 bool encode_sweep_tmaps(int precision, int order, void* const bufs[3], void* rhs, int nx, int ny, int nz,
-                        SweepMaps maps[3][3]);
+                        SweepMaps maps[3][3], void* const shadows[3] = nullptr);
+
+// Mixed precision: the FP32 shadow [6][n] of an FP64 state [5][n] (the sweeps'
+// staging input; see mixed_shadow).
+cudaError_t launch_shadow(const double* U, float* S, size_t n, double e_floor, cudaStream_t s);
 
 // Initial state: staging (5N FP64, prim or cons) -> conserved state in storage precision.
 cudaError_t launch_init(int precision, int kind, const double* staging, void* U, size_t n, DevDiag* diag,

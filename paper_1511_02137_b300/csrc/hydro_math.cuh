@@ -261,26 +261,69 @@ __device__ __forceinline__ void cons_to_prim_om(float Ef_signed, float mx, float
   vz = mz * vs;
 }
 
+// !(E >= e_floor) (e_floor > 0) on the integer pipe: non-negative doubles order
+// like their bit patterns, negative ones have negative patterns, NaN floors.
+__device__ __forceinline__ bool mixed_floored(double E, double e_floor) {
+  const long long eb = __double_as_longlong(E);
+  const bool nan = !finite_bits(E) && (eb & 0xfffffffffffffLL) != 0;
+  return eb < __double_as_longlong(e_floor) || nan;
+}
+
+// om = 1 - |M|/E of the mixed recovery: the cancelling E^2 - |M|^2 from the
+// floored FP64 energy Ee and the FP64 momentum, the rest from the FP32 roundings.
+__device__ __forceinline__ float mixed_om_of(double Ee, double Mx, double My, double Mz, float Eef, float mx,
+                                             float my, float mz) {
+  const double D = Ee * Ee - (Mx * Mx + My * My + Mz * Mz);
+  const float Mabs = sqrt_approx(mx * mx + my * my + mz * mz);
+  return d2f_rn(D) * rcp_approx(Eef * (Eef + Mabs));
+}
+
 // The mixed recovery of the sweeps, given the state in FP64 and its FP32
 // roundings (converted once, on the integer pipe, and shared with the fluxes).
 __device__ __forceinline__ void cons_to_prim_mixed_f(double E, double Mx, double My, double Mz, float Ef, float mx,
                                                      float my, float mz, double e_floor, float& e, float& vx,
                                                      float& vy, float& vz, int& hit) {
   double Ee = E;
-  // !(E >= e_floor) (e_floor > 0) on the integer pipe: non-negative doubles order
-  // like their bit patterns, negative ones have negative patterns, NaN floors
-  const long long eb = __double_as_longlong(E);
-  const bool nan = !finite_bits(E) && (eb & 0xfffffffffffffLL) != 0;
-  const bool floored = eb < __double_as_longlong(e_floor) || nan;
+  const bool floored = mixed_floored(E, e_floor);
   float Eef = Ef;
   if (floored) {
     Ee = e_floor;
     Eef = d2f_rn(e_floor);
   }
-  const double D = Ee * Ee - (Mx * Mx + My * My + Mz * Mz);
-  const float Mabs = sqrt_approx(mx * mx + my * my + mz * mz);
-  const float om = d2f_rn(D) * rcp_approx(Eef * (Eef + Mabs));
+  const float om = mixed_om_of(Ee, Mx, My, Mz, Eef, mx, my, mz);
   cons_to_prim_om(floored ? -Eef : Eef, mx, my, mz, om, e, vx, vy, vz, hit);
+}
+
+// The FP32 shadow of an FP64 mixed-precision state, six values per cell that
+// carry everything the sweeps need from it: the roundings of E, M^x, M^y, M^z
+// and R, and om = 1 - |M|/E of the recovery (E^2 - |M|^2 in FP64).  The stored
+// E satisfies !(E_s >= e_floor_f) exactly when the FP64 recovery floors E
+// (E_s is moved by at most one FP32 ulp, and only for an E within one ulp below
+// the floor), so that a sweep reading the shadow takes the FP64 floor decision.
+// From a shadow, cons_to_prim_shadow returns the same primitives, bit for bit,
+// as cons_to_prim_mixed_f from the FP64 state.
+__device__ __forceinline__ void mixed_shadow(double E, double Mx, double My, double Mz, double R, double e_floor,
+                                             float s[6]) {
+  const bool floored = mixed_floored(E, e_floor);
+  const float ef = d2f_rn(e_floor);
+  float Ef = d2f_rn(E);
+  const float mx = d2f_rn(Mx), my = d2f_rn(My), mz = d2f_rn(Mz);
+  s[5] = mixed_om_of(floored ? e_floor : E, Mx, My, Mz, floored ? ef : Ef, mx, my, mz);
+  // E < e_floor rounds to at most ef; equality is the only ambiguous case
+  if (floored && Ef >= ef)   // the next float below ef (ef > 0), or a negative one if e_floor rounds to 0
+    Ef = ef > 0.0f ? __uint_as_float(__float_as_uint(ef) - 1u) : -1.17549435e-38f;
+  s[0] = Ef;
+  s[1] = mx;
+  s[2] = my;
+  s[3] = mz;
+  s[4] = d2f_rn(R);
+}
+
+// The mixed recovery from a shadow (see mixed_shadow); ef = the FP32 rounding of e_floor.
+__device__ __forceinline__ void cons_to_prim_shadow(float Es, float mx, float my, float mz, float om, float ef,
+                                                    float& e, float& vx, float& vy, float& vz, int& hit) {
+  const bool floored = !(Es >= ef);
+  cons_to_prim_om(floored ? -ef : Es, mx, my, mz, om, e, vx, vy, vz, hit);
 }
 
 // Spectral radius of the flux Jacobian along an axis: max |lambda_pm| with

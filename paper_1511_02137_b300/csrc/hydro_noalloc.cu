@@ -34,8 +34,12 @@ constexpr size_t kNoAllocMaxCells = HYDRO_NOALLOC_MAX_CELLS;
 constexpr size_t kAlign = 256;
 constexpr size_t kStateBytesMax = ((5 * kNoAllocMaxCells * sizeof(double) + kAlign - 1) / kAlign) * kAlign;
 constexpr size_t kDiagBytes = ((sizeof(DevDiag) + kAlign - 1) / kAlign) * kAlign;
-// two stage states and the accumulator at FP64 width, then the diagnostics block
+// two stage states and the accumulator at FP64 width, then the diagnostics block;
+// mixed precision instead keeps three FP32 shadows of 6 fields and an FP32
+// accumulator (6 + 6 + 6 + 5 floats per cell), which fit in the same space
 constexpr size_t kScratchBytes = 3 * kStateBytesMax + kDiagBytes;
+constexpr size_t kShadowBytesMax = ((6 * kNoAllocMaxCells * sizeof(float) + kAlign - 1) / kAlign) * kAlign;
+static_assert(3 * kShadowBytesMax + kStateBytesMax <= 3 * kStateBytesMax, "mixed layout fits the scratch array");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -96,14 +100,23 @@ extern "C" hydro_status hydro_step_noalloc(const hydro_config* cfg, void* d_stat
   hydro_status st = scratch_address(&base);
   if (st != HYDRO_OK) return st;
   char* b = static_cast<char*>(base);
+  const bool mixed = cfg->precision == HYDRO_MIXED;
   void* U1 = b;
   void* U2 = b + align_up(5 * n * store);
   void* rhs = b + 2 * align_up(5 * n * store);
+  float* S[3] = {nullptr, nullptr, nullptr};
+  if (mixed) {   // the shadows of the stage states, then the FP32 accumulator
+    for (int k = 0; k < 3; ++k) S[k] = reinterpret_cast<float*>(b + k * align_up(6 * n * sizeof(float)));
+    rhs = b + 3 * align_up(6 * n * sizeof(float));
+  }
   DevDiag* diag = reinterpret_cast<DevDiag*>(b + 3 * kStateBytesMax);
   cudaStream_t stream = static_cast<cudaStream_t>(cfg->cuda_stream);
 
   // the diagnostics block keeps the previous call's contents: start from zero
   cudaError_t err = cudaMemsetAsync(diag, 0, sizeof(DevDiag), stream);
+  // mixed precision stages the FP32 shadow of the caller's state
+  if (err == cudaSuccess && mixed && nsteps > 0)
+    err = hydro::launch_shadow(static_cast<const double*>(d_state), S[0], n, cfg->e_floor, stream);
 
   static const double kStageC[3] = {0.0, 1.0, 0.5};
   static const double kStageW[3] = {1.0 / 6.0, 1.0 / 6.0, 4.0 / 6.0};
@@ -153,6 +166,12 @@ extern "C" hydro_status hydro_step_noalloc(const hydro_config* cfg, void* d_stat
       a.src.wdt_vol = cfg->dt * kStageW[k] * vol;
       a.U = U[k];
       a.Uout = (k == 2) ? U[0] : U[k + 1];
+      if (mixed) {   // stage states as FP32 increments over U0 in the accumulator, as hydro_step
+        a.U = U[0];
+        a.Uout = k == 2 ? U[0] : nullptr;
+        a.S = S[k];
+        a.Sout = S[k == 2 ? 0 : k + 1];
+      }
       a.a = kA[k];
       a.b = kB[k];
       a.reduce_speed = (k == 0);

@@ -40,10 +40,27 @@ namespace hydro {
 // Storage type of the state, arithmetic type of the fluxes, and the math
 // policy of the flux arithmetic.  Mixed: FP64 storage and RK3 accumulation,
 // FP64 for the cancelling part of the primitive recovery, FP32 for the rest.
+// kMixedShadow is the mixed precision of single-grid contexts: the sweeps stage
+// an FP32 shadow of each stage state (mixed_shadow: the five roundings and
+// om = 1 - |M|/E from E^2 - |M|^2 in FP64), written by the z sweep that forms
+// the state, so that no staged cell is converted or recovered in FP64 again;
+// and the stage states are kept as FP32 increments over the step state U0,
+// delta_k = U_k - U0, in the right-hand-side accumulator itself: with a + b = 1
+// the stage combination is delta_{k+1} = b delta_k + b dt (L_x + L_y + L_z + S),
+// which the x sweep starts (b delta_k + b dt L_x), the y sweep continues and
+// the z sweep finishes, forming U_{k+1} = U0 + delta_{k+1} in FP64 for the
+// shadow and, at the last stage, as the new FP64 state.  The increments carry
+// FP32 accuracy relative to their own size, as HYDRO_MIXED's FP32 stage
+// increments do; no FP64 stage state other than U0 is stored.
+constexpr int kMixedShadow = 3;
 template <int PREC> struct Types;
 template <> struct Types<HYDRO_FP64> { using Store = double; using Flux = double; using Math = MathD; };
 template <> struct Types<HYDRO_FP32> { using Store = float; using Flux = float; using Math = MathF; };
 template <> struct Types<HYDRO_MIXED> { using Store = double; using Flux = float; using Math = MathF; };
+template <> struct Types<kMixedShadow> { using Store = double; using Flux = float; using Math = MathF; };
+template <int PREC> constexpr bool kIsMixed = PREC == HYDRO_MIXED || PREC == kMixedShadow;
+// Fields of a staged cell as stored: 5, or 6 for the mixed shadow (with om).
+template <int PREC> constexpr int kStagedFields = PREC == kMixedShadow ? 6 : 5;
 
 // Tile shape per sweep axis: SEG cells along the sweep axis, LANES lines.  The
 // lines of the y and z sweeps run along x so that loads stay coalesced.
@@ -196,20 +213,26 @@ __device__ __forceinline__ void publish_block(T vmax, unsigned hits, DevDiag* d,
 // the stage state) are fetched into shared memory asynchronously at the start
 // of the tile, so that their latency hides behind phases 1 and 2.  FP64 tiles
 // are bound by the FP64 pipe and keep the direct loads (and their occupancy).
+// The mixed shadow's x sweep also fetches the accumulator (delta_k).
 template <int PREC, int DIR>
 struct Prefetch {
-  static constexpr bool on = sizeof(typename Types<PREC>::Flux) == 4 && DIR != 0;
+  static constexpr bool on = sizeof(typename Types<PREC>::Flux) == 4 && (DIR != 0 || PREC == kMixedShadow);
   static constexpr int rhs = on ? 5 : 0;                      // accumulator fields
-  static constexpr int state = on && DIR == 2 ? (PREC == HYDRO_MIXED ? 10 : 5) : 0;   // U0 (+ U)
+  // step-state operands in flux-type words per cell: U0 (FP32), U0 and U (mixed,
+  // FP64), U0 (mixed shadow, FP64)
+  static constexpr int state_words =
+      on && DIR == 2 ? (PREC == kMixedShadow ? 10 : (PREC == HYDRO_MIXED ? 20 : 5)) : 0;
 };
 
 // Single-grid WENO7 sweeps stage interior tiles with one TMA copy.  FP64 copies
 // straight into the tile's U array; FP32 tiles interleave U with F_d/2, so their
-// copy lands in a separate staging box that phase 1 reads.  Mixed tiles convert
-// every staged value and load through registers.
-template <int PREC>
+// copy lands in a separate staging box that phase 1 reads; the mixed shadow's x
+// and y sweeps copy the shadow the same way (its z tile keeps plain loads: the
+// staging box would cost it a resident block per SM).  HYDRO_MIXED tiles
+// convert every staged value and load through registers.
+template <int PREC, int DIR = 0>
 __host__ __device__ constexpr bool tma_staged() {
-  return PREC != HYDRO_MIXED;
+  return PREC == kMixedShadow ? DIR != 2 : PREC != HYDRO_MIXED;
 }
 
 // Shared memory of one tile, in units of the flux type (word offsets): U, F_d/2
@@ -227,10 +250,12 @@ struct TileLayout {
   __host__ __device__ static constexpr int up(int w) { return (w + A - 1) / A * A; }
   static constexpr int pr = up(11 * NCS + 5 * NIF);                      // [5][NC] accumulator
   static constexpr int p0 = pr + Prefetch<PREC, DIR>::rhs * NC;          // [5][NC] U0 (+ [5][NC] U), Store
-  static constexpr int delta = p0 + Prefetch<PREC, DIR>::state * NC * (int)(sizeof(Store) / sizeof(F));
+  static constexpr int delta = p0 + Prefetch<PREC, DIR>::state_words * NC;
   static constexpr int body = delta + ((sizeof(F) == 8 && ORDER == 7) ? 10 * NCS : 0);
   static constexpr int stage = up(body);
-  __host__ __device__ static constexpr int words(bool stage_box) { return (stage_box && sizeof(F) == 4) ? stage + 5 * NCS : body; }
+  __host__ __device__ static constexpr int words(bool stage_box) {
+    return (stage_box && sizeof(F) == 4) ? stage + kStagedFields<PREC> * NCS : body;
+  }
 };
 
 template <int PREC, int ORDER, int DIR, int SEG, int LANES, bool STAGE = false>
@@ -311,24 +336,28 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   Store* sP0 = reinterpret_cast<Store*>(reinterpret_cast<F*>(smem_raw) + TL::p0);   // [5][NC] U0, then (mixed) [5][NC] U
   // every tile shape updates one cell per thread (phase 3 and its operands)
   static_assert(NC == kThreads, "one updated cell per thread");
+  // the mixed shadow's z sweep needs U0 at every stage (U_{k+1} = U0 + delta_{k+1}),
+  // and its x sweep at the first stage reads no increment (delta_0 = 0)
+  constexpr bool SH = PREC == kMixedShadow;
+  const bool need_u0 = FINAL && (SH || !a.k.first);
+  const bool pf_want = !(SH && DIR == 0 && a.k.first);
   if constexpr (PF::on && TMA) {
     // one thread copies the tile's boxes of cells (the box of an edge tile reaches
     // past the grid and is filled with zeros there, which phase 3 does not read)
-    if (threadIdx.x == 0) {
-      const bool need_u0 = FINAL && !a.k.first;
+    if (threadIdx.x == 0 && pf_want) {
       const unsigned bytes = (unsigned)(5 * NC * sizeof(F) +
                                         (need_u0 ? 5 * NC * sizeof(Store) : 0) +
                                         (FINAL && PREC == HYDRO_MIXED ? 5 * NC * sizeof(Store) : 0));
       mbar_expect_tx(tb->pf, bytes);
       if (!a.withhold) {
-        const int c1 = DIR == 1 ? a0 : fixed, c2 = DIR == 1 ? fixed : a0;
-        tma_load_4d(sPr, &maps->rhs, l0, c1, c2, 0, tb->pf);
-        if (need_u0) tma_load_4d(sP0, &maps->u0, l0, c1, c2, 0, tb->pf);
-        if (FINAL && PREC == HYDRO_MIXED) tma_load_4d(sP0 + 5 * NC, &maps->ust, l0, c1, c2, 0, tb->pf);
+        const int c0 = DIR == 0 ? a0 : l0, c1 = DIR == 0 ? l0 : (DIR == 1 ? a0 : fixed),
+                  c2 = DIR == 2 ? a0 : fixed;
+        tma_load_4d(sPr, &maps->rhs, c0, c1, c2, 0, tb->pf);
+        if (need_u0) tma_load_4d(sP0, &maps->u0, c0, c1, c2, 0, tb->pf);
+        if (FINAL && PREC == HYDRO_MIXED) tma_load_4d(sP0 + 5 * NC, &maps->ust, c0, c1, c2, 0, tb->pf);
       }
     }
   } else if constexpr (PF::on) {
-    const bool need_u0 = FINAL && !a.k.first;
     const F* rhs_in = static_cast<const F*>(a.rhs);
     const Store* U0_in = static_cast<const Store*>(a.U0);
     const int c = threadIdx.x;
@@ -336,7 +365,7 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
     if (DIR == 0) { lane = c / SEG; j = c - lane * SEG; }
     else { j = c / LANES; lane = c - j * LANES; }
     const int ga = a0 + j, gl = l0 + lane;
-    if (ga < n_along && gl < n_lane) {
+    if (ga < n_along && gl < n_lane && pf_want) {
       const unsigned o = offset(ga, gl);
 #pragma unroll
       for (int q = 0; q < 5; ++q) cp_async_ca<sizeof(F)>(sPr + q * NC + c, rhs_in + q * N + o);
@@ -349,6 +378,7 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
 #pragma unroll
           for (int q = 0; q < 5; ++q) cp_async_ca<sizeof(Store)>(sP0 + (5 + q) * NC + c, U + q * N + o);
         }
+
       }
     }
     cp_async_commit();
@@ -372,14 +402,17 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   }
 
   // ---------------- phase 1: stage cells, primitives, half fluxes, rho
-  // a tile whose halo lies inside the grid needs no ghost cells: one TMA box of all 5 fields
+  // a tile whose halo lies inside the grid needs no ghost cells: one TMA box of all
+  // 5 fields (6 shadow fields for kMixedShadow)
   bool staged = false;
-  F* sStage = IL ? reinterpret_cast<F*>(smem_raw) + TL::stage : sU;   // [5][NCS] U as copied
-  if constexpr (TMA && PREC != HYDRO_MIXED) {
-    static_assert(sizeof(Store) == sizeof(F), "TMA staging copies the stored type into the flux-type tile");
+  F* sStage = IL ? reinterpret_cast<F*>(smem_raw) + TL::stage : sU;   // [5 or 6][NCS] as copied
+  constexpr int NSF = kStagedFields<PREC>;
+  if constexpr (TMA && tma_staged<PREC, DIR>()) {
+    static_assert(PREC == kMixedShadow || sizeof(Store) == sizeof(F),
+                  "TMA staging copies the stored type into the flux-type tile");
     if (a0 - G >= 0 && a0 + SEG + G <= n_along && l0 + LANES <= n_lane) {
       if (threadIdx.x == 0) {
-        mbar_expect_tx(tb->stage, (unsigned)(5 * NCS * sizeof(Store)));
+        mbar_expect_tx(tb->stage, (unsigned)(NSF * NCS * sizeof(F)));
         if (a.withhold) {
           // fault injection: the barrier is armed but no copy is issued
         } else if (DIR == 0) tma_load_4d(sStage, &maps->stage, a0 - G, l0, fixed, 0, tb->stage);
@@ -405,6 +438,22 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
     else { s = c / LANES; lane = c - s * LANES; }
     const int ga = a0 - G + s;
     const int gl = l0 + lane;
+    F e, vx, vy, vz, E, Mx, My, Mz, R;
+    F v2, rden;   // v^2 and 1/(1 - v^2/3) from the recovery (FP64, FP32)
+    int hit = 0;
+    if constexpr (PREC == kMixedShadow) {
+      // the shadow written with the state: FP32 values and om, no FP64 work here
+      float om;
+      if (staged) {
+        E = sStage[c]; Mx = sStage[NCS + c]; My = sStage[2 * NCS + c]; Mz = sStage[3 * NCS + c];
+        R = sStage[4 * NCS + c]; om = sStage[5 * NCS + c];
+      } else {
+        const float* __restrict__ S = a.S;
+        const unsigned o = offset(map_along(ga, n_along, a.periodic), gl < n_lane ? gl : n_lane - 1);
+        E = S[o]; Mx = S[N + o]; My = S[2 * N + o]; Mz = S[3 * N + o]; R = S[4 * N + o]; om = S[5 * N + o];
+      }
+      cons_to_prim_shadow(E, Mx, My, Mz, om, a.k.e_floor_f, e, vx, vy, vz, hit);
+    } else {
     Store Es, Mxs, Mys, Mzs, Rs;
     if (staged) {
       Es = (Store)sStage[c]; Mxs = (Store)sStage[NCS + c]; Mys = (Store)sStage[2 * NCS + c];
@@ -413,9 +462,6 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
       const unsigned o = offset(map_along(ga, n_along, a.periodic), gl < n_lane ? gl : n_lane - 1);
       Es = U[o]; Mxs = U[N + o]; Mys = U[2 * N + o]; Mzs = U[3 * N + o]; Rs = U[4 * N + o];
     }
-    F e, vx, vy, vz, E, Mx, My, Mz, R;
-    F v2, rden;   // v^2 and 1/(1 - v^2/3) from the recovery (FP64, FP32)
-    int hit = 0;
     if constexpr (PREC == HYDRO_MIXED) {
       // the x and y sweeps have FP64-pipe time to spare (E^2 - |M|^2 is their only
       // FP64 arithmetic) and convert in hardware; the z sweep's FP64 pipe also
@@ -430,10 +476,11 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
       cons_to_prim_rho<Math>(Es, Mxs, Mys, Mzs, kconst<F>(a.e_floor, a.k.e_floor_f), e, vx, vy, vz, v2, rden, hit);
       E = (F)Es; Mx = (F)Mxs; My = (F)Mys; Mz = (F)Mzs; R = (F)Rs;
     }
+    }
     const F p = e * F(1.0 / 3.0);
     const F vd = DIR == 0 ? vx : (DIR == 1 ? vy : vz);
     F rho;
-    if constexpr (PREC == HYDRO_MIXED) rho = spectral_radius<Math>(vd, vx * vx + vy * vy + vz * vz);
+    if constexpr (kIsMixed<PREC>) rho = spectral_radius<Math>(vd, vx * vx + vy * vy + vz * vz);
     else rho = spectral_radius_r<Math>(vd, v2, rden);
     const F Md = DIR == 0 ? Mx : (DIR == 1 ? My : Mz);
     const F Fh[5] = {F(0.5) * Md, F(0.5) * (Mx * vd + (DIR == 0 ? p : F(0))),
@@ -568,12 +615,14 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   const F inv_dx = kconst<F>(a.inv_dx, a.k.inv_dx_f);
   bool bad = false;
   if constexpr (PF::on && TMA) {
-    if (!mbar_wait_bounded(tb->pf, tb->ph_pf, a.wait_ns)) {
-      atomicCAS(&a.diag->status, 0, (int)HYDRO_ETIMEOUT);
-      if (late) *late = 1;
-      if (!a.withhold) mbar_wait_bounded(tb->pf, tb->ph_pf, a.wait_ns);   // as for the staging copy
+    if (pf_want) {
+      if (!mbar_wait_bounded(tb->pf, tb->ph_pf, a.wait_ns)) {
+        atomicCAS(&a.diag->status, 0, (int)HYDRO_ETIMEOUT);
+        if (late) *late = 1;
+        if (!a.withhold) mbar_wait_bounded(tb->pf, tb->ph_pf, a.wait_ns);   // as for the staging copy
+      }
+      tb->ph_pf ^= 1u;
     }
-    tb->ph_pf ^= 1u;
   } else if constexpr (PF::on) {
     cp_async_wait_all();   // each thread reads only its own copies
   }
@@ -589,6 +638,14 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
       F L[5];
 #pragma unroll
       for (int q = 0; q < 5; ++q) L[q] = -(sH[q * NIF + h1] - sH[q * NIF + h0]) * inv_dx;
+      if constexpr (SH) {
+        // the mixed shadow accumulates the stage increment b dt L (x: on top of b delta_k)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          L[q] *= a.k.bdt_f;
+          if (DIR == 0 && !a.k.first) L[q] = fmaf(a.k.b_f, PF::on ? sPr[q * NC + c] : rhs[q * N + o], L[q]);
+        }
+      }
       if (!FINAL) {
         if constexpr (TST && DIR == 0) {
 #pragma unroll
@@ -616,16 +673,27 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
             const int* cl = jets.cell[jn];
             if (cl[0] != gx || cl[1] != gy || cl[2] != gz) continue;
             // Eq. 3 at the temperature of this cell, deposited as in Eq. 2
-            double e, vx, vy, vz;
+            double e;
             int hit = 0;
-            cons_to_prim<MathD>((double)U[o], (double)U[N + o], (double)U[2 * N + o], (double)U[3 * N + o],
-                                 a.e_floor, e, vx, vy, vz, hit);
+            if constexpr (SH) {
+              // the stage state's recovery from its shadow (FP32 e: the source enters in FP32)
+              const float* S = a.S;
+              float ef, vxf, vyf, vzf;
+              cons_to_prim_shadow(S[o], S[N + o], S[2 * N + o], S[3 * N + o], S[5 * N + o], a.k.e_floor_f, ef,
+                                  vxf, vyf, vzf, hit);
+              e = ef;
+            } else {
+              double vx, vy, vz;
+              cons_to_prim<MathD>((double)U[o], (double)U[N + o], (double)U[2 * N + o], (double)U[3 * N + o],
+                                   a.e_floor, e, vx, vy, vz, hit);
+            }
             const double T = temperature(e, a.src.t4coef);
             const double S0 = (a.src.rad * T * T * T * jets.ell[jn] + a.src.coll * T * T) * a.src.inv_vol;
-            Lq[0] += (F)S0;
-            Lq[1] += (F)(jets.dir[jn][0] * S0);
-            Lq[2] += (F)(jets.dir[jn][1] * S0);
-            Lq[3] += (F)(jets.dir[jn][2] * S0);
+            const double Sw = SH ? a.b * a.dt * S0 : S0;   // the mixed shadow accumulates b dt S
+            Lq[0] += (F)Sw;
+            Lq[1] += (F)(jets.dir[jn][0] * Sw);
+            Lq[2] += (F)(jets.dir[jn][1] * Sw);
+            Lq[3] += (F)(jets.dir[jn][2] * Sw);
             a.diag->dep[jn] += a.src.wdt_vol * S0;
             a.diag->cell[jn][0] = gx;
             a.diag->cell[jn][1] = gy;
@@ -639,10 +707,16 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
         // FP32: the finite test runs once on the sum of the five results (NaN and
         // infinities propagate into it; a finite sum of physical values cannot overflow)
         float chk = 0.0f;
+        Store outv[5];
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
           Store out;
-          if constexpr (PREC == HYDRO_MIXED) {
+          if constexpr (SH) {
+            // Lq = delta_{k+1} (FP32); U_{k+1} = U0 + delta_{k+1} in FP64.  Before the
+            // last stage the increment goes back into the accumulator for the next x sweep.
+            out = sP0[q * NC + c] + f2d(Lq[q]);
+            if (!Uout) rhs[q * N + o] = Lq[q];
+          } else if constexpr (PREC == HYDRO_MIXED) {
             // a U0 + b (u + dt L) = u + a (U0 - u) + b dt L (a + b = 1): the FP64
             // state takes an FP32 increment, which carries the FP32 accuracy of L
             // anyway; two FP64 additions per field instead of three operations
@@ -658,9 +732,18 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
           }
           if constexpr (sizeof(Store) == 4) chk += out;
           else bad |= !finite_bits(out);
-          Uout[q * N + o] = out;
+          if (PREC != kMixedShadow || Uout) Uout[q * N + o] = out;   // (the shadow stores U only at stage 3)
+          outv[q] = out;
         }
         if constexpr (sizeof(Store) == 4) bad |= !finite_bits(chk);
+        if constexpr (PREC == kMixedShadow) {
+          // the shadow of the new state, for the sweeps that stage it next
+          float sh[6];
+          mixed_shadow(outv[0], outv[1], outv[2], outv[3], outv[4], a.e_floor, sh);
+          float* __restrict__ So = a.Sout;
+#pragma unroll
+          for (int q = 0; q < 6; ++q) So[q * N + o] = sh[q];
+        }
       }
     }
   }
@@ -699,12 +782,13 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a, cons
   sweep_block<PREC, ORDER, DIR, FINAL, TMA>(a, maps);
 }
 
-// The FP32 z sweep held to 40 registers (six blocks of 256 threads per SM); left
-// alone it takes 46 and five blocks.  The other sweeps stay at or below 40 by
-// themselves; FP64 and mixed tiles are limited by shared memory first.
-template <int ORDER, bool TMA>
-__global__ void __launch_bounds__(kThreads, 6) sweep_kernel_z32(const SweepArgs a, const __grid_constant__ SweepMaps maps) {
-  sweep_block<HYDRO_FP32, ORDER, 2, true, TMA>(a, maps);
+// The FP32 and mixed-shadow z sweeps held to 40 registers (six blocks of 256
+// threads per SM); left alone they take 46-48 and five blocks.  The other sweeps
+// stay at or below 40 by themselves; FP64 and HYDRO_MIXED tiles are limited by
+// shared memory first.
+template <int PREC, int ORDER, bool TMA>
+__global__ void __launch_bounds__(kThreads, 6) sweep_kernel_z6(const SweepArgs a, const __grid_constant__ SweepMaps maps) {
+  sweep_block<PREC, ORDER, 2, true, TMA>(a, maps);
 }
 
 // Resident blocks per SM the batched kernels' register budget is held to: six
@@ -747,7 +831,7 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<PREC>()) batch_swee
       const BatchEvent ev = b.events[td.x];
       g.U = static_cast<const Store*>(b.U) + ev.off;
       g.U0 = static_cast<const Store*>(b.U0) + ev.off;
-      g.Uout = static_cast<Store*>(b.Uout) + ev.off;
+      g.Uout = b.Uout ? static_cast<Store*>(b.Uout) + ev.off : nullptr;
       g.rhs = static_cast<F*>(b.rhs) + ev.off;
       g.diag = b.diags + td.x;
       g.nx = ev.nx;
@@ -764,6 +848,9 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<PREC>()) batch_swee
       g.count_floors = b.count_floors;
       g.wait_ns = b.wait_ns;
       g.withhold = 0;
+      const size_t soff = ev.off / 5 * 6;   // event e's shadow block: 6 fields of its cells
+      g.S = b.S ? b.S + soff : nullptr;
+      g.Sout = b.Sout ? b.Sout + soff : nullptr;
       g.src = b.src;
       g.k = b.k;
     }
@@ -791,7 +878,7 @@ __global__ void reset_vmax_kernel(DevDiag* d, int n) {
 
 template <int PREC, int ORDER, int DIR, bool TMA>
 static auto pick_sweep_kernel() {
-  if constexpr (PREC == HYDRO_FP32 && DIR == 2) return sweep_kernel_z32<ORDER, TMA>;
+  if constexpr ((PREC == HYDRO_FP32 || PREC == kMixedShadow) && DIR == 2) return sweep_kernel_z6<PREC, ORDER, TMA>;
   else return sweep_kernel<PREC, ORDER, DIR, DIR == 2, TMA>;
 }
 
@@ -799,9 +886,9 @@ template <int PREC, int ORDER, int DIR>
 static cudaError_t launch_one(const SweepArgs& a, cudaStream_t s, const SweepMaps* maps) {
   using F = typename Types<PREC>::Flux;
   constexpr int SEG = Tile<PREC, DIR>::SEG, LANES = Tile<PREC, DIR>::LANES;
-  // tensor maps serve the staging copy (FP64, FP32), and the phase-3 operands and
-  // results of FP32-flux tiles (FP32, mixed)
-  constexpr bool kStage = ORDER == 7 && tma_staged<PREC>();
+  // tensor maps serve the staging copy (FP64, FP32, the mixed shadow's x and y
+  // sweeps), and the phase-3 operands and results of FP32-flux tiles (FP32, mixed)
+  constexpr bool kStage = ORDER == 7 && tma_staged<PREC, DIR>();
   constexpr bool kMapsUsed = kStage || (ORDER == 7 && sizeof(F) == 4);
   constexpr size_t smem = sizeof(F) * (size_t)tile_smem_words<PREC, ORDER, DIR, SEG, LANES>();
   constexpr size_t smem_tma = sizeof(F) * (size_t)tile_smem_words<PREC, ORDER, DIR, SEG, LANES, kStage>();
@@ -862,7 +949,9 @@ cudaError_t launch_sweep(int precision, int order, int dir, const SweepArgs& arg
   switch (precision) {
     case HYDRO_FP64: return launch_order<HYDRO_FP64>(order, dir, a, s, tmap);
     case HYDRO_FP32: return launch_order<HYDRO_FP32>(order, dir, a, s, tmap);
-    default: return launch_order<HYDRO_MIXED>(order, dir, a, s, tmap);
+    default:
+      if (a.S) return launch_order<kMixedShadow>(order, dir, a, s, tmap);   // shadow given: stage it
+      return launch_order<HYDRO_MIXED>(order, dir, a, s, tmap);
   }
 }
 
@@ -897,14 +986,16 @@ static EncodeTiled encode_entry() {
   return reinterpret_cast<EncodeTiled>(fn);
 }
 
-// The maps of one grid for the three stages and axes, with tile shapes seg[d] x lanes[d].
+// The maps of one grid for the three stages and axes, with tile shapes seg[d] x lanes[d];
+// shadows (mixed precision, may be NULL) give the staging boxes of the FP32 shadows.
 static bool encode_grid(EncodeTiled encode, int precision, void* const bufs[3], void* rhs, int nx, int ny, int nz,
-                        const int seg[3], const int lanes[3], SweepMaps maps[3][3]) {
+                        const int seg[3], const int lanes[3], SweepMaps maps[3][3],
+                        void* const shadows[3] = nullptr) {
   const size_t es = precision == HYDRO_FP32 ? 4 : 8;   // stored type
   const size_t fs = precision == HYDRO_FP64 ? 8 : 4;   // flux type
-  // a 4-D (x, y, z, field) map of one 5-field array with elements of `size` bytes
+  // a 4-D (x, y, z, field) map of one array of box[3] fields with elements of `size` bytes
   auto enc = [&](CUtensorMap* m, void* base, size_t size, const cuuint32_t box[4]) {
-    const cuuint64_t dim[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, 5};
+    const cuuint64_t dim[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)box[3]};
     const cuuint64_t stride[3] = {(cuuint64_t)nx * size, (cuuint64_t)nx * ny * size, (cuuint64_t)nx * ny * nz * size};
     for (int k = 0; k < 3; ++k)
       if (stride[k] % 16 != 0) return false;
@@ -928,13 +1019,17 @@ static bool encode_grid(EncodeTiled encode, int precision, void* const bufs[3], 
       if (precision != HYDRO_MIXED) {   // staging box of the stage state
         box_of(d, lanes[d], seg[d] + 8, box);
         if (!enc(&maps[st][d].stage, bufs[st], es, box)) return false;
+      } else if (shadows && d != 2) {   // staging box of the stage state's FP32 shadow (6 fields)
+        box_of(d, lanes[d], seg[d] + 8, box);
+        box[3] = 6;
+        if (!enc(&maps[st][d].stage, shadows[st], 4, box)) return false;
       }
       if (precision != HYDRO_FP64) {   // phase-3 operand and result boxes
         box_of(d, lanes[d], seg[d], box);
         if (!enc(&maps[st][d].rhs, rhs, fs, box)) return false;
         if (d == 2) {
           if (!enc(&maps[st][d].u0, bufs[0], es, box)) return false;
-          if (precision == HYDRO_MIXED && !enc(&maps[st][d].ust, bufs[st], es, box)) return false;
+          if (precision == HYDRO_MIXED && !shadows && !enc(&maps[st][d].ust, bufs[st], es, box)) return false;
         }
       }
     }
@@ -942,17 +1037,17 @@ static bool encode_grid(EncodeTiled encode, int precision, void* const bufs[3], 
 }
 
 bool encode_sweep_tmaps(int precision, int order, void* const bufs[3], void* rhs, int nx, int ny, int nz,
-                        SweepMaps maps[3][3]) {
+                        SweepMaps maps[3][3], void* const shadows[3]) {
   if (order != 7) return false;
   EncodeTiled encode = encode_entry();
   if (!encode) return false;
   int seg[3], lanes[3];
   for (int d = 0; d < 3; ++d) tile_shape(precision, d, seg[d], lanes[d]);
-  return encode_grid(encode, precision, bufs, rhs, nx, ny, nz, seg, lanes, maps);
+  return encode_grid(encode, precision, bufs, rhs, nx, ny, nz, seg, lanes, maps, shadows);
 }
 
 bool encode_batch_tmaps(int precision, void* const bufs[3], void* rhs, int nev, const int32_t* dims,
-                        const size_t* off, const int variant[3], SweepMaps* maps) {
+                        const size_t* off, const int variant[3], SweepMaps* maps, void* const shadows[3]) {
   EncodeTiled encode = encode_entry();
   if (!encode) return false;
   const size_t es = precision == HYDRO_FP32 ? 4 : 8, fs = precision == HYDRO_FP64 ? 8 : 4;
@@ -965,10 +1060,14 @@ bool encode_batch_tmaps(int precision, void* const bufs[3], void* rhs, int nev, 
   }
   for (int e = 0; e < nev; ++e) {
     void* eb[3];
-    for (int k = 0; k < 3; ++k) eb[k] = static_cast<char*>(bufs[k]) + off[e] * es;
+    void* es6[3];
+    for (int k = 0; k < 3; ++k) {
+      eb[k] = static_cast<char*>(bufs[k]) + off[e] * es;
+      es6[k] = shadows ? static_cast<char*>(shadows[k]) + off[e] / 5 * 6 * sizeof(float) : nullptr;
+    }
     SweepMaps m[3][3];
     if (!encode_grid(encode, precision, eb, static_cast<char*>(rhs) + off[e] * fs, dims[3 * e], dims[3 * e + 1],
-                     dims[3 * e + 2], seg, lanes, m))
+                     dims[3 * e + 2], seg, lanes, m, shadows ? es6 : nullptr))
       return false;
     for (int st = 0; st < 3; ++st)
       for (int d = 0; d < 3; ++d) maps[(size_t)(st * 3 + d) * nev + e] = m[st][d];
@@ -982,7 +1081,7 @@ bool encode_batch_tmaps(int precision, void* const bufs[3], void* rhs, int nev, 
 template <int PREC, int DIR, int SEG, int LANES, bool TMA>
 static constexpr size_t batch_smem() {
   using F = typename Types<PREC>::Flux;
-  return sizeof(F) * (size_t)tile_smem_words<PREC, 7, DIR, SEG, LANES, TMA && tma_staged<PREC>()>();
+  return sizeof(F) * (size_t)tile_smem_words<PREC, 7, DIR, SEG, LANES, TMA && tma_staged<PREC, DIR>()>();
 }
 
 template <int PREC, int DIR, int SEG, int LANES, bool TMA>
@@ -1072,10 +1171,11 @@ cudaError_t launch_batch_sweep(int precision, int dir, int variant, const BatchA
   g.e_floor = a.e_floor;
   g.eps = a.eps;
   a.k = derive_constants(g, 7);
+  // batches of mixed precision always carry shadows (the mixed shadow kernels)
   switch (precision) {
     case HYDRO_FP64: return batch_launch_prec<HYDRO_FP64>(dir, variant, a, grid, s);
     case HYDRO_FP32: return batch_launch_prec<HYDRO_FP32>(dir, variant, a, grid, s);
-    default: return batch_launch_prec<HYDRO_MIXED>(dir, variant, a, grid, s);
+    default: return batch_launch_prec<kMixedShadow>(dir, variant, a, grid, s);
   }
 }
 
@@ -1083,7 +1183,7 @@ int batch_sweep_blocks_per_sm(int precision, int dir, int variant, bool tma) {
   switch (precision) {
     case HYDRO_FP64: return batch_occupancy_prec<HYDRO_FP64>(dir, variant, tma);
     case HYDRO_FP32: return batch_occupancy_prec<HYDRO_FP32>(dir, variant, tma);
-    default: return batch_occupancy_prec<HYDRO_MIXED>(dir, variant, tma);
+    default: return batch_occupancy_prec<kMixedShadow>(dir, variant, tma);
   }
 }
 
@@ -1146,6 +1246,15 @@ __global__ void readback_kernel(int kind, const Store* __restrict__ U, double* _
   }
 }
 
+__global__ void shadow_kernel(const double* __restrict__ U, float* __restrict__ S, size_t n, double e_floor) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    float sh[6];
+    mixed_shadow(U[i], U[n + i], U[2 * n + i], U[3 * n + i], U[4 * n + i], e_floor, sh);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) S[q * n + i] = sh[q];
+  }
+}
+
 static unsigned grid_for(size_t n) {
   size_t b = (n + 255) / 256;
   return (unsigned)(b < 148 * 32 ? (b > 0 ? b : 1) : 148 * 32);
@@ -1157,6 +1266,11 @@ cudaError_t launch_init(int precision, int kind, const double* staging, void* U,
     init_kernel<float><<<grid_for(n), 256, 0, s>>>(kind, staging, static_cast<float*>(U), n, diag);
   else
     init_kernel<double><<<grid_for(n), 256, 0, s>>>(kind, staging, static_cast<double*>(U), n, diag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shadow(const double* U, float* S, size_t n, double e_floor, cudaStream_t s) {
+  shadow_kernel<<<grid_for(n), 256, 0, s>>>(U, S, n, e_floor);
   return cudaGetLastError();
 }
 

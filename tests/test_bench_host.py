@@ -84,19 +84,19 @@ def test_algorithmic_counts_and_traffic_table():
     """The FLOP counts behind roofline.achieved, assembled from their per-unit
     terms (122 per WENO7 reconstruction, 1366 per interface; 1428 / 1405 / 1425
     per cell for the x / y / z sweeps, 12774 per cell and RK3 step), and a DRAM
-    entry for every sweep of every precision that is null (stale) or at least
-    the sweep's own field accesses."""
+    entry for every sweep of every precision: null (stale) or at least the
+    sweep's own stored-field accesses per cell (x: 5 staged fields read and 5
+    accumulator fields written; y: also 5 read; z: also the step state)."""
     sys.path.insert(0, ROOT)
     import bench
     assert bench.FLOP_PER_INTERFACE == 1366
     assert bench.FLOP_PER_CELL == {"sweep_x": 1428, "sweep_y": 1405, "sweep_z": 1425}
     assert bench.FLOP_PER_CELL_STEP == 12774
-    own = {"sweep_x": 10, "sweep_y": 15, "sweep_z": 15}   # field reads + writes of one sweep per cell
+    own = {"sweep_x": 10, "sweep_y": 15, "sweep_z": 15}   # 4-byte field accesses at least
     for p in ("fp64", "fp32", "mixed"):
-        byte = 4 if p == "fp32" else 8
         for k in ("sweep_x", "sweep_y", "sweep_z"):
             t = bench.TRAFFIC_B_PER_CELL[(p, k)]
-            assert t is None or t >= 0.9 * own[k] * (4 if p != "fp64" and k != "sweep_z" else byte) * 0.5
+            assert t is None or t >= 0.9 * own[k] * 4   # (writes still in L2 at the end escape the count)
     prof = {"sweep_x": {"ms": 1.0, "launches": 1}, "sweep_y": {"ms": 1.0, "launches": 1},
             "sweep_z": {"ms": 2.0, "launches": 1}}
     t = bench.TRAFFIC_B_PER_CELL[("fp64", "sweep_z")]
