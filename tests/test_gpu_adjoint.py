@@ -10,6 +10,7 @@ FP64 finite differences: central differences of its own FP32-flux forward at
 a relative step of 1e-6 would be dominated by FP32 rounding.
 """
 import math
+import statistics
 import time
 
 import numpy as np
@@ -147,22 +148,32 @@ def full_fd(env):
 
 
 def _timed(env, run, e, runs=3):
-    """(forward seconds, backward seconds), each the fastest of `runs` runs (wall clock
-    around the API calls; the GPU is shared)."""
-    torch = env[0]
-    fwd, bwd = [], []
+    """Times `runs` forward + backward calls with CUDA events on the library's
+    stream (torch's current stream): per call one interval around the forward
+    pass and one around the backward pass.  Returns the median forward and
+    backward times (s), the median of the per-call ratios backward / forward, and
+    (J, dJ/de, dJ/dk_rad, dJ/dk_coll) of the last call."""
+    torch, hy, A, W = env
+    fwd, bwd, ratio = [], [], []
+    out = None
     for _ in range(runs):
+        ee = e.clone().requires_grad_(True)
+        kr = torch.tensor(4.0, dtype=torch.float64, device=e.device, requires_grad=True)
+        kc = torch.tensor(2.5, dtype=torch.float64, device=e.device, requires_grad=True)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        _J(env, run, e)
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        out = _value_and_grad(env, run, e)
-        torch.cuda.synchronize()
-        t2 = time.perf_counter()
-        fwd.append(t1 - t0)
-        bwd.append((t2 - t1) - (t1 - t0))
-    return min(fwd), min(bwd), out
+        ev[0].record()
+        J = A.cone_energy(ee, kr, kc, run)
+        ev[1].record()
+        J.backward()
+        ev[2].record()
+        ev[2].synchronize()
+        f, b = ev[0].elapsed_time(ev[1]) / 1e3, ev[1].elapsed_time(ev[2]) / 1e3
+        fwd.append(f)
+        bwd.append(b)
+        ratio.append(b / f)
+        out = (J.item(), ee.grad.clone(), kr.grad.item(), kc.grad.item())
+    return statistics.median(fwd), statistics.median(bwd), statistics.median(ratio), out
 
 
 def _directional(ge, gkr, gkc, e, dirs):
@@ -173,14 +184,14 @@ def test_adjoint_full_config_128_cube_50_steps(env, full_fd):
     """The adjoint configuration: 128^3, 50 steps, checkpoint every 10, one jet
     from (-4, 0, 0) fm along +x, cone apex at the jet start; 16 seeded
     central-difference directions at relative step 1e-6 agree to 1e-4, and the
-    backward pass costs at most 4 forward passes (measured 3.3 on B300, the
-    fastest of three runs)."""
+    backward pass costs at most 4 forward passes (the median over three calls of
+    the per-call ratio, CUDA events on the library stream; measured 3.3 on B300)."""
     torch = env[0]
     e, dirs, fd, J0 = full_fd
     w, prim, run, _ = _problem(env, **FULL)
-    t_fwd, t_bwd, (J, ge, gkr, gkc) = _timed(env, run, e)
-    ratio = t_bwd / t_fwd
-    print(f"128^3 x 50 FP64: forward {t_fwd:.2f} s, backward {t_bwd:.2f} s, backward / forward = {ratio:.2f}")
+    t_fwd, t_bwd, ratio, (J, ge, gkr, gkc) = _timed(env, run, e)
+    print(f"128^3 x 50 FP64: forward {t_fwd:.2f} s, backward {t_bwd:.2f} s, backward / forward = {ratio:.2f} "
+          "(medians of three calls, CUDA events)")
     adj = _directional(ge, gkr, gkc, e, dirs)
     rel = [abs(f - a) / max(abs(f), abs(a), 1e-300) for f, a in zip(fd, adj)]
     print("128^3 FP64: J =", J, "max relative FD mismatch over 16 directions:", max(rel))
@@ -210,12 +221,11 @@ def test_mixed_adjoint_full_config_against_fp64_differences(env, full_fd):
     """Mixed precision at the adjoint configuration: the 16 directional
     derivatives of the mixed adjoint agree with the FP64 central differences
     to 1e-3 relative (FP32 flux arithmetic; measured 1.5e-4), at no more than 4
-    forward costs (measured 3.8, the fastest of three runs)."""
+    forward costs (median per-call ratio, CUDA events; measured 3.8)."""
     torch = env[0]
     e, dirs, fd, J0 = full_fd
     w, prim, run, _ = _problem(env, precision="mixed", **FULL)
-    t_fwd, t_bwd, (J, ge, gkr, gkc) = _timed(env, run, e)
-    ratio = t_bwd / t_fwd
+    t_fwd, t_bwd, ratio, (J, ge, gkr, gkc) = _timed(env, run, e)
     adj = _directional(ge, gkr, gkc, e, dirs)
     rel = [abs(f - a) / max(abs(f), abs(a), 1e-300) for f, a in zip(fd, adj)]
     print(f"128^3 x 50 mixed: forward {t_fwd:.3f} s, backward {t_bwd:.3f} s, backward / forward = "
