@@ -370,13 +370,20 @@ def _cpu_baseline(w, seconds_hint=20.0):
             "seconds": round(sec, 2)}
 
 
-def _batched(hy, steps, warmup, peaks=None):
+def _batched(hy, steps, warmup, peaks=None, events=None, edge=None):
     """The batched configuration: 64 uneven grids (edges 64-160), FP32, tiles
     picked by the autotuner, steps replayed from a CUDA graph.  Wall clock around
-    the synchronous hydro_batch_step call (host jet tables, graph launch, sync)."""
+    the synchronous hydro_batch_step call (host jet tables, graph launch, sync).
+    For profiling: `events` keeps the first events of the ensemble, `edge` replaces
+    every grid by one cube of that edge (the first event's profile)."""
     import torch
     from paper_1511_02137_b300 import workloads as W
     E = W.ENSEMBLE_64
+    if events:
+        E = W.Ensemble(name=f"{E.name} [first {events} events]", events=E.events[:events], steps=E.steps)
+    if edge:
+        E = W.Ensemble(name=f"{E.name} [{len(E.events)} x {edge}^3]",
+                       events=tuple(W.replace(w, n=(edge, edge, edge)) for w in E.events), steps=E.steps)
     cfg = hy.hydro_config_default(1, 1, 1, precision="fp32")
     b = hy.hydro_batch_create(cfg, [w.n for w in E.events])
     for e, w in enumerate(E.events):
@@ -384,6 +391,7 @@ def _batched(hy, steps, warmup, peaks=None):
         for j in w.jets:
             hy.hydro_batch_add_jet(b, e, j.x0, j.direction, j.t_start)
     choice, ms = hy.hydro_batch_autotune(b)
+    _, per_tile = hy.hydro_batch_get_tuning(b)
     hy.hydro_batch_step(b, warmup)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -399,6 +407,7 @@ def _batched(hy, steps, warmup, peaks=None):
     return {"workload": E.name, "events": len(E.events), "cells": cells, "precision": "fp32",
             "value": cells * steps / sec, "unit": UNIT, "ms_per_step": round(sec * 1e3 / steps, 3), "steps": steps,
             "tile_choice": [choice[d] for d in range(3)],
+            "launch_per_tile": [per_tile[d] for d in range(3)],
             "autotune_ms": [[round(x, 3) for x in ms[d]] for d in range(3)],
             "roofline": {"bound": "alu", "kernel": dom, "achieved": round(achieved, 4), "peak": round(peak, 3),
                          "unit": "TFLOP/s", "frac": round(achieved / peak, 4)},
@@ -603,6 +612,10 @@ def main(argv=None):
     ap.add_argument("--no-variant-error", action="store_true",
                     help="skip the 70-step FP64 reference run behind the variants' error columns")
     ap.add_argument("--variant-steps", type=int, default=200, help="timed steps of each reduced-precision variant")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="run only the batched ensemble section (for profiling its kernels)")
+    ap.add_argument("--batched-events", type=int, default=0, help="first N events of the ensemble (profiling)")
+    ap.add_argument("--batched-edge", type=int, default=0, help="every event a cube of this edge (profiling)")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="run only the adjoint section (for profiling its kernels)")
     ap.add_argument("--adjoint-grid", type=int, default=128)
@@ -615,7 +628,13 @@ def main(argv=None):
     args.precisions = [p.strip() for p in args.precisions.split(",") if p.strip()]
     args.warmup = max(args.warmup, 3)   # timing rule: at least 3 untimed warm-up steps
     rank, ws, _ = _dist()
-    if args.adjoint_only:
+    if args.batched_only:
+        from paper_1511_02137_b300 import build
+        build.build()
+        from paper_1511_02137_b300 import hydro as hy
+        out = ({"batched": _batched(hy, args.steps, args.warmup, None, args.batched_events, args.batched_edge)}
+               if rank == 0 else None)
+    elif args.adjoint_only:
         from paper_1511_02137_b300 import build
         build.build()
         from paper_1511_02137_b300 import hydro as hy

@@ -196,9 +196,10 @@ hydro_status hydro_profile_query(hydro_ctx* ctx, int32_t kind, double* total_ms,
  * ensemble form of the same step; BASELINE's batched configuration).  All
  * grids share the configuration (precision, boundary, dx, dt, t0, Eq. 3
  * constants, WENO7 only); nx/ny/nz of cfg are ignored, dims[3*e .. 3*e+2] give
- * grid e.  Each sweep of each RK3 stage is one persistent launch over the tiles
- * of all grids, and hydro_batch_step records up to 64 steps into one CUDA graph
- * that it replays.  Device work runs on a stream the batch creates; calls
+ * grid e.  Each sweep of each RK3 stage is one launch over the tiles of all
+ * grids (one block per tile, or persistent blocks walking the tile list; the
+ * autotuner picks), and hydro_batch_step records up to 64 steps into one CUDA
+ * graph that it replays.  Device work runs on a stream the batch creates; calls
  * synchronise cfg->cuda_stream first and their own stream before returning.
  * Results are identical to advancing each grid with hydro_step.
  * ------------------------------------------------------------------------- */
@@ -226,10 +227,21 @@ hydro_status hydro_batch_add_jet(hydro_batch* b, int32_t event, const double x0[
  * hydro_batch_autotune).  HYDRO_EINVAL for an unknown shape. */
 hydro_status hydro_batch_set_tiles(hydro_batch* b, const int32_t variant[3]);
 
-/* Times every compiled tile shape of each sweep axis on this ensemble (three
- * first-stage launches each, writing only scratch) and keeps the fastest.
- * variant_out (may be NULL) receives the choice per axis, ms_out (may be NULL)
- * the 9 times in ms, axis-major.  Needs every grid initialised. */
+/* Selects the launch form of each sweep axis: per_tile[d] = 1 launches one
+ * block per tile of every grid (the hardware scheduler balances the uneven
+ * grids; the default), 0 launches persistent blocks (blocks per SM x SMs) that
+ * walk the tile list.  Results are identical.  HYDRO_EINVAL for other values. */
+hydro_status hydro_batch_set_launch(hydro_batch* b, const int32_t per_tile[3]);
+
+/* The current tile shape and launch form of each axis (either may be NULL). */
+hydro_status hydro_batch_get_tuning(hydro_batch* b, int32_t variant[3], int32_t per_tile[3]);
+
+/* Times every compiled tile shape of each sweep axis on this ensemble, each in
+ * both launch forms (three first-stage launches each, writing only scratch),
+ * and keeps the fastest shape and form.  variant_out (may be NULL) receives the
+ * shape per axis, ms_out (may be NULL) the 9 times in ms, axis-major, each the
+ * faster of its two launch forms (hydro_batch_get_tuning gives the forms).
+ * Needs every grid initialised. */
 hydro_status hydro_batch_autotune(hydro_batch* b, int32_t variant_out[3], double ms_out[9]);
 
 /* Advances every grid by nsteps SSP-RK3 steps; statuses as hydro_step (the

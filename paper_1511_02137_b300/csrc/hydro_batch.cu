@@ -35,31 +35,42 @@ bool config_ok(const hydro_config* c) {
   return config_valid(c, kCheckWorkspace) && c->weno_order == 7 && c->test_withhold_copies == 0;
 }
 
+// Every grid within the single-grid index limit, and the ensemble within the
+// 32-bit cell offsets of the tile list.
 bool dims_ok(int32_t nev, const int32_t* dims) {
   if (nev < 1 || !dims) return false;
+  double total = 0.0;
   for (int e = 0; e < nev; ++e) {
     const int32_t* d = dims + 3 * e;
     if (d[0] < 1 || d[1] < 1 || d[2] < 1) return false;
     if ((double)d[0] * d[1] * d[2] > 4.0e8) return false;
+    total += (double)d[0] * d[1] * d[2];
   }
-  return true;
+  return total <= 4.0e9;
 }
 
 int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
-// Tiles of one grid for sweep axis dir with tile shape variant v: (event, a0, l0, fixed).
-void append_tiles(std::vector<int4>& t, int e, int nx, int ny, int nz, int dir, int v) {
+// Tiles of one grid for sweep axis dir with tile shape variant v, two int4 each:
+// (event, a0, l0, fixed) and the grid's (nx, ny, nz, first cell), so that a block
+// finds everything about its tile in one 32-byte read (see batch_sweep_kernel).
+void append_tiles(std::vector<int4>& t, int e, int nx, int ny, int nz, int dir, int v, size_t cell0) {
+  const int4 grid = make_int4(nx, ny, nz, (int)(unsigned)cell0);
+  auto add = [&](int a0, int l0, int f) {
+    t.push_back(make_int4(e, a0, l0, f));
+    t.push_back(grid);
+  };
   if (dir == 0) {
     const int seg = kTileSegX[v], lanes = kTileLanesX[v];
     for (int z = 0; z < nz; ++z)
       for (int ly = 0; ly < ceil_div(ny, lanes); ++ly)
-        for (int ax = 0; ax < ceil_div(nx, seg); ++ax) t.push_back(make_int4(e, ax * seg, ly * lanes, z));
+        for (int ax = 0; ax < ceil_div(nx, seg); ++ax) add(ax * seg, ly * lanes, z);
   } else {
     const int seg = kTileSegYZ[v], lanes = kTileLanesYZ[v];
     const int nalong = dir == 1 ? ny : nz, nfixed = dir == 1 ? nz : ny;
     for (int f = 0; f < nfixed; ++f)
       for (int aa = 0; aa < ceil_div(nalong, seg); ++aa)
-        for (int lx = 0; lx < ceil_div(nx, lanes); ++lx) t.push_back(make_int4(e, aa * seg, lx * lanes, f));
+        for (int lx = 0; lx < ceil_div(nx, lanes); ++lx) add(aa * seg, lx * lanes, f);
   }
 }
 
@@ -67,7 +78,7 @@ size_t max_tiles(int32_t nev, const int32_t* dims, int dir) {
   size_t best = 0;
   for (int v = 0; v < kBatchVariants; ++v) {
     std::vector<int4> t;
-    for (int e = 0; e < nev; ++e) append_tiles(t, e, dims[3 * e], dims[3 * e + 1], dims[3 * e + 2], dir, v);
+    for (int e = 0; e < nev; ++e) append_tiles(t, e, dims[3 * e], dims[3 * e + 1], dims[3 * e + 2], dir, v, 0);
     best = std::max(best, t.size());
   }
   return best;
@@ -126,6 +137,7 @@ struct hydro_batch {
   cudaStream_t cs = nullptr;   // internal stream (capturable)
   int sms = 0;
   int variant[3] = {0, 0, 0};
+  int per_tile[3] = {1, 1, 1};   // 1: one block per tile; 0: persistent (blocks per SM x SMs)
   int ntiles[3] = {0, 0, 0};
   int grid[3] = {0, 0, 0};
   bool tma = false;   // tensor maps of the current tile shapes are uploaded
@@ -172,15 +184,16 @@ hydro_status set_tiles(hydro_batch* b) {
   for (int d = 0; d < 3; ++d) {
     std::vector<int4> t;
     for (int e = 0; e < b->nev; ++e)
-      append_tiles(t, e, b->dims[3 * e], b->dims[3 * e + 1], b->dims[3 * e + 2], d, b->variant[d]);
+      append_tiles(t, e, b->dims[3 * e], b->dims[3 * e + 1], b->dims[3 * e + 2], d, b->variant[d], b->off[e] / 5);
     if (t.size() > b->lay.tile_cap[d]) return HYDRO_EINVAL;
     if (cudaMemcpyAsync(b->at(b->lay.tiles[d]), t.data(), t.size() * sizeof(int4), cudaMemcpyHostToDevice, b->cs) !=
         cudaSuccess)
       return HYDRO_ECUDA;
-    b->ntiles[d] = (int)t.size();
+    b->ntiles[d] = (int)(t.size() / 2);
     const int per_sm = batch_sweep_blocks_per_sm(b->cfg.precision, d, b->variant[d], b->tma);
     if (per_sm <= 0) return HYDRO_ECUDA;
-    b->grid[d] = std::min<long long>((long long)per_sm * b->sms, (long long)b->ntiles[d]);
+    b->grid[d] = b->per_tile[d] ? b->ntiles[d]
+                                : (int)std::min<long long>((long long)per_sm * b->sms, (long long)b->ntiles[d]);
   }
   drop_graph(b);
   return cudaStreamSynchronize(b->cs) == cudaSuccess ? HYDRO_OK : HYDRO_ECUDA;
@@ -404,6 +417,23 @@ hydro_status hydro_batch_set_tiles(hydro_batch* b, const int32_t variant[3]) {
   return set_tiles(b);
 }
 
+hydro_status hydro_batch_set_launch(hydro_batch* b, const int32_t per_tile[3]) {
+  if (!b || !per_tile) return HYDRO_EINVAL;
+  for (int d = 0; d < 3; ++d)
+    if (per_tile[d] != 0 && per_tile[d] != 1) return HYDRO_EINVAL;
+  for (int d = 0; d < 3; ++d) b->per_tile[d] = per_tile[d];
+  return set_tiles(b);
+}
+
+hydro_status hydro_batch_get_tuning(hydro_batch* b, int32_t variant[3], int32_t per_tile[3]) {
+  if (!b) return HYDRO_EINVAL;
+  for (int d = 0; d < 3; ++d) {
+    if (variant) variant[d] = b->variant[d];
+    if (per_tile) per_tile[d] = b->per_tile[d];
+  }
+  return HYDRO_OK;
+}
+
 hydro_status hydro_batch_autotune(hydro_batch* b, int32_t variant_out[3], double ms_out[9]) {
   if (!b) return HYDRO_EINVAL;
   if (!all_initialized(b)) return HYDRO_ESTATE;
@@ -425,39 +455,46 @@ hydro_status hydro_batch_autotune(hydro_batch* b, int32_t variant_out[3], double
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return HYDRO_ECUDA;
   hydro_status status = HYDRO_OK;
+  // each tile shape with both launch forms: one block per tile, and persistent blocks
   for (int d = 0; d < 3 && status == HYDRO_OK; ++d) {
     double best = 1e300;
-    int best_v = 0;
+    int best_v = 0, best_m = 1;
     for (int v = 0; v < kBatchVariants && status == HYDRO_OK; ++v) {
-      b->variant[d] = v;
-      status = set_tiles(b);
-      if (status != HYDRO_OK) break;
-      a.tiles = reinterpret_cast<const int4*>(b->at(b->lay.tiles[d]));
-      a.ntiles = b->ntiles[d];
-      // stage 1 of a step: the maps of stage 0 for this axis
-      a.maps = b->tma ? reinterpret_cast<const SweepMaps*>(b->at(b->lay.maps)) + (size_t)d * b->nev : nullptr;
-      double ms_min = 1e300;
-      for (int rep = 0; rep < 3; ++rep) {
-        cudaEventRecord(e0, b->cs);
-        if (launch_batch_sweep(b->cfg.precision, d, v, a, b->grid[d], b->cs) != cudaSuccess) {
-          status = HYDRO_ECUDA;
-          break;
+      b->last_ms[3 * d + v] = 1e300;
+      for (int m = 1; m >= 0 && status == HYDRO_OK; --m) {
+        b->variant[d] = v;
+        b->per_tile[d] = m;
+        status = set_tiles(b);
+        if (status != HYDRO_OK) break;
+        a.tiles = reinterpret_cast<const int4*>(b->at(b->lay.tiles[d]));
+        a.ntiles = b->ntiles[d];
+        // stage 1 of a step: the maps of stage 0 for this axis
+        a.maps = b->tma ? reinterpret_cast<const SweepMaps*>(b->at(b->lay.maps)) + (size_t)d * b->nev : nullptr;
+        double ms_min = 1e300;
+        for (int rep = 0; rep < 3; ++rep) {
+          cudaEventRecord(e0, b->cs);
+          if (launch_batch_sweep(b->cfg.precision, d, v, a, b->grid[d], b->cs) != cudaSuccess) {
+            status = HYDRO_ECUDA;
+            break;
+          }
+          cudaEventRecord(e1, b->cs);
+          float ms = 0.f;
+          if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            status = HYDRO_ECUDA;
+            break;
+          }
+          if (rep > 0) ms_min = std::min(ms_min, (double)ms);
         }
-        cudaEventRecord(e1, b->cs);
-        float ms = 0.f;
-        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-          status = HYDRO_ECUDA;
-          break;
+        b->last_ms[3 * d + v] = std::min(b->last_ms[3 * d + v], ms_min);
+        if (ms_min < best) {
+          best = ms_min;
+          best_v = v;
+          best_m = m;
         }
-        if (rep > 0) ms_min = std::min(ms_min, (double)ms);
-      }
-      b->last_ms[3 * d + v] = ms_min;
-      if (ms_min < best) {
-        best = ms_min;
-        best_v = v;
       }
     }
     b->variant[d] = best_v;
+    b->per_tile[d] = best_m;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

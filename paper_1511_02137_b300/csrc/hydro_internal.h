@@ -117,11 +117,12 @@ struct BatchEvent {
 
 struct SweepMaps;
 
-// Arguments of a batched (persistent) sweep launch: one launch covers every
-// tile of every grid; tiles are (event, a0, l0, fixed).
+// Arguments of a batched sweep launch: one launch covers every tile of every
+// grid; a tile is two int4, (event, a0, l0, fixed) and (nx, ny, nz, first cell of
+// the grid in the concatenated arrays).
 struct BatchArgs {
   const BatchEvent* events;
-  const int4* tiles;
+  const int4* tiles;   // 2 ntiles entries
   int ntiles;
   int periodic;
   const void* U;    // base of the concatenated state arrays

@@ -797,8 +797,12 @@ __global__ void __launch_bounds__(kThreads, 6) sweep_kernel_z6(const SweepArgs a
 template <int PREC>
 __host__ __device__ constexpr int batch_min_blocks() { return PREC == HYDRO_FP64 ? 3 : 6; }
 
-// Batched sweep: a persistent grid walks the tile list of all grids of the
-// ensemble; each tile finds its grid's size and field offset in the event table.
+// Batched sweep over the tile list of all grids of the ensemble: one block per
+// tile, or persistent blocks that walk the list (tile t, t + gridDim.x, ...).  A
+// tile is two int4 in the list, (event, a0, l0, fixed) and its grid's (nx, ny,
+// nz, first cell), read together, so that a block starts its tile after one
+// global read; persistent blocks keep the next two tiles' entries in flight
+// (cp.async) while they work.
 template <int PREC, int DIR, bool FINAL, int SEG, int LANES, bool TMA>
 __global__ void __launch_bounds__(kThreads, batch_min_blocks<PREC>()) batch_sweep_kernel(const BatchArgs b) {
   using Store = typename Types<PREC>::Store;
@@ -807,52 +811,62 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<PREC>()) batch_swee
   // the tile's grid arguments live in shared memory (one thread fills them): held in
   // registers across the tile they would cost the persistent kernel occupancy
   __shared__ GridArgs g;
-  __shared__ __align__(16) int4 tdq[2];   // this tile's descriptor and the next one's, copied ahead
+  __shared__ __align__(16) int4 tdq[3][2];   // entries of this tile and the next two
   __shared__ int4 td;
   __shared__ __align__(8) uint64_t bar, bar_pf;
   __shared__ int sLate;   // a wait of this block ran out (set once, never cleared)
   TileBars tb{&bar, &bar_pf, 0u, 0u};
-  if (threadIdx.x == 0) sLate = 0;
-  if constexpr (TMA) init_tile_bars(tb);   // (its barrier also orders sLate = 0)
-  else __syncthreads();
-  if (threadIdx.x == 0 && blockIdx.x < b.ntiles) {
-    cp_async_ca<16>(&tdq[0], &b.tiles[blockIdx.x]);
+  const int G = (int)gridDim.x;
+  auto fetch = [&](int q, int t) {
+    cp_async_ca<16>(&tdq[q][0], &b.tiles[2 * (size_t)t]);
+    cp_async_ca<16>(&tdq[q][1], &b.tiles[2 * (size_t)t + 1]);
+  };
+  if (threadIdx.x == 0) {
+    sLate = 0;
+    // the fields every tile shares
+    g.periodic = b.periodic;
+    g.inv_dx = b.inv_dx;
+    g.dt = b.dt;
+    g.a = b.a;
+    g.b = b.b;
+    g.e_floor = b.e_floor;
+    g.eps = b.eps;
+    g.reduce_speed = b.reduce_speed;
+    g.count_floors = b.count_floors;
+    g.wait_ns = b.wait_ns;
+    g.withhold = 0;
+    g.src = b.src;
+    g.k = b.k;
+    const int t0 = blockIdx.x;
+    if (t0 < b.ntiles) fetch(0, t0);
+    if (t0 + G < b.ntiles) fetch(1, t0 + G);
     cp_async_commit();
   }
-  int slot = 0;
-  for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x, slot ^= 1) {
+  if constexpr (TMA) init_tile_bars(tb);   // (its barrier also orders the writes above)
+  else __syncthreads();
+  int it = 0;
+  for (int t = blockIdx.x; t < b.ntiles; t += G, ++it) {
     if (threadIdx.x == 0) {
-      cp_async_wait_all();   // this tile's descriptor (copied during the previous tile)
-      if (t + (int)gridDim.x < b.ntiles) {
-        cp_async_ca<16>(&tdq[slot ^ 1], &b.tiles[t + gridDim.x]);
+      cp_async_wait_all();   // this tile's entries (and the next tile's)
+      const int q = it % 3;
+      if (t + 2 * G < b.ntiles) {
+        fetch((it + 2) % 3, t + 2 * G);
         cp_async_commit();
       }
-      td = tdq[slot];
-      const BatchEvent ev = b.events[td.x];
-      g.U = static_cast<const Store*>(b.U) + ev.off;
-      g.U0 = static_cast<const Store*>(b.U0) + ev.off;
-      g.Uout = b.Uout ? static_cast<Store*>(b.Uout) + ev.off : nullptr;
-      g.rhs = static_cast<F*>(b.rhs) + ev.off;
+      td = tdq[q][0];
+      const int4 gd = tdq[q][1];
+      const size_t cell0 = (unsigned)gd.w;
+      const size_t off = 5 * cell0;   // element offset of the grid's 5 fields
+      g.U = static_cast<const Store*>(b.U) + off;
+      g.U0 = static_cast<const Store*>(b.U0) + off;
+      g.Uout = b.Uout ? static_cast<Store*>(b.Uout) + off : nullptr;
+      g.rhs = static_cast<F*>(b.rhs) + off;
       g.diag = b.diags + td.x;
-      g.nx = ev.nx;
-      g.ny = ev.ny;
-      g.nz = ev.nz;
-      g.periodic = b.periodic;
-      g.inv_dx = b.inv_dx;
-      g.dt = b.dt;
-      g.a = b.a;
-      g.b = b.b;
-      g.e_floor = b.e_floor;
-      g.eps = b.eps;
-      g.reduce_speed = b.reduce_speed;
-      g.count_floors = b.count_floors;
-      g.wait_ns = b.wait_ns;
-      g.withhold = 0;
-      const size_t soff = ev.off / 5 * 6;   // event e's shadow block: 6 fields of its cells
-      g.S = b.S ? b.S + soff : nullptr;
-      g.Sout = b.Sout ? b.Sout + soff : nullptr;
-      g.src = b.src;
-      g.k = b.k;
+      g.nx = gd.x;
+      g.ny = gd.y;
+      g.nz = gd.z;
+      g.S = b.S ? b.S + 6 * cell0 : nullptr;   // the grid's shadow block: 6 fields of its cells
+      g.Sout = b.Sout ? b.Sout + 6 * cell0 : nullptr;
     }
     __syncthreads();
     const int4 tile = td;
@@ -867,7 +881,7 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<PREC>()) batch_swee
     // inside a tile, so every thread reads the same value here.
     if (sLate) break;
   }
-  // a block that stopped early may still have the next descriptor's copy in flight
+  // a block that stopped early may still have copies of the next tiles in flight
   if (threadIdx.x == 0) cp_async_wait_all();
 }
 

@@ -85,6 +85,8 @@ def _lib():
         lib.hydro_batch_add_jet.argtypes = [vp, ctypes.c_int32, dp, dp, ctypes.c_double, i32p]
         lib.hydro_batch_set_tiles.argtypes = [vp, i32p]
         lib.hydro_batch_autotune.argtypes = [vp, i32p, dp]
+        lib.hydro_batch_set_launch.argtypes = [vp, i32p]
+        lib.hydro_batch_get_tuning.argtypes = [vp, i32p, i32p]
         lib.hydro_batch_step.argtypes = [vp, ctypes.c_int32]
         lib.hydro_batch_read_fields.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, vp]
         lib.hydro_batch_get_diag.argtypes = [vp, ctypes.c_int32, P(hydro_diag)]
@@ -110,6 +112,7 @@ def _lib():
                      "hydro_read_fields", "hydro_get_diag", "hydro_profile_enable", "hydro_profile_query",
                      "hydro_batch_workspace_size", "hydro_batch_create", "hydro_batch_set_initial",
                      "hydro_batch_add_jet", "hydro_batch_set_tiles", "hydro_batch_autotune", "hydro_batch_step",
+                     "hydro_batch_set_launch", "hydro_batch_get_tuning",
                      "hydro_batch_read_fields", "hydro_batch_get_diag"):
             getattr(lib, name).restype = ctypes.c_int
         _LIB = lib
@@ -304,6 +307,19 @@ def hydro_batch_add_jet(b: Batch, event: int, x0, direction, t_start: float) -> 
 def hydro_batch_set_tiles(b: Batch, variants) -> None:
     v = (ctypes.c_int32 * 3)(*variants)
     _check(_lib().hydro_batch_set_tiles(b.handle, v), "hydro_batch_set_tiles")
+
+
+def hydro_batch_set_launch(b: Batch, per_tile) -> None:
+    v = (ctypes.c_int32 * 3)(*per_tile)
+    _check(_lib().hydro_batch_set_launch(b.handle, v), "hydro_batch_set_launch")
+
+
+def hydro_batch_get_tuning(b: Batch):
+    """(tile shape per axis, launch form per axis: 1 one block per tile, 0 persistent)."""
+    v = (ctypes.c_int32 * 3)()
+    m = (ctypes.c_int32 * 3)()
+    _check(_lib().hydro_batch_get_tuning(b.handle, v, m), "hydro_batch_get_tuning")
+    return tuple(v), tuple(m)
 
 
 def hydro_batch_autotune(b: Batch):

@@ -137,6 +137,25 @@ def test_autotune_picks_a_shape_and_leaves_the_state_alone(hy, W):
         assert np.array_equal(hy.hydro_batch_read_fields(b, e), want)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_persistent_and_per_tile_launches_are_bitwise_equal(hy, W, precision):
+    """The two launch forms of a batched sweep (one block per tile; persistent
+    blocks walking the tile list) run the same tiles with the same arithmetic:
+    the states after 3 steps are bitwise equal, and the tuning query reports the
+    form that was set."""
+    events = _small_ensemble(W)
+    res = []
+    for per_tile in ((1, 1, 1), (0, 0, 0)):
+        b = _batch(hy, W, events, precision)
+        hy.hydro_batch_set_launch(b, per_tile)
+        assert hy.hydro_batch_get_tuning(b)[1] == per_tile
+        hy.hydro_batch_step(b, 3)
+        res.append([hy.hydro_batch_read_fields(b, e) for e in range(len(events))])
+        hy.hydro_batch_destroy(b)
+    for a, c in zip(*res):
+        assert np.array_equal(a, c)
+
+
 def test_graph_replay_across_chunks_matches_one_call(hy, W):
     """70 steps run as one 64-step graph plus a 6-step graph; the same 70 steps
     in 7 calls of 10 replay one cached 10-step graph."""
