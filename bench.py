@@ -468,7 +468,7 @@ def _variant(hy, W, prec, args, ws, bus, peaks, ref_final):
     """One reduced-precision variant on the mixed-precision configuration (256^3,
     3 seeded jets): its error per field against the FP64 path after the 70
     configured steps, then the timing of a fresh run (W warm-up steps, then
-    max(K, 200) steps so that the clock sampler sees the timed region)."""
+    max(K, 300) steps so that the clock sampler sees the timed region)."""
     w = W.ELLIPSOIDAL_256_3JETS if _GRID == 256 else W.scaled(W.ELLIPSOIDAL_256_3JETS, _GRID)
     prim = W.ellipsoidal_primitives(w).ravel()
     err = None
@@ -611,7 +611,7 @@ def main(argv=None):
     ap.add_argument("--no-peaks", action="store_true", help="skip the ALU peak measurement (derived peaks instead)")
     ap.add_argument("--no-variant-error", action="store_true",
                     help="skip the 70-step FP64 reference run behind the variants' error columns")
-    ap.add_argument("--variant-steps", type=int, default=200, help="timed steps of each reduced-precision variant")
+    ap.add_argument("--variant-steps", type=int, default=300, help="timed steps of each reduced-precision variant")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched ensemble section (for profiling its kernels)")
     ap.add_argument("--batched-events", type=int, default=0, help="first N events of the ensemble (profiling)")
