@@ -301,7 +301,9 @@ __device__ __forceinline__ void cons_to_prim_mixed_f(double E, double Mx, double
 // (E_s is moved by at most one FP32 ulp, and only for an E within one ulp below
 // the floor), so that a sweep reading the shadow takes the FP64 floor decision.
 // From a shadow, cons_to_prim_shadow returns the same primitives, bit for bit,
-// as cons_to_prim_mixed_f from the FP64 state.
+// as cons_to_prim_mixed_f from the FP64 state; the sweeps use
+// cons_to_prim_shadow_rho, the same closed form with s from a reciprocal
+// square root, which also serves the spectral radius.
 __device__ __forceinline__ void mixed_shadow(double E, double Mx, double My, double Mz, double R, double e_floor,
                                              float s[6]) {
   const bool floored = mixed_floored(E, e_floor);
@@ -319,11 +321,53 @@ __device__ __forceinline__ void mixed_shadow(double E, double Mx, double My, dou
   s[4] = d2f_rn(R);
 }
 
+// cons_to_prim_om that also returns what the spectral radius needs, v^2 and
+// 1/(1 - v^2/3), from the same s: with s^2 = 4 - 3 m^2 = 1 + 3 om (2 - om) and
+// r = 1/(2 + s), v^2 = 3 r (2 - s) and 1 - v^2/3 = 2 s r (as cons_to_prim_rho);
+// one reciprocal square root gives s and 1/s.
+__device__ __forceinline__ void cons_to_prim_om_rho(float Ef_signed, float mx, float my, float mz, float om_in,
+                                                    float& e, float& vx, float& vy, float& vz, float& v2,
+                                                    float& rden, int& hit) {
+  if (Ef_signed < 0.0f) hit = 1;
+  const float Ef = fabsf(Ef_signed);
+  const float invE = rcp_approx(Ef);
+  float om = om_in;
+  const float om_min = (float)(1.0 - MathD::m_max);
+  float m_over_M = invE;   // m / |M|
+  if (!(om >= om_min)) {
+    om = om_min;
+    m_over_M = (1.0f - om) / sqrt_approx(mx * mx + my * my + mz * mz);
+    hit = 1;
+  }
+  const float s2 = 1.0f + 3.0f * om * (2.0f - om);
+  const float ys = rsqrt_approx(s2);
+  const float s = s2 * ys;
+  const float twos = 2.0f + s;
+  const float r = rcp_approx(twos);
+  const float omv = 3.0f * om * (1.0f + (2.0f - om) * rcp_approx(s + 1.0f)) * r;   // 1 - v
+  const float v = 1.0f - omv;
+  e = Ef * (omv + v * om);
+  const float vs = 3.0f * m_over_M * r;   // v / |M|
+  vx = mx * vs;
+  vy = my * vs;
+  vz = mz * vs;
+  v2 = 3.0f * r * (2.0f - s);
+  rden = 0.5f * twos * ys;
+}
+
 // The mixed recovery from a shadow (see mixed_shadow); ef = the FP32 rounding of e_floor.
 __device__ __forceinline__ void cons_to_prim_shadow(float Es, float mx, float my, float mz, float om, float ef,
                                                     float& e, float& vx, float& vy, float& vz, int& hit) {
   const bool floored = !(Es >= ef);
   cons_to_prim_om(floored ? -ef : Es, mx, my, mz, om, e, vx, vy, vz, hit);
+}
+
+// cons_to_prim_shadow with v^2 and 1/(1 - v^2/3) for the spectral radius.
+__device__ __forceinline__ void cons_to_prim_shadow_rho(float Es, float mx, float my, float mz, float om, float ef,
+                                                        float& e, float& vx, float& vy, float& vz, float& v2,
+                                                        float& rden, int& hit) {
+  const bool floored = !(Es >= ef);
+  cons_to_prim_om_rho(floored ? -ef : Es, mx, my, mz, om, e, vx, vy, vz, v2, rden, hit);
 }
 
 // Spectral radius of the flux Jacobian along an axis: max |lambda_pm| with

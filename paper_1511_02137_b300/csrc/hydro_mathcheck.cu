@@ -36,10 +36,11 @@ __global__ void eval_math_kernel(int fn, long long n, const double* __restrict__
                                 rdenf, hit);
         e = ef; vx = vxf; vy = vyf; vz = vzf;
       } else {
-        // the mixed path: FP64 state, its FP32 roundings shared with the fluxes
-        float ef, vxf, vyf, vzf;
-        cons_to_prim_mixed_f(E, Mx, My, Mz, d2f_rn(E), d2f_rn(Mx), d2f_rn(My), d2f_rn(Mz), param, ef, vxf, vyf, vzf,
-                             hit);
+        // the mixed path: the FP32 shadow of the FP64 state (E^2 - |M|^2 in FP64), then
+        // the recovery the sweeps run from it
+        float sh[6], ef, vxf, vyf, vzf, v2f, rdf;
+        mixed_shadow(E, Mx, My, Mz, 0.0, param, sh);
+        cons_to_prim_shadow_rho(sh[0], sh[1], sh[2], sh[3], sh[5], d2f_rn(param), ef, vxf, vyf, vzf, v2f, rdf, hit);
         e = ef; vx = vxf; vy = vyf; vz = vzf;
       }
       out[i] = e;

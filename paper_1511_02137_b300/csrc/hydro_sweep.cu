@@ -452,7 +452,7 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
         const unsigned o = offset(map_along(ga, n_along, a.periodic), gl < n_lane ? gl : n_lane - 1);
         E = S[o]; Mx = S[N + o]; My = S[2 * N + o]; Mz = S[3 * N + o]; R = S[4 * N + o]; om = S[5 * N + o];
       }
-      cons_to_prim_shadow(E, Mx, My, Mz, om, a.k.e_floor_f, e, vx, vy, vz, hit);
+      cons_to_prim_shadow_rho(E, Mx, My, Mz, om, a.k.e_floor_f, e, vx, vy, vz, v2, rden, hit);
     } else {
     Store Es, Mxs, Mys, Mzs, Rs;
     if (staged) {
@@ -480,7 +480,7 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
     const F p = e * F(1.0 / 3.0);
     const F vd = DIR == 0 ? vx : (DIR == 1 ? vy : vz);
     F rho;
-    if constexpr (kIsMixed<PREC>) rho = spectral_radius<Math>(vd, vx * vx + vy * vy + vz * vz);
+    if constexpr (PREC == HYDRO_MIXED) rho = spectral_radius<Math>(vd, vx * vx + vy * vy + vz * vz);
     else rho = spectral_radius_r<Math>(vd, v2, rden);
     const F Md = DIR == 0 ? Mx : (DIR == 1 ? My : Mz);
     const F Fh[5] = {F(0.5) * Md, F(0.5) * (Mx * vd + (DIR == 0 ? p : F(0))),
@@ -678,9 +678,9 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
             if constexpr (SH) {
               // the stage state's recovery from its shadow (FP32 e: the source enters in FP32)
               const float* S = a.S;
-              float ef, vxf, vyf, vzf;
-              cons_to_prim_shadow(S[o], S[N + o], S[2 * N + o], S[3 * N + o], S[5 * N + o], a.k.e_floor_f, ef,
-                                  vxf, vyf, vzf, hit);
+              float ef, vxf, vyf, vzf, v2f, rdf;
+              cons_to_prim_shadow_rho(S[o], S[N + o], S[2 * N + o], S[3 * N + o], S[5 * N + o], a.k.e_floor_f, ef,
+                                      vxf, vyf, vzf, v2f, rdf, hit);
               e = ef;
             } else {
               double vx, vy, vz;
