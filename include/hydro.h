@@ -330,9 +330,9 @@ void hydro_adjoint_destroy(hydro_adjoint* a);
  * receives the diagnostics of this call only.  cfg->workspace is ignored; all
  * work runs on cfg->cuda_stream and the call synchronises it before returning.
  *
- * The two intermediate stages, the right-hand-side accumulator and the
- * diagnostics live in one fixed device array inside the library (about
- * 7.9 MB), which every GPU that loads the library holds until the process
+ * The two intermediate stages, the right-hand-side accumulator, the cached
+ * primitives and the diagnostics live in one fixed device array inside the
+ * library (about 10.5 MB), which every GPU that loads the library holds until the process
  * exits.  The first call on a device, made with that device current, looks up
  * the array's device address (cudaGetSymbolAddress).  Every call copies its
  * diagnostics to host memory and synchronises cfg->cuda_stream, so the call

@@ -42,11 +42,12 @@ size_t store_bytes(int precision) { return precision == HYDRO_FP32 ? 4 : 8; }
 size_t flux_bytes(int precision) { return precision == HYDRO_FP64 ? 8 : 4; }
 
 struct Layout {
-  size_t u0, u1, u2, rhs, diag, s[3], total;
+  size_t u0, u1, u2, rhs, prim, diag, s[3], total;
 };
 
-// Three states and the accumulator, the diagnostics block, and for mixed
-// precision the FP32 shadows [6][n] of the three states that the sweeps stage.
+// Three states and the accumulator, in FP64 the primitives the x sweep caches for
+// the y and z sweeps, the diagnostics block, and for mixed precision the FP32
+// shadows [6][n] of the three states that the sweeps stage.
 Layout layout_for(const hydro_config& c) {
   const size_t n = (size_t)c.nx * c.ny * c.nz;
   const size_t state = align_up(5 * n * store_bytes(c.precision));
@@ -55,7 +56,10 @@ Layout layout_for(const hydro_config& c) {
   L.u1 = L.u0 + state;
   L.u2 = L.u1 + state;   // u1 .. u2 end also serves as the 5n-double host-transfer staging area
   L.rhs = L.u2 + state;
-  L.diag = L.rhs + align_up(5 * n * flux_bytes(c.precision));
+  // FP64: the primitives the x sweep caches for the y and z sweeps (in FP32 and
+  // mixed precision the sweeps recover their staged cells faster than they load them)
+  L.prim = L.rhs + align_up(5 * n * flux_bytes(c.precision));
+  L.diag = L.prim + (c.precision == HYDRO_FP64 ? align_up(5 * n * sizeof(double)) : 0);
   size_t off = L.diag + align_up(sizeof(DevDiag));
   for (int k = 0; k < 3; ++k) {
     L.s[k] = off;
@@ -284,6 +288,7 @@ hydro_status hydro_step(hydro_ctx* c, int32_t nsteps) {
   std::memset(&a, 0, sizeof(a));
   a.U0 = U[0];
   a.rhs = c->U(c->lay.rhs);
+  a.P = g.precision == HYDRO_FP64 ? c->U(c->lay.prim) : nullptr;
   a.diag = c->diag();
   a.nx = g.nx;
   a.ny = g.ny;

@@ -86,7 +86,8 @@ size_t max_tiles(int32_t nev, const int32_t* dims, int dir) {
 
 struct BLayout {
   size_t cells = 0;
-  size_t u0 = 0, u1 = 0, u2 = 0, rhs = 0, diags = 0, events = 0, tiles[3] = {0, 0, 0}, jets = 0, maps = 0, total = 0;
+  size_t u0 = 0, u1 = 0, u2 = 0, rhs = 0, prim = 0, diags = 0, events = 0, tiles[3] = {0, 0, 0}, jets = 0, maps = 0,
+         total = 0;
   size_t tile_cap[3] = {0, 0, 0};
   size_t s[3] = {0, 0, 0};   // mixed precision: the FP32 shadows [6][cells] of the three stage states
 };
@@ -99,7 +100,8 @@ BLayout layout_for(const hydro_config& c, int32_t nev, const int32_t* dims) {
   L.u1 = L.u0 + state;
   L.u2 = L.u1 + state;   // u1 .. u2 end: 5 N doubles of host-transfer staging for any one grid
   L.rhs = L.u2 + state;
-  L.diags = L.rhs + align_up(5 * L.cells * flux);
+  L.prim = L.rhs + align_up(5 * L.cells * flux);   // FP64: primitives cached by the x sweep, laid out as rhs
+  L.diags = L.prim + (c.precision == HYDRO_FP64 ? align_up(5 * L.cells * flux) : 0);
   L.events = L.diags + align_up((size_t)nev * sizeof(DevDiag));
   size_t off = L.events + align_up((size_t)nev * sizeof(BatchEvent));
   for (int d = 0; d < 3; ++d) {
@@ -206,6 +208,7 @@ BatchArgs base_args(hydro_batch* b) {
   a.events = reinterpret_cast<const BatchEvent*>(b->at(b->lay.events));
   a.periodic = g.boundary == HYDRO_PERIODIC;
   a.rhs = b->at(b->lay.rhs);
+  a.P = g.precision == HYDRO_FP64 ? b->at(b->lay.prim) : nullptr;
   a.diags = b->diags();
   a.inv_dx = 1.0 / g.dx;
   a.dt = g.dt;

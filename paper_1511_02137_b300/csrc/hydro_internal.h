@@ -87,6 +87,9 @@ struct GridArgs {
                     // it the accumulator holds delta_k = U_k - U0 between stages and the z
                     // sweep writes U (into Uout = U0) only at the last stage (Uout != NULL)
   float* Sout;      // mixed precision: shadow of the stage result, written by the z sweep (with S)
+  void* P;          // FP64: primitives the x sweep recovers, cached for the y and z sweeps of the
+                    // same stage: [5][n], v_y, rho_y, p, v_z, rho_z (NULL: every sweep recovers its
+                    // staged cells itself, as FP32 and mixed precision do)
   DevDiag* diag;
   int nx, ny, nz;
   int periodic;
@@ -131,6 +134,7 @@ struct BatchArgs {
   void* rhs;
   const float* S;   // mixed precision: bases of the concatenated shadows (event e's [6][n_e] block
   float* Sout;      // starts at 6/5 of its state offset); NULL otherwise
+  void* P;          // cached primitives, laid out like the accumulator (see GridArgs::P), or NULL
   DevDiag* diags;   // one per event
   const JetStage* jets;   // one per event, for this stage
   double inv_dx, dt, a, b, e_floor, eps;

@@ -5,12 +5,13 @@
 // a memory pool or arena it does not own, a plugin whose host forbids device
 // allocation after start-up, or a real-time loop where an allocation's
 // latency (or its failure) is not acceptable.  hydro_create needs a workspace
-// (three state copies and a right-hand-side accumulator); this entry point
-// instead keeps the two intermediate RK3 stages, the accumulator and the
-// diagnostics block in one fixed array compiled into the library.
+// (three state copies, a right-hand-side accumulator and a primitive cache);
+// this entry point instead keeps the two intermediate RK3 stages, the
+// accumulator, the cache and the diagnostics block in one fixed array compiled
+// into the library.
 //
 // Cost of that choice: every GPU that loads the library holds the array
-// (kScratchBytes, about 7.9 MB) until the process exits, the grid is limited
+// (kScratchBytes, about 10.5 MB) until the process exits, the grid is limited
 // to kNoAllocMaxCells cells, and all calls share the array, so calls whose
 // work overlaps on the GPU (different streams or threads sharing the device)
 // race on it and must be serialised by the caller.
@@ -34,12 +35,13 @@ constexpr size_t kNoAllocMaxCells = HYDRO_NOALLOC_MAX_CELLS;
 constexpr size_t kAlign = 256;
 constexpr size_t kStateBytesMax = ((5 * kNoAllocMaxCells * sizeof(double) + kAlign - 1) / kAlign) * kAlign;
 constexpr size_t kDiagBytes = ((sizeof(DevDiag) + kAlign - 1) / kAlign) * kAlign;
-// two stage states and the accumulator at FP64 width, then the diagnostics block;
-// mixed precision instead keeps three FP32 shadows of 6 fields and an FP32
-// accumulator (6 + 6 + 6 + 5 floats per cell), which fit in the same space
-constexpr size_t kScratchBytes = 3 * kStateBytesMax + kDiagBytes;
+// two stage states, the accumulator and (FP64) the x sweep's primitive cache at
+// FP64 width, then the diagnostics block; mixed precision instead keeps three
+// FP32 shadows of 6 fields and an FP32 accumulator (6 + 6 + 6 + 5 floats per
+// cell), which fit in the same space
+constexpr size_t kScratchBytes = 4 * kStateBytesMax + kDiagBytes;
 constexpr size_t kShadowBytesMax = ((6 * kNoAllocMaxCells * sizeof(float) + kAlign - 1) / kAlign) * kAlign;
-static_assert(3 * kShadowBytesMax + kStateBytesMax <= 3 * kStateBytesMax, "mixed layout fits the scratch array");
+static_assert(3 * kShadowBytesMax + kStateBytesMax <= 4 * kStateBytesMax, "mixed layout fits the scratch array");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -104,12 +106,13 @@ extern "C" hydro_status hydro_step_noalloc(const hydro_config* cfg, void* d_stat
   void* U1 = b;
   void* U2 = b + align_up(5 * n * store);
   void* rhs = b + 2 * align_up(5 * n * store);
+  void* prim = cfg->precision == HYDRO_FP64 ? b + 3 * align_up(5 * n * store) : nullptr;
   float* S[3] = {nullptr, nullptr, nullptr};
   if (mixed) {   // the shadows of the stage states, then the FP32 accumulator
     for (int k = 0; k < 3; ++k) S[k] = reinterpret_cast<float*>(b + k * align_up(6 * n * sizeof(float)));
     rhs = b + 3 * align_up(6 * n * sizeof(float));
   }
-  DevDiag* diag = reinterpret_cast<DevDiag*>(b + 3 * kStateBytesMax);
+  DevDiag* diag = reinterpret_cast<DevDiag*>(b + 4 * kStateBytesMax);
   cudaStream_t stream = static_cast<cudaStream_t>(cfg->cuda_stream);
 
   // the diagnostics block keeps the previous call's contents: start from zero
@@ -127,6 +130,7 @@ extern "C" hydro_status hydro_step_noalloc(const hydro_config* cfg, void* d_stat
   std::memset(&a, 0, sizeof(a));
   a.U0 = d_state;
   a.rhs = rhs;
+  a.P = prim;
   a.diag = diag;
   a.nx = cfg->nx;
   a.ny = cfg->ny;

@@ -432,6 +432,12 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   }
   F vmax = F(0);
   unsigned hits = 0;
+  // FP64: the y and z sweeps take v_d, p and rho_d of their staged cells from the x
+  // sweep's cache when there is one, and recover nothing (FP32 and mixed tiles
+  // recover faster than they would load, and compile without the cache)
+  constexpr bool CACHE = PREC == HYDRO_FP64;
+  F* __restrict__ Pc = CACHE ? static_cast<F*>(a.P) : nullptr;
+  const bool cached = CACHE && DIR != 0 && Pc != nullptr;
   for (int c = threadIdx.x; c < NCS; c += kThreads) {
     int lane, s;
     if (DIR == 0) { lane = c / W; s = c - lane * W; }
@@ -440,6 +446,7 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
     const int gl = l0 + lane;
     F e, vx, vy, vz, E, Mx, My, Mz, R;
     F v2, rden;   // v^2 and 1/(1 - v^2/3) from the recovery (FP64, FP32)
+    F p, vd, rho;
     int hit = 0;
     if constexpr (PREC == kMixedShadow) {
       // the shadow written with the state: FP32 values and om, no FP64 work here
@@ -453,35 +460,62 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
         E = S[o]; Mx = S[N + o]; My = S[2 * N + o]; Mz = S[3 * N + o]; R = S[4 * N + o]; om = S[5 * N + o];
       }
       cons_to_prim_shadow_rho(E, Mx, My, Mz, om, a.k.e_floor_f, e, vx, vy, vz, v2, rden, hit);
-    } else {
-    Store Es, Mxs, Mys, Mzs, Rs;
-    if (staged) {
-      Es = (Store)sStage[c]; Mxs = (Store)sStage[NCS + c]; Mys = (Store)sStage[2 * NCS + c];
-      Mzs = (Store)sStage[3 * NCS + c]; Rs = (Store)sStage[4 * NCS + c];
-    } else {
-      const unsigned o = offset(map_along(ga, n_along, a.periodic), gl < n_lane ? gl : n_lane - 1);
-      Es = U[o]; Mxs = U[N + o]; Mys = U[2 * N + o]; Mzs = U[3 * N + o]; Rs = U[4 * N + o];
-    }
-    if constexpr (PREC == HYDRO_MIXED) {
-      // the x and y sweeps have FP64-pipe time to spare (E^2 - |M|^2 is their only
-      // FP64 arithmetic) and convert in hardware; the z sweep's FP64 pipe also
-      // carries the stage combination, so it converts on the integer pipe
-      if constexpr (DIR == 2) {
-        E = d2f_rn(Es); Mx = d2f_rn(Mxs); My = d2f_rn(Mys); Mz = d2f_rn(Mzs); R = d2f_rn(Rs);
+    } else if constexpr (CACHE) {
+      const unsigned og = offset(map_along(ga, n_along, a.periodic), gl < n_lane ? gl : n_lane - 1);
+      Store Es, Mxs, Mys, Mzs, Rs;
+      if (staged) {
+        Es = (Store)sStage[c]; Mxs = (Store)sStage[NCS + c]; Mys = (Store)sStage[2 * NCS + c];
+        Mzs = (Store)sStage[3 * NCS + c]; Rs = (Store)sStage[4 * NCS + c];
       } else {
-        E = (float)Es; Mx = (float)Mxs; My = (float)Mys; Mz = (float)Mzs; R = (float)Rs;
+        Es = U[og]; Mxs = U[N + og]; Mys = U[2 * N + og]; Mzs = U[3 * N + og]; Rs = U[4 * N + og];
       }
-      cons_to_prim_mixed_f(Es, Mxs, Mys, Mzs, E, Mx, My, Mz, a.e_floor, e, vx, vy, vz, hit);
-    } else {
-      cons_to_prim_rho<Math>(Es, Mxs, Mys, Mzs, kconst<F>(a.e_floor, a.k.e_floor_f), e, vx, vy, vz, v2, rden, hit);
       E = (F)Es; Mx = (F)Mxs; My = (F)Mys; Mz = (F)Mzs; R = (F)Rs;
+      if (cached) {
+        // cache layout v_y, rho_y, p, v_z, rho_z: the y sweep reads fields 0-2, the z sweep 2-4
+        vd = Pc[(DIR == 1 ? 0 : 3) * N + og];
+        rho = Pc[(DIR == 1 ? 1 : 4) * N + og];
+        p = Pc[2 * N + og];
+      } else {
+        cons_to_prim_rho<Math>(Es, Mxs, Mys, Mzs, kconst<F>(a.e_floor, a.k.e_floor_f), e, vx, vy, vz, v2, rden, hit);
+        if (DIR == 0 && Pc != nullptr && s >= G && s < G + SEG && ga < n_along && gl < n_lane) {
+          // this tile's own cells: their primitives for the y and z sweeps of the stage
+          Pc[og] = vy;
+          Pc[N + og] = spectral_radius_r<Math>(vy, v2, rden);
+          Pc[2 * N + og] = e * F(1.0 / 3.0);
+          Pc[3 * N + og] = vz;
+          Pc[4 * N + og] = spectral_radius_r<Math>(vz, v2, rden);
+        }
+      }
+    } else {
+      Store Es, Mxs, Mys, Mzs, Rs;
+      if (staged) {
+        Es = (Store)sStage[c]; Mxs = (Store)sStage[NCS + c]; Mys = (Store)sStage[2 * NCS + c];
+        Mzs = (Store)sStage[3 * NCS + c]; Rs = (Store)sStage[4 * NCS + c];
+      } else {
+        const unsigned o = offset(map_along(ga, n_along, a.periodic), gl < n_lane ? gl : n_lane - 1);
+        Es = U[o]; Mxs = U[N + o]; Mys = U[2 * N + o]; Mzs = U[3 * N + o]; Rs = U[4 * N + o];
+      }
+      if constexpr (PREC == HYDRO_MIXED) {
+        // the x and y sweeps have FP64-pipe time to spare (E^2 - |M|^2 is their only
+        // FP64 arithmetic) and convert in hardware; the z sweep's FP64 pipe also
+        // carries the stage combination, so it converts on the integer pipe
+        if constexpr (DIR == 2) {
+          E = d2f_rn(Es); Mx = d2f_rn(Mxs); My = d2f_rn(Mys); Mz = d2f_rn(Mzs); R = d2f_rn(Rs);
+        } else {
+          E = (float)Es; Mx = (float)Mxs; My = (float)Mys; Mz = (float)Mzs; R = (float)Rs;
+        }
+        cons_to_prim_mixed_f(Es, Mxs, Mys, Mzs, E, Mx, My, Mz, a.e_floor, e, vx, vy, vz, hit);
+      } else {
+        cons_to_prim_rho<Math>(Es, Mxs, Mys, Mzs, kconst<F>(a.e_floor, a.k.e_floor_f), e, vx, vy, vz, v2, rden, hit);
+        E = (F)Es; Mx = (F)Mxs; My = (F)Mys; Mz = (F)Mzs; R = (F)Rs;
+      }
     }
+    if (!cached) {
+      p = e * F(1.0 / 3.0);
+      vd = DIR == 0 ? vx : (DIR == 1 ? vy : vz);
+      if constexpr (PREC == HYDRO_MIXED) rho = spectral_radius<Math>(vd, vx * vx + vy * vy + vz * vz);
+      else rho = spectral_radius_r<Math>(vd, v2, rden);
     }
-    const F p = e * F(1.0 / 3.0);
-    const F vd = DIR == 0 ? vx : (DIR == 1 ? vy : vz);
-    F rho;
-    if constexpr (PREC == HYDRO_MIXED) rho = spectral_radius<Math>(vd, vx * vx + vy * vy + vz * vz);
-    else rho = spectral_radius_r<Math>(vd, v2, rden);
     const F Md = DIR == 0 ? Mx : (DIR == 1 ? My : Mz);
     const F Fh[5] = {F(0.5) * Md, F(0.5) * (Mx * vd + (DIR == 0 ? p : F(0))),
                      F(0.5) * (My * vd + (DIR == 1 ? p : F(0))), F(0.5) * (Mz * vd + (DIR == 2 ? p : F(0))),
@@ -861,6 +895,7 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<PREC>()) batch_swee
       g.U0 = static_cast<const Store*>(b.U0) + off;
       g.Uout = b.Uout ? static_cast<Store*>(b.Uout) + off : nullptr;
       g.rhs = static_cast<F*>(b.rhs) + off;
+      g.P = b.P ? static_cast<F*>(b.P) + off : nullptr;
       g.diag = b.diags + td.x;
       g.nx = gd.x;
       g.ny = gd.y;
