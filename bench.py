@@ -63,7 +63,7 @@ FIELD_ACCESSES_PER_CELL_STEP = 40
 # taken with the kernels as built; a kernel change makes them stale, and a stale entry
 # is None (reported as null).
 TRAFFIC_B_PER_CELL = {
-    ("fp64", "sweep_x"): None, ("fp64", "sweep_y"): None, ("fp64", "sweep_z"): None,
+    ("fp64", "sweep_x"): 116.9, ("fp64", "sweep_y"): 142.2, ("fp64", "sweep_z"): 169.6,
     ("fp32", "sweep_x"): 37.5, ("fp32", "sweep_y"): 57.7, ("fp32", "sweep_z"): 71.9,
     ("mixed", "sweep_x"): 55.2, ("mixed", "sweep_y"): 61.9, ("mixed", "sweep_z"): 132.4,
 }
