@@ -464,11 +464,13 @@ def _adjoint(hy, grid=128, steps=50):
     return out
 
 
-def _variant(hy, W, prec, args, ws, bus, peaks, ref_final):
+def _variant(hy, W, prec, args, ws, bus, peaks, ref_final, pinned=None):
     """One reduced-precision variant on the mixed-precision configuration (256^3,
     3 seeded jets): its error per field against the FP64 path after the 70
     configured steps, then the timing of a fresh run (W warm-up steps, then
-    max(K, 300) steps so that the clock sampler sees the timed region)."""
+    max(K, 300) steps so that the clock sampler sees the timed region), and the
+    same metric end to end through the C ABI with host buffers (K steps; pinned =
+    the pinned host buffers of the initial state and the read-back)."""
     w = W.ELLIPSOIDAL_256_3JETS if _GRID == 256 else W.scaled(W.ELLIPSOIDAL_256_3JETS, _GRID)
     prim = W.ellipsoidal_primitives(w).ravel()
     err = None
@@ -483,11 +485,17 @@ def _variant(hy, W, prec, args, ws, bus, peaks, ref_final):
     sec = _max_over_ranks(sec, ws)
     hy.hydro_destroy(ctx)
     roof = _roofline(prof, w.cells, prec, peaks)
+    e2e = None
+    if pinned is not None and not args.no_e2e:
+        esec, sb, db = _e2e(hy, w, pinned[0], pinned[1], args.steps, prec)
+        esec = _max_over_ranks(esec, ws)
+        e2e = {"value": w.cells * args.steps * ws / esec, "h2d_bytes_per_step": sb / args.steps,
+               "d2h_bytes_per_step": sb / args.steps + db}
     return sec, steps, {
         "value": w.cells * steps * ws / sec, "ms_per_step": round(sec * 1e3 / steps, 4), "steps": steps,
         "err_vs_fp64_per_field_E_Mx_My_Mz_R": err,
         "roofline": {k: roof[k] for k in ("kernel", "achieved", "peak", "frac", "traffic", "avg_launch_ms", "share")},
-        "hbm": _hbm(sec, steps, w.cells, prec)["frac_of_measured_hbm"], "clocks": clk}
+        "hbm": _hbm(sec, steps, w.cells, prec)["frac_of_measured_hbm"], "e2e": e2e, "clocks": clk}
 
 
 def run_cuda(args, rank, ws):
@@ -556,7 +564,8 @@ def run_cuda(args, rank, ws):
             ref = hy.hydro_read_fields(ctx, hy.HYDRO_CONSERVED)
             hy.hydro_destroy(ctx)
         for prec in args.precisions[1:]:
-            vsec, vsteps, v = _variant(hy, W, prec, args, ws, bus, peaks, ref)
+            vsec, vsteps, v = _variant(hy, W, prec, args, ws, bus, peaks, ref,
+                                       (prim_pinned, out_pinned) if _GRID == 256 else None)
             v["speedup_vs_fp64"] = round((sec / args.steps) / (vsec / vsteps), 2) if head == "fp64" else None
             variants[prec] = v
         variants["config"] = ("error: 256^3, 3 seeded jets, 70 steps vs the FP64 path (per field, norm-relative); "
