@@ -56,7 +56,9 @@ template <int PREC> __host__ __device__ constexpr int adj_threads() { return Adj
 template <int PREC, class P>
 constexpr size_t adj_smem() {
   using T = AdjTile<PREC>;
-  return sizeof(P) * (size_t)(16 * T::NCS + 16 * T::NIF + 2 * T::NIF + 10 * T::NC) + sizeof(unsigned) * T::NIF;
+  constexpr size_t shadow_words = PREC == HYDRO_MIXED ? 2 * T::NCS : 0;
+  return sizeof(P) * (size_t)(16 * T::NCS + 16 * T::NIF + 2 * T::NIF + 15 * T::NC + shadow_words) +
+         sizeof(unsigned) * T::NIF;
 }
 
 // Flux arithmetic of the adjoint sweeps: the forward's (FP64, or FP32 for mixed).
@@ -85,6 +87,40 @@ __device__ __forceinline__ int bits_of(float x) { return __float_as_int(x); }
 template <class P> __device__ __forceinline__ P from_bits(long long b) { return __longlong_as_double(b); }
 template <> __device__ __forceinline__ float from_bits<float>(long long b) { return __int_as_float((int)b); }
 
+// Moves the adjoints of the ghost slots of one interface to its edge-cell slots:
+// slots t < t0 (left of position 0) join slot t0, slots t > t1 (right of position
+// n - 1) join slot t1.  Compile-time slot indices, so the arrays stay in registers.
+template <class P>
+__device__ __forceinline__ void fold_ghost_slots(P (&vf)[8], P (&vu)[8], int t0, int t1) {
+  P lf = P(0), lu = P(0), rf = P(0), ru = P(0);
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    if (t < t0) {
+      lf += vf[t];
+      lu += vu[t];
+      vf[t] = P(0);
+      vu[t] = P(0);
+    }
+    if (t > t1) {
+      rf += vf[t];
+      ru += vu[t];
+      vf[t] = P(0);
+      vu[t] = P(0);
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    if (t == t0) {
+      vf[t] += lf;
+      vu[t] += lu;
+    }
+    if (t == t1) {
+      vf[t] += rf;
+      vu[t] += ru;
+    }
+  }
+}
+
 template <int PREC, int DIR>
 __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs p) {
   constexpr int kAdjThreads = adj_threads<PREC>();
@@ -107,7 +143,10 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
   P* sAhb = sAl + NIF;                      // [NIF] adjoint of alpha/2
   P* sFb = sAhb + NIF;                      // [5][NC] gathered adjoint of F_d/2
   P* sUb = sFb + 5 * NC;                    // [5][NC] gathered direct adjoint of U
-  unsigned* sTie = reinterpret_cast<unsigned*>(sUb + 5 * NC);   // [NIF] slots attaining max rho
+  P* sRp = sUb + 5 * NC;                    // [5][NC] y, z: r of the cells before this sweep adds to it
+  P* sEf = sRp + 5 * NC;                    // mixed: [NCS] signed floored E of the recovery
+  P* sOm = sEf + (MIXED ? NCS : 0);         // mixed: [NCS] om = 1 - |M|/E
+  unsigned* sTie = reinterpret_cast<unsigned*>(sOm + (MIXED ? NCS : 0));   // [NIF] slots attaining max rho
   P* r_out = static_cast<P*>(p.r);
 
   const int nx = p.nx, ny = p.ny, nz = p.nz;
@@ -133,21 +172,53 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
   // J_L^T a carries a factor of a): it writes its zeros (x sweep) and stops.  The
   // adjoint of a localised observable starts on a small support that each stage
   // widens by the stencil reach.
-  bool live = false;
-  for (int c = threadIdx.x; c < NCS; c += kAdjThreads) {
-    int lane, s;
-    if (DIR == 0) { lane = c / W; s = c - lane * W; }
-    else { s = c / LANES; lane = c - s * LANES; }
-    const int ga = a0 - 8 + s;
-    const int gl = l0 + lane;
-    const bool inside = ga >= 0 && ga < n_along && gl < n_lane;
-    const unsigned oa = offset(inside ? ga : 0, gl < n_lane ? gl : 0);
-    for (int q = 0; q < 5; ++q) {
-      P aq;
-      if constexpr (MIXED) aq = inside ? p.lamf[q * N + oa] : P(0);
-      else aq = inside ? p.ascale * p.lam[q * N + oa] : P(0);
-      sA[q * NCS + c] = aq;
-      live |= aq != P(0);
+  // The charge density R feeds no other field, so its adjoint is zero for an
+  // observable of E and M: a block whose R window is exactly zero skips the R
+  // pass, which would only add zeros (s_liveR is cleared before the first barrier
+  // and set after it).
+  __shared__ int s_liveR;
+  if (threadIdx.x == 0) s_liveR = 0;
+  // Every load of the window (the adjoint, the state and, for y and z, the r values
+  // this sweep adds to) is issued before any of them is used, so that the block
+  // waits for one round of memory latency.
+  constexpr int RND = (NCS + kAdjThreads - 1) / kAdjThreads;   // positions per thread
+  constexpr int NSH = MIXED ? 7 : 5;                            // state words per position
+  constexpr bool RPRE = DIR != 0;
+  P av[RND][5], uv[RND][NSH], rv[RND][5];
+  bool live = false, liveR = false;
+#pragma unroll
+  for (int rd = 0; rd < RND; ++rd) {
+    const int c = threadIdx.x + rd * kAdjThreads;
+    if (c < NCS) {
+      int lane, s;
+      if (DIR == 0) { lane = c / W; s = c - lane * W; }
+      else { s = c / LANES; lane = c - s * LANES; }
+      const int ga = a0 - 8 + s;
+      const int gl = l0 + lane;
+      const bool inside = ga >= 0 && ga < n_along && gl < n_lane;
+      const unsigned oa = offset(inside ? ga : 0, gl < n_lane ? gl : 0);
+      const unsigned o = offset(clampi(ga, n_along), gl < n_lane ? gl : n_lane - 1);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        if constexpr (MIXED) av[rd][q] = inside ? p.lamf[q * N + oa] : P(0);
+        else av[rd][q] = inside ? p.ascale * p.lam[q * N + oa] : P(0);
+      }
+#pragma unroll
+      for (int f = 0; f < NSH; ++f) {
+        if constexpr (MIXED) uv[rd][f] = p.sh[f * N + o];
+        else uv[rd][f] = p.U[f * N + o];
+      }
+      if constexpr (RPRE) {
+        const bool cell = inside && s >= 8 && s < 8 + SEG;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) rv[rd][k] = cell ? r_out[k * N + oa] : P(0);
+      }
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        sA[q * NCS + c] = av[rd][q];
+        live |= av[rd][q] != P(0);
+        if (q == 4) liveR |= av[rd][q] != P(0);
+      }
     }
   }
   if (!__syncthreads_or(live)) {
@@ -163,33 +234,42 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
     }
     return;
   }
+  if (liveR) s_liveR = 1;
 
-  // ---- stage: U, F_d/2, rho_d at positions a0-8 .. a0+SEG+7 (clamped)
-  for (int c = threadIdx.x; c < NCS; c += kAdjThreads) {
-    int lane, s;
-    if (DIR == 0) { lane = c / W; s = c - lane * W; }
-    else { s = c / LANES; lane = c - s * LANES; }
-    const int ga = a0 - 8 + s;
-    const int gl = l0 + lane;
-    const unsigned o = offset(clampi(ga, n_along), gl < n_lane ? gl : n_lane - 1);
-    P e, vx, vy, vz, E, Mx, My, Mz, R;
-    int hit = 0;
-    if constexpr (MIXED) {
-      E = p.sh[o]; Mx = p.sh[N + o]; My = p.sh[2 * N + o]; Mz = p.sh[3 * N + o]; R = p.sh[4 * N + o];
-      cons_to_prim_om(p.sh[5 * N + o], Mx, My, Mz, p.sh[6 * N + o], e, vx, vy, vz, hit);
-    } else {
-      E = p.U[o]; Mx = p.U[N + o]; My = p.U[2 * N + o]; Mz = p.U[3 * N + o]; R = p.U[4 * N + o];
-      cons_to_prim<MathD>(E, Mx, My, Mz, p.e_floor, e, vx, vy, vz, hit);
+  // ---- U, F_d/2, rho_d at positions a0-8 .. a0+SEG+7 (clamped), from the loaded window
+#pragma unroll
+  for (int rd = 0; rd < RND; ++rd) {
+    const int c = threadIdx.x + rd * kAdjThreads;
+    if (c < NCS) {
+      int lane, s;
+      if (DIR == 0) { lane = c / W; s = c - lane * W; }
+      else { s = c / LANES; lane = c - s * LANES; }
+      P e, vx, vy, vz;
+      const P E = uv[rd][0], Mx = uv[rd][1], My = uv[rd][2], Mz = uv[rd][3], R = uv[rd][4];
+      int hit = 0;
+      if constexpr (MIXED) {
+        cons_to_prim_om(uv[rd][5], Mx, My, Mz, uv[rd][6], e, vx, vy, vz, hit);
+        sEf[c] = uv[rd][5];
+        sOm[c] = uv[rd][6];
+      } else {
+        cons_to_prim<MathD>(E, Mx, My, Mz, p.e_floor, e, vx, vy, vz, hit);
+      }
+      const P pr = e * P(1.0 / 3.0);
+      const P vd = DIR == 0 ? vx : (DIR == 1 ? vy : vz);
+      sU[c] = E; sU[NCS + c] = Mx; sU[2 * NCS + c] = My; sU[3 * NCS + c] = Mz; sU[4 * NCS + c] = R;
+      sF[c] = P(0.5) * (DIR == 0 ? Mx : (DIR == 1 ? My : Mz));
+      sF[NCS + c] = P(0.5) * (Mx * vd + (DIR == 0 ? pr : P(0)));
+      sF[2 * NCS + c] = P(0.5) * (My * vd + (DIR == 1 ? pr : P(0)));
+      sF[3 * NCS + c] = P(0.5) * (Mz * vd + (DIR == 2 ? pr : P(0)));
+      sF[4 * NCS + c] = P(0.5) * (R * vd);
+      sR[c] = spectral_radius<Math>(vd, vx * vx + vy * vy + vz * vz);
+      if constexpr (RPRE) {
+        if (s >= 8 && s < 8 + SEG) {
+#pragma unroll
+          for (int k = 0; k < 5; ++k) sRp[k * NC + cidx(lane, s - 8)] = rv[rd][k];
+        }
+      }
     }
-    const P pr = e * P(1.0 / 3.0);
-    const P vd = DIR == 0 ? vx : (DIR == 1 ? vy : vz);
-    sU[c] = E; sU[NCS + c] = Mx; sU[2 * NCS + c] = My; sU[3 * NCS + c] = Mz; sU[4 * NCS + c] = R;
-    sF[c] = P(0.5) * (DIR == 0 ? Mx : (DIR == 1 ? My : Mz));
-    sF[NCS + c] = P(0.5) * (Mx * vd + (DIR == 0 ? pr : P(0)));
-    sF[2 * NCS + c] = P(0.5) * (My * vd + (DIR == 1 ? pr : P(0)));
-    sF[3 * NCS + c] = P(0.5) * (Mz * vd + (DIR == 2 ? pr : P(0)));
-    sF[4 * NCS + c] = P(0.5) * (R * vd);
-    sR[c] = spectral_radius<Math>(vd, vx * vx + vy * vy + vz * vz);
   }
   __syncthreads();
 
@@ -219,9 +299,10 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
     sAhb[iidx(lane, ii)] = P(0);
   }
   __syncthreads();
+  const int nq = s_liveR ? 5 : 4;   // block-uniform
 
   // ---- per component: reverse WENO at every interface, then gather per cell
-  for (int q = 0; q < 5; ++q) {
+  for (int q = 0; q < nq; ++q) {
     for (int it = threadIdx.x; it < NIF; it += kAdjThreads) {
       int lane, ii;
       if (DIR == 0) { lane = it / NI; ii = it - lane * NI; }
@@ -266,14 +347,23 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
         weno7_vjp<P>(fp, (P)p.eps_s, g, gp);
         weno7_vjp<P>(fm, (P)p.eps_s, g, gm);
       }
-      P ahb = P(0);
+      P ahb = P(0), vf[8], vu[8];
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
         const P bp = t <= 6 ? gp[t] : P(0);
         const P bm = t >= 1 ? gm[7 - t] : P(0);
-        cf[t * NIF] = bp + bm;
-        cu[t * NIF] = ah * (bp - bm);
+        vf[t] = bp + bm;
+        vu[t] = ah * (bp - bm);
         ahb += u[t] * (bp - bm);
+      }
+      // slot t is position i - 3 + t; a position outside the grid is a clamped copy
+      // of the edge cell, whose adjoint it therefore joins
+      const int i = a0 - 4 + ii;
+      if (i < 3 || i > n_along - 5) fold_ghost_slots(vf, vu, 3 - i, n_along + 2 - i);
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        cf[t * NIF] = vf[t];
+        cu[t * NIF] = vu[t];
       }
       sAhb[x] += ahb;
     }
@@ -282,27 +372,14 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
       int lane, j;
       if (DIR == 0) { lane = c / SEG; j = c - lane * SEG; }
       else { j = c / LANES; lane = c - j * LANES; }
-      const int gcell = a0 + j;
       P fb = P(0), ub = P(0);
-      // cell gcell is slot 7 - k of interface j + k; the edge cells also own the
-      // clamped ghost slots beyond them (interfaces outside the grid hold zeros)
+      // cell j is slot 7 - k of interface j + k (the ghost slots are folded into the
+      // edge cells' slots; interfaces outside the grid hold zeros)
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const int x = iidx(lane, j + k);
         fb += cF[(7 - k) * NIF + x];
         ub += cU[(7 - k) * NIF + x];
-      }
-      if (gcell == 0 || gcell == n_along - 1) {
-        for (int k = 0; k < 8; ++k) {
-          const int x = iidx(lane, j + k);
-          for (int t = 0; t < 8; ++t) {
-            const bool ghost = (gcell == 0 && t < 7 - k) || (gcell == n_along - 1 && t > 7 - k);
-            if (ghost) {
-              fb += cF[t * NIF + x];
-              ub += cU[t * NIF + x];
-            }
-          }
-        }
       }
       sFb[q * NC + cidx(lane, j)] = fb;
       sUb[q * NC + cidx(lane, j)] = ub;
@@ -334,14 +411,14 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
     const P Mx = sU[NCS + sc], My = sU[2 * NCS + sc], Mz = sU[3 * NCS + sc], R = sU[4 * NCS + sc];
     P e, vx, vy, vz;
     C2PTape<P> tape;
-    if constexpr (MIXED) cons_to_prim_om_tape(p.sh[5 * N + o], Mx, My, Mz, p.sh[6 * N + o], tape, e, vx, vy, vz);
+    if constexpr (MIXED) cons_to_prim_om_tape(sEf[sc], Mx, My, Mz, sOm[sc], tape, e, vx, vy, vz);
     else cons_to_prim_tape(sU[sc], Mx, My, Mz, p.e_floor, tape, e, vx, vy, vz);
     const P v[3] = {vx, vy, vz};
     const P vd = v[DIR];
     const int ci = cidx(lane, j);
     // F/2 adjoint -> F adjoint
     P Fb[5];
-    for (int k = 0; k < 5; ++k) Fb[k] = P(0.5) * sFb[k * NC + ci];
+    for (int k = 0; k < 5; ++k) Fb[k] = k < nq ? P(0.5) * sFb[k * NC + ci] : P(0);
     P Mb[3] = {P(0), P(0), P(0)}, vb[3] = {P(0), P(0), P(0)}, Rb = P(0), pb = P(0);
     const P M[3] = {Mx, My, Mz};
     Mb[DIR] += Fb[0];
@@ -358,14 +435,14 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
     for (int k = 0; k < 3; ++k) vb[k] += rhob * d_v2 * P(2) * v[k];
     P Eb = sUb[ci];
     P Mbx = sUb[NC + ci] + Mb[0], Mby = sUb[2 * NC + ci] + Mb[1], Mbz = sUb[3 * NC + ci] + Mb[2];
-    Rb += sUb[4 * NC + ci];
+    if (nq == 5) Rb += sUb[4 * NC + ci];
     c2p_vjp_core<Math>(tape.m, tape.s, tape.r, tape.v, tape.vs, tape.invE, tape.nx, tape.ny, tape.nz, tape.capped,
                        tape.floored, pb * P(1.0 / 3.0), vb[0], vb[1], vb[2], Eb, Mbx, Mby, Mbz);
     const P out[5] = {Eb, Mbx, Mby, Mbz, Rb};
     if (DIR == 0) {
       for (int k = 0; k < 5; ++k) r_out[k * N + o] = out[k];
     } else {
-      for (int k = 0; k < 5; ++k) r_out[k * N + o] += out[k];
+      for (int k = 0; k < 5; ++k) r_out[k * N + o] = sRp[k * NC + ci] + out[k];
     }
   }
 
