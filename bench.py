@@ -425,24 +425,31 @@ def _adjoint_one(hy, grid, steps, precision):
     run = A.ConeEnergyRun(hy.hydro_config_default(*w.n, precision=precision), w.steps, min(10, w.steps), w.jets,
                           torch.from_numpy(prim[1:].copy()).cuda(), apex=jet.x0, axis=jet.direction)
     e = torch.from_numpy(prim[0].copy()).cuda()
-    kr = torch.tensor(4.0, dtype=torch.float64, requires_grad=True)
-    kc = torch.tensor(2.5, dtype=torch.float64, requires_grad=True)
-    A.cone_energy(e, kr.detach(), kc.detach(), run)            # warm-up
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    A.cone_energy(e, kr.detach(), kc.detach(), run)
-    torch.cuda.synchronize()
-    t_fwd = time.perf_counter() - t0
-    ev = e.clone().requires_grad_(True)
-    t0 = time.perf_counter()
-    J = A.cone_energy(ev, kr, kc, run)
-    J.backward()
-    torch.cuda.synchronize()
-    t_all = time.perf_counter() - t0
+    A.cone_energy(e, torch.tensor(4.0, dtype=torch.float64), torch.tensor(2.5, dtype=torch.float64), run)   # warm-up
+    # three calls of forward + backward, CUDA events on the library stream (torch's
+    # current stream); medians of the forward and backward times and of the per-call ratio
+    fwd, bwd, ratio = [], [], []
+    for _ in range(3):
+        ev = e.clone().requires_grad_(True)
+        kr = torch.tensor(4.0, dtype=torch.float64, requires_grad=True)
+        kc = torch.tensor(2.5, dtype=torch.float64, requires_grad=True)
+        mark = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize()
+        mark[0].record()
+        J = A.cone_energy(ev, kr, kc, run)
+        mark[1].record()
+        J.backward()
+        mark[2].record()
+        mark[2].synchronize()
+        f, b = mark[0].elapsed_time(mark[1]) / 1e3, mark[1].elapsed_time(mark[2]) / 1e3
+        fwd.append(f)
+        bwd.append(b)
+        ratio.append(b / f)
     res = {"precision": precision, "checkpoint_every": min(10, w.steps), "J_GeV": J.item(),
            "dJ_dk_rad": kr.grad.item(), "dJ_dk_coll": kc.grad.item(),
-           "forward_s": round(t_fwd, 3), "backward_s": round(t_all - t_fwd, 3),
-           "backward_over_forward": round((t_all - t_fwd) / t_fwd, 3)}
+           "forward_s": round(statistics.median(fwd), 5), "backward_s": round(statistics.median(bwd), 5),
+           "backward_over_forward": round(statistics.median(ratio), 3),
+           "timing": "medians of 3 calls, CUDA events"}
     return res, ev.grad
 
 
@@ -450,9 +457,10 @@ def _adjoint(hy, grid=128, steps=50):
     """The adjoint configuration: 128^3, 50 steps, checkpoint every 10, one jet
     from (-4, 0, 0) fm along +x, energy in a 30-degree cone of radius 3 fm around
     the jet axis; gradient with respect to k_rad, k_coll and e(x), in FP64 and in
-    mixed precision.  Times one forward and one forward + backward through
-    torch.autograd (wall clock, synced).  The mixed entry carries its gradient's
-    deviation from the FP64 gradient (relative, max-norm for the e field)."""
+    mixed precision.  Times three calls of forward and backward through
+    torch.autograd (CUDA events on the library stream, medians).  The mixed entry
+    carries its gradient's deviation from the FP64 gradient (relative, max-norm
+    for the e field)."""
     out, g64 = _adjoint_one(hy, grid, steps, "fp64")
     mixed, g32 = _adjoint_one(hy, grid, steps, "mixed")
     mixed["vs_fp64"] = {"J": float("%.3g" % abs(mixed["J_GeV"] / out["J_GeV"] - 1)),

@@ -185,7 +185,7 @@ def test_adjoint_full_config_128_cube_50_steps(env, full_fd):
     from (-4, 0, 0) fm along +x, cone apex at the jet start; 16 seeded
     central-difference directions at relative step 1e-6 agree to 1e-4, and the
     backward pass costs at most 4 forward passes (the median over three calls of
-    the per-call ratio, CUDA events on the library stream; measured 3.3 on B300)."""
+    the per-call ratio, CUDA events on the library stream; measured 3.2 on B300)."""
     torch = env[0]
     e, dirs, fd, J0 = full_fd
     w, prim, run, _ = _problem(env, **FULL)
@@ -221,7 +221,7 @@ def test_mixed_adjoint_full_config_against_fp64_differences(env, full_fd):
     """Mixed precision at the adjoint configuration: the 16 directional
     derivatives of the mixed adjoint agree with the FP64 central differences
     to 1e-3 relative (FP32 flux arithmetic; measured 1.5e-4), at no more than 4
-    forward costs (median per-call ratio, CUDA events; measured 3.8)."""
+    forward costs (median per-call ratio, CUDA events; measured 2.9)."""
     torch = env[0]
     e, dirs, fd, J0 = full_fd
     w, prim, run, _ = _problem(env, precision="mixed", **FULL)
