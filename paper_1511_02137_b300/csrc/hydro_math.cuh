@@ -215,10 +215,15 @@ __device__ __forceinline__ bool finite_bits(float x) { return isfinite(x); }
 
 __device__ __forceinline__ double f2d(float f) {
   const unsigned u = __float_as_uint(f);
-  const unsigned ex = (u >> 23) & 0xffu, sign = u & 0x80000000u, m = u & 0x7fffffu;
-  unsigned hi = sign | ((ex + 896u) << 20) | (m >> 3), lo = m << 29;
-  if (ex == 0u) { hi = sign; lo = 0u; }
-  if (ex == 0xffu) hi = sign | 0x7ff00000u | (m >> 3);
+  const unsigned mag = u & 0x7fffffffu;
+  // exponent and the top 20 fraction bits move down by 3 and the exponent bias
+  // grows by 1023 - 127 = 896; the low 3 fraction bits open the low word
+  unsigned hi = ((mag >> 3) + (896u << 20)) | (u & 0x80000000u), lo = u << 29;
+  if (mag < 0x00800000u) {   // zero and subnormals: signed zero
+    hi = u & 0x80000000u;
+    lo = 0u;
+  }
+  if (mag >= 0x7f800000u) hi += 896u << 20;   // infinity and NaN: exponent 255 + 896 + 896 = 2047
   return __hiloint2double((int)hi, (int)lo);
 }
 

@@ -764,12 +764,15 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
             const Store l = Lq[q];
             out = a.k.first ? u + dt * l : ca * (PF::on ? sP0[q * NC + c] : U0[q * N + o]) + cb * (u + dt * l);
           }
+          // (the mixed shadow path tests its FP32 increments: U0 is finite, as the
+          // result of the previous step or of a checked initial state)
           if constexpr (sizeof(Store) == 4) chk += out;
+          else if constexpr (SH) chk += Lq[q];
           else bad |= !finite_bits(out);
           if (PREC != kMixedShadow || Uout) Uout[q * N + o] = out;   // (the shadow stores U only at stage 3)
           outv[q] = out;
         }
-        if constexpr (sizeof(Store) == 4) bad |= !finite_bits(chk);
+        if constexpr (sizeof(Store) == 4 || SH) bad |= !finite_bits(chk);
         if constexpr (PREC == kMixedShadow) {
           // the shadow of the new state, for the sweeps that stage it next
           float sh[6];
