@@ -370,6 +370,15 @@ hydro_status hydro_step_noalloc(const hydro_config* cfg, void* d_state, int64_t 
  *                           rounds them first, as its storage does), out =
  *                           (e, v^x, v^y, v^z, floor hit 0/1) as 5 arrays of n
  *                           doubles; param = e_floor.
+ *   HYDRO_MATH_D2F          out = the FP32 rounding of in[i] by the integer-pipe
+ *                           conversion of the mixed-precision path (nearest,
+ *                           ties to even; below the FP32 normal range signed
+ *                           zero, above it infinity, NaN stays NaN); in: n
+ *                           doubles, out: n FP32 values (the first 4n bytes).
+ *   HYDRO_MATH_F2D          out[i] = the FP64 value of an FP32 input by the
+ *                           integer-pipe widening of the mixed-precision path
+ *                           (exact; FP32 subnormals give signed zero); in: n
+ *                           FP32 values (4n bytes at d_in), out: n doubles.
  * Runs on cuda_stream and synchronises it.  HYDRO_EINVAL for an unknown fn,
  * n < 0 or NULL pointers; HYDRO_ECUDA on a launch failure. */
 enum {
@@ -377,7 +386,9 @@ enum {
   HYDRO_MATH_SQRT_RSQRT = 1,
   HYDRO_MATH_C2P_FP64 = 2,
   HYDRO_MATH_C2P_FP32 = 3,
-  HYDRO_MATH_C2P_MIXED = 4
+  HYDRO_MATH_C2P_MIXED = 4,
+  HYDRO_MATH_D2F = 5,
+  HYDRO_MATH_F2D = 6
 };
 hydro_status hydro_eval_math(int32_t fn, int64_t n, const double* d_in, double* d_out, double param,
                              void* cuda_stream);

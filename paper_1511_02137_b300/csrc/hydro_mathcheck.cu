@@ -1,5 +1,6 @@
 // Test and measurement support: elementwise evaluation of the device
-// arithmetic the sweeps use (hydro_eval_math), and the FMA throughput kernels
+// arithmetic the sweeps use (hydro_eval_math: reciprocals, recoveries and the
+// integer-pipe FP64/FP32 conversions), and the FMA throughput kernels
 // that give the roofline its measured ALU peaks (hydro_alu_peak).  Neither has
 // a counterpart in the paper; the recovery evaluated here is Eq. 1 with
 // p = e/3 inverted in closed form, exactly as the sweeps call it.
@@ -22,6 +23,10 @@ __global__ void eval_math_kernel(int fn, long long n, const double* __restrict__
       sqrt_rsqrt_nr(in[i], s, y);
       out[i] = s;
       out[n + i] = y;
+    } else if (fn == HYDRO_MATH_D2F) {
+      reinterpret_cast<float*>(out)[i] = d2f_rn(in[i]);
+    } else if (fn == HYDRO_MATH_F2D) {
+      out[i] = f2d(reinterpret_cast<const float*>(in)[i]);
     } else {
       const double E = in[i], Mx = in[n + i], My = in[2 * n + i], Mz = in[3 * n + i];
       int hit = 0;
@@ -147,7 +152,7 @@ using namespace hydro;
 
 extern "C" hydro_status hydro_eval_math(int32_t fn, int64_t n, const double* d_in, double* d_out, double param,
                                         void* cuda_stream) {
-  if (fn < HYDRO_MATH_RCP || fn > HYDRO_MATH_C2P_MIXED || n < 0 || !d_in || !d_out) return HYDRO_EINVAL;
+  if (fn < HYDRO_MATH_RCP || fn > HYDRO_MATH_F2D || n < 0 || !d_in || !d_out) return HYDRO_EINVAL;
   if (n == 0) return HYDRO_OK;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   const long long blocks = (n + 255) / 256;

@@ -22,7 +22,8 @@ HYDRO_OUTFLOW, HYDRO_PERIODIC = 0, 1
 HYDRO_PRIMITIVE, HYDRO_CONSERVED = 0, 1
 HYDRO_KERNEL_SWEEP_X, HYDRO_KERNEL_SWEEP_Y, HYDRO_KERNEL_SWEEP_Z, HYDRO_KERNEL_OTHER = 0, 1, 2, 3
 HYDRO_MAX_JETS = 16
-HYDRO_MATH_RCP, HYDRO_MATH_SQRT_RSQRT, HYDRO_MATH_C2P_FP64, HYDRO_MATH_C2P_FP32, HYDRO_MATH_C2P_MIXED = range(5)
+(HYDRO_MATH_RCP, HYDRO_MATH_SQRT_RSQRT, HYDRO_MATH_C2P_FP64, HYDRO_MATH_C2P_FP32, HYDRO_MATH_C2P_MIXED,
+ HYDRO_MATH_D2F, HYDRO_MATH_F2D) = range(7)
 HYDRO_PEAK_FFMA, HYDRO_PEAK_FFMA2, HYDRO_PEAK_DFMA = range(3)
 PRECISIONS = {"fp64": HYDRO_FP64, "fp32": HYDRO_FP32, "mixed": HYDRO_MIXED}
 
@@ -443,13 +444,18 @@ def hydro_adjoint_destroy(a: Adjoint) -> None:
 
 
 def hydro_eval_math(fn: int, x_dev, param: float = 0.0, stream=None):
-    """Evaluates device routine `fn` (HYDRO_MATH_*) over the float64 CUDA tensor
-    x_dev (n values, or 4n for the recoveries); returns the output tensor
-    (n, 2n or 5n float64 values)."""
+    """Evaluates device routine `fn` (HYDRO_MATH_*) over the CUDA tensor x_dev
+    (float64: n values, or 4n for the recoveries; float32 for HYDRO_MATH_F2D);
+    returns the output tensor (n, 2n or 5n float64 values; n float32 values for
+    HYDRO_MATH_D2F)."""
     import torch
-    if x_dev.dtype != torch.float64 or not x_dev.is_cuda or not x_dev.is_contiguous():
-        raise ValueError("expected a contiguous float64 CUDA tensor")
-    if fn in (HYDRO_MATH_RCP, HYDRO_MATH_SQRT_RSQRT):
+    want = torch.float32 if fn == HYDRO_MATH_F2D else torch.float64
+    if x_dev.dtype != want or not x_dev.is_cuda or not x_dev.is_contiguous():
+        raise ValueError(f"expected a contiguous {want} CUDA tensor")
+    if fn in (HYDRO_MATH_D2F, HYDRO_MATH_F2D):
+        n = x_dev.numel()
+        out = torch.empty(n, dtype=torch.float32 if fn == HYDRO_MATH_D2F else torch.float64, device=x_dev.device)
+    elif fn in (HYDRO_MATH_RCP, HYDRO_MATH_SQRT_RSQRT):
         n = x_dev.numel()
         out = torch.empty(n * (1 if fn == HYDRO_MATH_RCP else 2), dtype=torch.float64, device=x_dev.device)
     else:

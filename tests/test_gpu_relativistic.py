@@ -80,6 +80,67 @@ def test_fp64_sqrt_rsqrt_pair_is_within_its_stated_bound(env):
     assert float(es.max()) <= 2.3e-16 and float(er.max()) <= 2.3e-16
 
 
+def test_integer_pipe_widening_matches_the_hardware_on_every_fp32_value(env):
+    """f2d, the FP32 -> FP64 widening of the mixed path on the integer pipe, on
+    all 2^32 FP32 bit patterns against CUDA's conversion (cvt.f64.f32, exact):
+    bitwise equal for zeros, normals and infinities; FP32 subnormals give the
+    signed zero; NaN stays NaN."""
+    torch, hy, _ = env
+    chunk = 1 << 28
+    bad = 0
+    for start in range(0, 1 << 32, chunk):
+        bits = torch.arange(start, start + chunk, dtype=torch.int64, device="cuda").to(torch.int32)
+        f = bits.view(torch.float32)
+        got = hy.hydro_eval_math(hy.HYDRO_MATH_F2D, f)
+        ref = f.to(torch.float64)
+        mag = bits & 0x7FFFFFFF
+        sub = (mag > 0) & (mag < 0x00800000)
+        nan = mag > 0x7F800000
+        ref = torch.where(sub, torch.copysign(torch.zeros_like(ref), ref), ref)
+        same = got.view(torch.int64) == ref.view(torch.int64)
+        ok = torch.where(nan, torch.isnan(got), same)
+        bad += int((~ok).sum())
+        del bits, f, got, ref, mag, sub, nan, same, ok
+    torch.cuda.empty_cache()
+    assert bad == 0
+
+
+def test_integer_pipe_rounding_matches_the_hardware_round_to_nearest(env):
+    """d2f_rn, the FP64 -> FP32 rounding of the mixed path on the integer pipe,
+    against CUDA's cvt.rn.f32.f64: bitwise equal for every input of magnitude
+    at least 2^-126 (the FP32 normal range, rounding to nearest even, overflow
+    to infinity), signed zero below it, NaN for NaN.  Inputs: uniformly random
+    64-bit patterns (every exponent), random doubles inside the FP32 range,
+    exact ties between adjacent floats, and the edges of the range."""
+    torch, hy, _ = env
+    rng = np.random.default_rng(11)
+    n = 1 << 22
+    pats = rng.integers(0, 2 ** 63, n, dtype=np.int64) * np.where(rng.random(n) < 0.5, 1, -1)
+    x_bits = pats.view(np.float64)
+    x_in = (2.0 ** rng.uniform(-126, 128, n)) * rng.choice([-1.0, 1.0], n) * rng.uniform(1, 2, n) / 2
+    f = (2.0 ** rng.uniform(-125, 127, n)).astype(np.float32)
+    ties = (f.astype(np.float64) + np.nextafter(f, np.float32(np.inf)).astype(np.float64)) / 2   # exact midpoints
+    fmax = float(np.finfo(np.float32).max)
+    tmin = 2.0 ** -126
+    edges = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, fmax, -fmax, fmax * (1 + 2.0 ** -25),
+                      np.nextafter(fmax * (1 + 2.0 ** -25), 0), np.nextafter(fmax * (1 + 2.0 ** -25), np.inf),
+                      tmin, -tmin, np.nextafter(tmin, 0), np.nextafter(tmin, 1), 2.0 ** -149, 1e-300, 1e300,
+                      5e-324, 1.0, 3.0, 1.0 + 2.0 ** -24, 1.0 + 2.0 ** -23 + 2.0 ** -24])
+    x = np.concatenate([x_bits, x_in, ties, -ties, edges])
+    xd = torch.from_numpy(x).cuda()
+    got = hy.hydro_eval_math(hy.HYDRO_MATH_D2F, xd)
+    ref = xd.to(torch.float32)
+    ax = xd.abs()
+    small = ax < tmin
+    nan = torch.isnan(xd)
+    ref = torch.where(small, torch.copysign(torch.zeros_like(ref), ref), ref)   # (the conversion keeps the sign)
+    same = got.view(torch.int32) == ref.view(torch.int32)
+    ok = torch.where(nan, torch.isnan(got), same)
+    print(f"d2f_rn over {x.size} inputs ({int(small.sum())} below the FP32 normal range, "
+          f"{int((ax >= 2.0 ** 128).sum())} above it): mismatches {int((~ok).sum())}")
+    assert int((~ok).sum()) == 0
+
+
 def _boosted_states(n, gamma_max, seed):
     """Conserved (E, M) of random rest-frame states: e log-uniform in [1e-3, 1e2]
     GeV/fm^3, gamma log-uniform in [1, gamma_max], isotropic directions."""
