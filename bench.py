@@ -353,21 +353,37 @@ def _e2e(hy, w, prim_pinned, out_pinned, steps, precision="fp64"):
     return sec, state_bytes, diag_bytes
 
 
-def _cpu_baseline(w, seconds_hint=20.0):
-    """The FP64 oracle as it stands, on all host cores: one RK3 step of the
-    workload (the full 256^3 grid)."""
+def _cpu_baseline(w, single_core_grid=96):
+    """The FP64 oracle as it stands: one RK3 step of the workload (the full 256^3
+    grid) on all host cores, and one step of the centre sub-grid of edge
+    `single_core_grid` on one core, whose per-cell rate is extrapolated (not run)
+    to the full workload's steps."""
     import oracle
     from paper_1511_02137_b300 import workloads as W
     threads = oracle.max_threads()
+    jets = [oracle.Jet(j.x0, j.direction, j.t_start) for j in w.jets]
     U = oracle.prim_to_cons(W.ellipsoidal_primitives(w))
     cfg = oracle.Config(*w.n, dx=w.dx, dt=w.dt, t0=w.t0)
-    jets = [oracle.Jet(j.x0, j.direction, j.t_start) for j in w.jets]
     t0 = time.perf_counter()
     oracle.run(cfg, U, 1, jets)
     sec = time.perf_counter() - t0
-    return {"value": w.cells / sec, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"1 RK3 step of the full {w.n[0]}x{w.n[1]}x{w.n[2]} workload, FP64, {threads} OpenMP threads",
-            "seconds": round(sec, 2)}
+    out = {"value": w.cells / sec, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"1 RK3 step of the full {w.n[0]}x{w.n[1]}x{w.n[2]} workload, FP64, {threads} OpenMP threads",
+           "seconds": round(sec, 2)}
+    ws = W.scaled(w, single_core_grid, steps=1)
+    U1 = oracle.prim_to_cons(W.ellipsoidal_primitives(ws))
+    cfg1 = oracle.Config(*ws.n, dx=ws.dx, dt=ws.dt, t0=ws.t0, nthreads=1)
+    t0 = time.perf_counter()
+    oracle.run(cfg1, U1, 1, jets)
+    sec1 = time.perf_counter() - t0
+    rate1 = ws.cells / sec1
+    out["single_core"] = {
+        "value": rate1, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "sample": f"1 RK3 step of the {single_core_grid}^3 centre sub-grid, FP64, 1 thread",
+        "seconds": round(sec1, 2),
+        "full_run_s_extrapolated": round(w.cells * w.steps / rate1, 1),
+        "full_run": f"{w.steps} steps of {w.n[0]}^3 at this per-cell rate: extrapolated, not run"}
+    return out
 
 
 def _batched(hy, steps, warmup, peaks=None, events=None, edge=None):
