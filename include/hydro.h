@@ -265,15 +265,19 @@ void hydro_batch_destroy(hydro_batch* b);
  * WENO7 fluxes, the LLF split, the primitive recovery and the jet source),
  * states checkpointed every `checkpoint_every` steps and recomputed segment by
  * segment in reverse.  Outflow, WENO7 only; precision HYDRO_FP64, or
- * HYDRO_MIXED (the mixed forward; its vector-Jacobian products in FP32 flux
- * arithmetic, adjoint states and stage combinations in FP64).  The derivative
+ * HYDRO_MIXED (its vector-Jacobian products in FP32 flux arithmetic, adjoint
+ * states and stage combinations in FP64).  The forward runs the step exactly
+ * as hydro_step does for the same configuration, so J and its gradient belong
+ * to the step of the context API.  The derivative
  * of the LLF alpha = max over the stencil is split equally among tying cells
  * (within 1e-12 relative in FP64, 1e-6 in mixed).
  * ------------------------------------------------------------------------- */
 typedef struct hydro_adjoint hydro_adjoint;
 
-/* Device bytes an adjoint run needs (checkpoints, two sets of segment step and
- * stage states, adjoint and scratch fields).  HYDRO_EINVAL as hydro_adjoint_create. */
+/* Device bytes an adjoint run needs (checkpoints; two sets of segment step
+ * states with, in FP64, the stage states and the primitive cache or, in mixed
+ * precision, the FP32 shadows of the stage states; adjoint and scratch fields).
+ * HYDRO_EINVAL as hydro_adjoint_create. */
 hydro_status hydro_adjoint_workspace_size(const hydro_config* cfg, int32_t nsteps, int32_t checkpoint_every,
                                           size_t* bytes);
 

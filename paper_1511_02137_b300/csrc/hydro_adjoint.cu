@@ -3,7 +3,11 @@
 // initial energy density (checkpointed every k steps, recomputed in reverse).
 // Two precisions, as the forward: FP64 throughout, or mixed (FP64 states,
 // stage combinations and adjoint accumulation; FP32 flux arithmetic and its
-// vector-Jacobian products; E^2 - |M|^2 of the recovery in FP64).
+// vector-Jacobian products; E^2 - |M|^2 of the recovery in FP64).  The forward
+// and the recomputation run the step exactly as hydro_step does (the same sweep
+// kernels and tensor maps; in mixed precision the stage states are FP32
+// increments over the FP64 step state and the sweeps stage their FP32 shadows),
+// so the gradient is that of the step the context API computes.
 //
 // The vector-Jacobian product of the right-hand side L(U) = -div F + S runs as
 // three sweeps (x, y, z), like the forward.  A tile gathers, for each of its
@@ -15,7 +19,8 @@
 // radius and the primitive recovery.  The derivative of alpha = max rho is
 // split equally among the stencil cells that tie for the maximum (to 1e-12
 // relative), the symmetric subgradient.  The z sweep adds the adjoint of the jet
-// source of Eqs. 2-3 and accumulates dJ/dk_rad and dJ/dk_coll.  Outflow
+// source of Eqs. 2-3 and accumulates dJ/dk_rad and dJ/dk_coll.  The mixed reverse
+// sweeps read the shadows the forward wrote for each stage state.  Outflow
 // boundaries only: a clamped ghost hands its adjoint to the edge cell.  The
 // backward recomputes the next segment's states from its checkpoint on a side
 // stream while the main stream reverses the current segment (two buffer sets).
@@ -66,16 +71,17 @@ template <int PREC> struct AdjTypes { using P = double; using Math = MathD; };
 template <> struct AdjTypes<HYDRO_MIXED> { using P = float; using Math = MathF; };
 
 struct VjpArgs {
-  const double* U;      // stage state the right-hand side was evaluated on
+  const double* U;      // FP64: stage state the right-hand side was evaluated on
   const double* lam;    // adjoint of the stage result; a = ascale * lam is the adjoint of L (FP64)
-  const float* sh;      // mixed: FP32 shadow of U, [7][n] = E, M^x, M^y, M^z, R, signed floored E, om
+  const float* sh;      // mixed: the forward's FP32 shadow of the stage state, [6][n] = E, M^x, M^y, M^z,
+                        // R, om (E one ulp below the FP32 floor where the FP64 recovery floors it)
   const float* lamf;    // mixed: a = ascale * lam, already scaled, in FP32
   void* r;              // output J_L^T a in the flux type (x sweep writes, y and z add)
   double* kbar;         // [2 kMaxJets]: dJ/dk_rad, dJ/dk_coll per jet (one writer per jet and stage)
   double ascale;
   int nx, ny, nz;
   double inv_dx, e_floor, eps_s;
-  float inv_dx_f, eps_s_f;   // the same rounded to FP32 on the host (mixed)
+  float inv_dx_f, eps_s_f, e_floor_f;   // the same rounded to FP32 on the host (mixed)
   double rad_per_k, coll_per_k, k_rad, k_coll, t4coef, inv_vol;
   JetStage jets;
 };
@@ -182,7 +188,7 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
   // this sweep adds to) is issued before any of them is used, so that the block
   // waits for one round of memory latency.
   constexpr int RND = (NCS + kAdjThreads - 1) / kAdjThreads;   // positions per thread
-  constexpr int NSH = MIXED ? 7 : 5;                            // state words per position
+  constexpr int NSH = MIXED ? 6 : 5;                            // state words per position
   constexpr bool RPRE = DIR != 0;
   P av[RND][5], uv[RND][NSH], rv[RND][5];
   bool live = false, liveR = false;
@@ -248,9 +254,12 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
       const P E = uv[rd][0], Mx = uv[rd][1], My = uv[rd][2], Mz = uv[rd][3], R = uv[rd][4];
       int hit = 0;
       if constexpr (MIXED) {
-        cons_to_prim_om(uv[rd][5], Mx, My, Mz, uv[rd][6], e, vx, vy, vz, hit);
-        sEf[c] = uv[rd][5];
-        sOm[c] = uv[rd][6];
+        // the recovery of the forward's shadow (cons_to_prim_shadow): the floor acts
+        // where the shadow's E lies below the FP32 floor
+        const float Efs = E >= p.e_floor_f ? E : -p.e_floor_f;
+        cons_to_prim_om(Efs, Mx, My, Mz, uv[rd][5], e, vx, vy, vz, hit);
+        sEf[c] = Efs;
+        sOm[c] = uv[rd][5];
       } else {
         cons_to_prim<MathD>(E, Mx, My, Mz, p.e_floor, e, vx, vy, vz, hit);
       }
@@ -460,14 +469,26 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
         const int j = cl[2] - a0, lane = cl[0] - l0;
         const int sc = sidx(lane, j + 8);
         const unsigned o = offset(cl[2], cl[0]);
-        const double Ed = p.U[o], Mxd = p.U[N + o], Myd = p.U[2 * N + o], Mzd = p.U[3 * N + o];
         // S0 = inv_vol (k_rad C T^3 l / hc^2 + k_coll C T^2 / hc), T = (e t4)^(1/4): S = (S0, n S0, 0).
-        // The source runs in FP64 in both precisions (FP64 recovery at the jet cell).
+        // T comes from the recovery the forward used at the jet cell: FP64 from the
+        // FP64 state, or (mixed) FP32 from the shadow; its derivative in FP64.
+        double Ed, Mxd, Myd, Mzd, es;
+        if constexpr (MIXED) {
+          const float* S = p.sh;
+          float ef, vxf, vyf, vzf, v2f, rdf;
+          int hs = 0;
+          cons_to_prim_shadow_rho(S[o], S[N + o], S[2 * N + o], S[3 * N + o], S[5 * N + o], p.e_floor_f, ef, vxf,
+                                  vyf, vzf, v2f, rdf, hs);
+          Ed = S[o]; Mxd = S[N + o]; Myd = S[2 * N + o]; Mzd = S[3 * N + o];
+          es = ef;
+        } else {
+          Ed = p.U[o]; Mxd = p.U[N + o]; Myd = p.U[2 * N + o]; Mzd = p.U[3 * N + o];
+          double vsx, vsy, vsz;
+          int hs = 0;
+          cons_to_prim<MathD>(Ed, Mxd, Myd, Mzd, p.e_floor, es, vsx, vsy, vsz, hs);
+        }
         const double aE = sA[sc], aMx = sA[NCS + sc], aMy = sA[2 * NCS + sc], aMz = sA[3 * NCS + sc];
         const double Sb = aE + p.jets.dir[jn][0] * aMx + p.jets.dir[jn][1] * aMy + p.jets.dir[jn][2] * aMz;
-        double es, vsx, vsy, vsz;
-        int hs = 0;
-        cons_to_prim<MathD>(Ed, Mxd, Myd, Mzd, p.e_floor, es, vsx, vsy, vsz, hs);
         const double T = temperature(es, p.t4coef);
         const double l = p.jets.ell[jn];
         p.kbar[2 * jn] += Sb * p.rad_per_k * T * T * T * l * p.inv_vol;
@@ -534,23 +555,6 @@ __global__ void adj_combine_kernel(int mode, double ca, double cb, double* lamA,
       lam0[i] = next;
     }
     if (lamf) lamf[i] = fscale * d2f_rn(next);
-  }
-}
-
-// Mixed precision: FP32 shadow of a stage state for the reverse sweeps, with
-// the floored E and om = 1 - |M|/E of the recovery (E^2 - |M|^2 in FP64).
-__global__ void shadow_kernel(const double* U, float* sh, size_t n, double e_floor) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double E = U[i], Mx = U[n + i], My = U[2 * n + i], Mz = U[3 * n + i];
-    float Efs, om;
-    mixed_om(E, Mx, My, Mz, e_floor, Efs, om);
-    sh[i] = d2f_rn(E);
-    sh[n + i] = d2f_rn(Mx);
-    sh[2 * n + i] = d2f_rn(My);
-    sh[3 * n + i] = d2f_rn(Mz);
-    sh[4 * n + i] = d2f_rn(U[4 * n + i]);
-    sh[5 * n + i] = Efs;
-    sh[6 * n + i] = om;
   }
 }
 
@@ -623,6 +627,19 @@ unsigned grid_1d(size_t n) {
 
 using namespace hydro;
 
+// One set of segment buffers: the step and stage states of up to `every` steps
+// recomputed from a checkpoint.  FP64 keeps the stage states in FP64 (U1, U2 of
+// each step); mixed precision keeps what its reverse sweeps read, the FP32
+// shadows of the three stage states of each step (the stage states themselves
+// are FP32 increments in the accumulator while the step runs).
+struct AdjSet {
+  std::vector<double*> seg;     // every + 1 step states
+  std::vector<double*> stages;  // FP64: 2 every stage states
+  std::vector<float*> shd;      // mixed: 3 every + 1 shadows [6][n] (the last one: of the segment's end state)
+  double* rhs = nullptr;        // accumulator of the sweeps
+  double* prim = nullptr;       // FP64: primitive cache of the x sweep
+};
+
 struct hydro_adjoint {
   hydro_config cfg;
   size_t n = 0;
@@ -631,17 +648,12 @@ struct hydro_adjoint {
   char* ws = nullptr;
   bool owns_ws = false;          // ws came from cudaMalloc (no caller workspace)
   std::vector<double*> ckpt;     // states at steps 0, every, 2 every, ...
-  std::vector<double*> seg;      // (every + 1) step states for the recomputed segment
-  double* rhs = nullptr;
-  std::vector<double*> stages;   // every x 2 stage states (U1, U2) of the segment
-  // a second segment buffer set, refilled on a side stream while the main stream
-  // reverses the other one (set of segment k: (nckpt - 1 - k) & 1)
-  std::vector<double*> seg_b, stages_b;
-  double* rhs_b = nullptr;
+  // two segment buffer sets: the set of segment k is (nckpt - 1 - k) & 1; one is
+  // refilled on a side stream while the main stream reverses the other
+  AdjSet set[2];
   cudaStream_t side = nullptr;
   cudaEvent_t ev_ready[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr}, ev_start = nullptr;
   double *lamA = nullptr, *lamB = nullptr, *lam0 = nullptr, *r = nullptr, *prim = nullptr;
-  float* sh = nullptr;           // mixed: FP32 shadow of the stage state under reverse [7][n]
   float* lamf = nullptr;         // mixed: FP32 scaled adjoint input of the next reverse sweep [5][n]
   double* kbar = nullptr;        // [2]
   double* partial = nullptr;     // cone partial sums
@@ -650,7 +662,7 @@ struct hydro_adjoint {
   double jx0[kMaxJets][3], jn[kMaxJets][3], jt[kMaxJets];
   ConeArgs cone;
   bool forward_done = false;
-  bool last_kept = false;        // the forward left the last segment's states in seg / stages
+  bool last_kept = false;        // the forward left the last segment's states in set 0
   double J = 0.0;
 };
 
@@ -685,7 +697,6 @@ SweepArgs sweep_base(const hydro_adjoint* a) {
   SweepArgs s;
   std::memset(&s, 0, sizeof(s));
   const hydro_config& g = a->cfg;
-  s.rhs = a->rhs;
   s.diag = a->diag;
   s.nx = g.nx;
   s.ny = g.ny;
@@ -699,37 +710,66 @@ SweepArgs sweep_base(const hydro_adjoint* a) {
   s.src.coll = g.k_coll * g.cr_over_cf / g.hbarc;
   s.src.t4coef = g.hbarc * g.hbarc * g.hbarc / (M_PI * M_PI / 30.0 * g.dof);
   s.src.inv_vol = 1.0 / (g.dx * g.dx * g.dx);
+  s.wait_ns = wait_limit_ns(g);
   return s;
 }
 
-// One forward step from `in` (step index n) to `out`; the two intermediate stage
-// states go to s1, s2.
-cudaError_t forward_step(hydro_adjoint* a, int64_t n, const double* in, double* s1, double* s2, double* out,
-                         cudaStream_t stream, double* rhs) {
+// One forward step from `in` (step index n, position i in its segment set) to
+// `out`, as hydro_step runs it (same kernels, tensor maps where the grid admits
+// them): FP64 writes the stage states to the set's stages[2i], stages[2i + 1];
+// mixed precision reads the shadow of `in` from shd[3i] (computed here at i = 0)
+// and writes the shadows of the next stage states and of `out` to shd[3i + 1 ..
+// 3i + 3].
+cudaError_t forward_step(hydro_adjoint* a, int64_t n, AdjSet& S, int i, const double* in, double* out,
+                         cudaStream_t stream) {
+  const hydro_config& g = a->cfg;
+  const bool mixed = g.precision == HYDRO_MIXED;
   SweepArgs s = sweep_base(a);
-  s.rhs = rhs;
+  s.rhs = S.rhs;
   s.U0 = in;
-  const double vol = a->cfg.dx * a->cfg.dx * a->cfg.dx;
-  const double* Us[3] = {in, s1, s2};
-  double* Uo[3] = {s1, s2, out};
+  s.P = mixed ? nullptr : S.prim;
+  const double vol = g.dx * g.dx * g.dx;
   cudaError_t err = cudaSuccess;
+  SweepMaps maps[3][3];
+  bool tma;
+  if (mixed) {
+    if (i == 0) err = launch_shadow(in, S.shd[0], a->n, g.e_floor, stream);
+    void* bufs[3] = {const_cast<double*>(in), const_cast<double*>(in), const_cast<double*>(in)};
+    void* shs[3] = {S.shd[3 * i], S.shd[3 * i + 1], S.shd[3 * i + 2]};
+    tma = encode_sweep_tmaps(g.precision, 7, bufs, S.rhs, g.nx, g.ny, g.nz, maps, shs);
+  } else {
+    void* bufs[3] = {const_cast<double*>(in), S.stages[2 * i], S.stages[2 * i + 1]};
+    tma = encode_sweep_tmaps(g.precision, 7, bufs, S.rhs, g.nx, g.ny, g.nz, maps);
+  }
   for (int st = 0; st < 3 && err == cudaSuccess; ++st) {
-    jet_stage(a, a->cfg.t0 + ((double)n + kStageC[st]) * a->cfg.dt, s.jets);
-    s.src.wdt_vol = a->cfg.dt * kStageW[st] * vol;
-    s.U = Us[st];
-    s.Uout = Uo[st];
+    jet_stage(a, g.t0 + ((double)n + kStageC[st]) * g.dt, s.jets);
+    s.src.wdt_vol = g.dt * kStageW[st] * vol;
+    if (mixed) {   // stage states as FP32 increments over U0 in the accumulator
+      s.U = in;
+      s.Uout = st == 2 ? out : nullptr;
+      s.S = S.shd[3 * i + st];
+      s.Sout = S.shd[3 * i + st + 1];
+    } else {
+      s.U = st == 0 ? in : S.stages[2 * i + st - 1];
+      s.Uout = st == 2 ? out : S.stages[2 * i + st];
+    }
     s.a = kA[st];
     s.b = kB[st];
-    for (int d = 0; d < 3 && err == cudaSuccess; ++d) err = launch_sweep(a->cfg.precision, 7, d, s, stream);
+    for (int d = 0; d < 3 && err == cudaSuccess; ++d)
+      err = launch_sweep(g.precision, 7, d, s, stream, tma ? &maps[st][d] : nullptr);
   }
   return err;
 }
 
-cudaError_t vjp(hydro_adjoint* a, int64_t n, int st, const double* Uk, const double* lam, double ascale) {
+// The reverse sweeps of stage st of step n, on the stage state Uk (FP64) or its
+// shadow sh (mixed).
+cudaError_t vjp(hydro_adjoint* a, int64_t n, int st, const double* Uk, const float* sh, const double* lam,
+                double ascale) {
   VjpArgs p;
   std::memset(&p, 0, sizeof(p));
   const hydro_config& g = a->cfg;
   p.U = Uk;
+  p.sh = sh;
   p.lam = lam;
   p.r = a->r;
   p.kbar = a->kbar;
@@ -742,6 +782,7 @@ cudaError_t vjp(hydro_adjoint* a, int64_t n, int st, const double* Uk, const dou
   p.eps_s = kW7EpsScale * g.weno_eps;
   p.inv_dx_f = (float)p.inv_dx;
   p.eps_s_f = (float)p.eps_s;
+  p.e_floor_f = (float)g.e_floor;
   p.rad_per_k = g.cr_over_cf / (g.hbarc * g.hbarc);
   p.coll_per_k = g.cr_over_cf / g.hbarc;
   p.k_rad = g.k_rad;
@@ -751,11 +792,8 @@ cudaError_t vjp(hydro_adjoint* a, int64_t n, int st, const double* Uk, const dou
   jet_stage(a, g.t0 + ((double)n + kStageC[st]) * g.dt, p.jets);
   cudaError_t err;
   if (g.precision == HYDRO_MIXED) {
-    p.sh = a->sh;
     p.lamf = a->lamf;
-    shadow_kernel<<<grid_1d(a->n), 256, 0, a->stream>>>(Uk, a->sh, a->n, g.e_floor);
-    err = cudaGetLastError();
-    if (err == cudaSuccess) err = launch_vjp<HYDRO_MIXED, 0>(p, a->stream);
+    err = launch_vjp<HYDRO_MIXED, 0>(p, a->stream);
     if (err == cudaSuccess) err = launch_vjp<HYDRO_MIXED, 1>(p, a->stream);
     if (err == cudaSuccess) err = launch_vjp<HYDRO_MIXED, 2>(p, a->stream);
   } else {
@@ -803,28 +841,29 @@ size_t adjoint_layout(hydro_adjoint* a, char* base) {
     if (p) p += s;
     return q;
   };
-  const size_t n = a->n, f5 = 5 * n * sizeof(double);
+  const bool mixed = a->cfg.precision == HYDRO_MIXED;
+  const size_t n = a->n, f5 = 5 * n * sizeof(double), f6 = 6 * n * sizeof(float);
   a->ckpt.clear();
-  a->seg.clear();
-  a->stages.clear();
-  a->seg_b.clear();
-  a->stages_b.clear();
   for (int k = 0; k < a->nckpt; ++k) a->ckpt.push_back(reinterpret_cast<double*>(take(f5)));
-  for (int k = 0; k <= a->every; ++k) a->seg.push_back(reinterpret_cast<double*>(take(f5)));
-  for (int k = 0; k < 2 * a->every; ++k) a->stages.push_back(reinterpret_cast<double*>(take(f5)));
-  a->rhs = reinterpret_cast<double*>(take(f5));
-  for (int k = 0; k <= a->every; ++k) a->seg_b.push_back(reinterpret_cast<double*>(take(f5)));
-  for (int k = 0; k < 2 * a->every; ++k) a->stages_b.push_back(reinterpret_cast<double*>(take(f5)));
-  a->rhs_b = reinterpret_cast<double*>(take(f5));
+  for (AdjSet& S : a->set) {
+    S.seg.clear();
+    S.stages.clear();
+    S.shd.clear();
+    for (int k = 0; k <= a->every; ++k) S.seg.push_back(reinterpret_cast<double*>(take(f5)));
+    if (mixed) {
+      for (int k = 0; k <= 3 * a->every; ++k) S.shd.push_back(reinterpret_cast<float*>(take(f6)));
+    } else {
+      for (int k = 0; k < 2 * a->every; ++k) S.stages.push_back(reinterpret_cast<double*>(take(f5)));
+      S.prim = reinterpret_cast<double*>(take(f5));
+    }
+    S.rhs = reinterpret_cast<double*>(take(f5));
+  }
   a->lamA = reinterpret_cast<double*>(take(f5));
   a->lamB = reinterpret_cast<double*>(take(f5));
   a->lam0 = reinterpret_cast<double*>(take(f5));
   a->r = reinterpret_cast<double*>(take(f5));
   a->prim = reinterpret_cast<double*>(take(f5));
-  if (a->cfg.precision == HYDRO_MIXED) {
-    a->sh = reinterpret_cast<float*>(take(7 * n * sizeof(float)));
-    a->lamf = reinterpret_cast<float*>(take(5 * n * sizeof(float)));
-  }
+  if (mixed) a->lamf = reinterpret_cast<float*>(take(5 * n * sizeof(float)));
   a->kbar = reinterpret_cast<double*>(take(2 * kMaxJets * sizeof(double)));
   a->partial = reinterpret_cast<double*>(take(kConeBlocks * sizeof(double)));
   a->diag = reinterpret_cast<DevDiag*>(take(sizeof(DevDiag)));
@@ -934,31 +973,19 @@ hydro_status hydro_adjoint_forward(hydro_adjoint* a, const double* d_prim5, doub
   cudaError_t err = cudaMemcpyAsync(a->prim, d_prim5, f5, cudaMemcpyDeviceToDevice, a->stream);
   if (err == cudaSuccess) err = cudaMemsetAsync(a->diag, 0, sizeof(DevDiag), a->stream);
   if (err == cudaSuccess) err = launch_init(HYDRO_FP64, HYDRO_PRIMITIVE, a->prim, a->ckpt[0], a->n, a->diag, a->stream);
-  // march, keeping a checkpoint every `every` steps; other states ping-pong in
-  // seg[0], seg[1].  The last segment keeps its step and stage states where the
-  // reverse sweep expects them, so that the reverse sweep need not replay it.
-  const int s_last = (a->nckpt - 1) * a->every;
+  // march segment by segment from each checkpoint, step i of a segment at position
+  // i of set 0, the last step of a segment ending in the next checkpoint.  The last
+  // segment's states stay in set 0 where the reverse sweep reads them, so that the
+  // reverse sweep need not replay it.
+  AdjSet& S = a->set[0];
   const double* cur = a->ckpt[0];
-  int pp = 0;
-  for (int s = 0; s < a->nsteps && err == cudaSuccess; ++s) {
-    if (s >= s_last) {
-      const int i = s - s_last;
-      if (i == 0) err = cudaMemcpyAsync(a->seg[0], cur, 5 * a->n * sizeof(double), cudaMemcpyDeviceToDevice, a->stream);
-      if (err == cudaSuccess)
-        err = forward_step(a, s, a->seg[i], a->stages[2 * i], a->stages[2 * i + 1], a->seg[i + 1], a->stream, a->rhs);
-      cur = a->seg[i + 1];
-      continue;
+  for (int k = 0; k < a->nckpt && err == cudaSuccess; ++k) {
+    const int s0 = k * a->every, len = std::min(a->nsteps, s0 + a->every) - s0;
+    for (int i = 0; i < len && err == cudaSuccess; ++i) {
+      double* out = (i == len - 1 && k + 1 < a->nckpt) ? a->ckpt[k + 1] : S.seg[i + 1];
+      err = forward_step(a, s0 + i, S, i, i == 0 ? a->ckpt[k] : S.seg[i], out, a->stream);
+      cur = out;
     }
-    const int k = (s + 1) / a->every;
-    double* next;
-    if ((s + 1) % a->every == 0 && k < a->nckpt) {
-      next = a->ckpt[k];
-    } else {
-      next = a->seg[pp];
-      pp ^= 1;
-    }
-    err = forward_step(a, s, cur, a->stages[0], a->stages[1], next, a->stream, a->rhs);
-    cur = next;
   }
   if (err == cudaSuccess) cone_energy_kernel<<<kConeBlocks, 256, 0, a->stream>>>(cur, a->cone, a->partial);
   std::vector<double> part(kConeBlocks);
@@ -996,16 +1023,14 @@ hydro_status hydro_adjoint_backward(hydro_adjoint* a, double dJ, double* grad_k_
   // segments in reverse: the step and stage states of a segment are recomputed
   // from its checkpoint into one of two buffer sets on the side stream while the
   // main stream walks the previous segment's steps backwards in the other set
-  // (the reverse sweeps leave most issue slots idle; the forward sweeps fill them)
+  const bool mixed = a->cfg.precision == HYDRO_MIXED;
   auto set_of = [&](int k) { return (a->nckpt - 1 - k) & 1; };
   auto recompute = [&](int k, cudaStream_t st) {
     const int s0 = k * a->every, len = std::min(a->nsteps, s0 + a->every) - s0;
-    std::vector<double*>& sg = set_of(k) ? a->seg_b : a->seg;
-    std::vector<double*>& sta = set_of(k) ? a->stages_b : a->stages;
-    double* rhs = set_of(k) ? a->rhs_b : a->rhs;
-    cudaError_t e = cudaMemcpyAsync(sg[0], a->ckpt[k], 5 * a->n * sizeof(double), cudaMemcpyDeviceToDevice, st);
-    for (int s = 0; s < len && e == cudaSuccess; ++s)
-      e = forward_step(a, s0 + s, sg[s], sta[2 * s], sta[2 * s + 1], sg[s + 1], st, rhs);
+    AdjSet& S = a->set[set_of(k)];
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < len && e == cudaSuccess; ++i)
+      e = forward_step(a, s0 + i, S, i, i == 0 ? a->ckpt[k] : S.seg[i], S.seg[i + 1], st);
     return e;
   };
   const int last = a->nckpt - 1;
@@ -1025,19 +1050,23 @@ hydro_status hydro_adjoint_backward(hydro_adjoint* a, double dJ, double* grad_k_
     if (err == cudaSuccess && k < last) err = cudaStreamWaitEvent(a->stream, a->ev_ready[set_of(k)], 0);
     const int s0 = k * a->every;
     const int len = std::min(a->nsteps, s0 + a->every) - s0;
-    const std::vector<double*>& sg = set_of(k) ? a->seg_b : a->seg;
-    const std::vector<double*>& sta = set_of(k) ? a->stages_b : a->stages;
+    const AdjSet& S = a->set[set_of(k)];
     for (int s = len - 1; s >= 0 && err == cudaSuccess; --s) {
       const int64_t n = s0 + s;
-      const double* Us[3] = {sg[s], sta[2 * s], sta[2 * s + 1]};
+      // the stage states (FP64) or their shadows (mixed) of step n
+      auto Uk = [&](int st) -> const double* {
+        if (mixed) return nullptr;
+        return st == 0 ? (s == 0 ? a->ckpt[k] : S.seg[s]) : S.stages[2 * s + st - 1];
+      };
+      auto Sk = [&](int st) -> const float* { return mixed ? S.shd[3 * s + st] : nullptr; };
       // stage 3: U = 1/3 U0 + 2/3 (U2 + dt L(U2))
-      err = vjp(a, n, 2, Us[2], a->lamA, kB[2] * a->cfg.dt);
+      err = vjp(a, n, 2, Uk(2), Sk(2), a->lamA, kB[2] * a->cfg.dt);
       if (err == cudaSuccess) err = combine(a, 0, 2);
       // stage 2: U2 = 3/4 U0 + 1/4 (U1 + dt L(U1))
-      if (err == cudaSuccess) err = vjp(a, n, 1, Us[1], a->lamB, kB[1] * a->cfg.dt);
+      if (err == cudaSuccess) err = vjp(a, n, 1, Uk(1), Sk(1), a->lamB, kB[1] * a->cfg.dt);
       if (err == cudaSuccess) err = combine(a, 1, 1);
       // stage 1: U1 = U0 + dt L(U0)
-      if (err == cudaSuccess) err = vjp(a, n, 0, Us[0], a->lamA, kB[0] * a->cfg.dt);
+      if (err == cudaSuccess) err = vjp(a, n, 0, Uk(0), Sk(0), a->lamA, kB[0] * a->cfg.dt);
       if (err == cudaSuccess) err = combine(a, 2, 0);
       std::swap(a->lamA, a->lam0);   // adjoint of the step's input becomes the next output adjoint
     }

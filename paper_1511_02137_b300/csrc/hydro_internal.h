@@ -168,12 +168,13 @@ bool encode_batch_tmaps(int precision, void* const bufs[3], void* rhs, int nev, 
 cudaError_t launch_reset_vmax(DevDiag* diags, int n, cudaStream_t s);
 
 // Tensor maps of one sweep launch: `stage` boxes the staged cells of a tile in
-// the state the right-hand side is evaluated on (FP64 and FP32); `rhs`, `u0` and
-// `ust` box the tile's updated cells in the accumulator, the step state and the
-// stage state.  FP32-flux (FP32, mixed) sweeps fetch their phase-3 operands
-// through them (y and z) and store their accumulator values through `rhs` (x, y).
+// the state the right-hand side is evaluated on (FP64 and FP32) or in its FP32
+// shadow (mixed); `rhs` and `u0` box the tile's updated cells in the accumulator
+// and the step state.  FP32-flux (FP32, mixed) sweeps fetch their phase-3
+// operands through them (y and z) and store their accumulator values through
+// `rhs` (x, y).
 struct SweepMaps {
-  CUtensorMap stage, rhs, u0, ust;
+  CUtensorMap stage, rhs, u0;
 };
 
 // Launches one directional sweep (dir 0/1/2) for the given precision
@@ -190,8 +191,9 @@ cudaError_t launch_sweep(int precision, int order, int dir, const SweepArgs& a, 
 // maps unusable) when the grid does not meet the TMA layout rules (row pitch a
 // multiple of 16 bytes) or the driver entry point is missing; callers then use
 // plain loads.
-// shadows (may be NULL): for mixed precision, the FP32 shadows [6][n] of the three
-// stage states, whose staging boxes then go into the maps' `stage` entries.
+// shadows: for mixed precision (required there; NULL otherwise), the FP32 shadows
+// [6][n] of the three stage states, whose staging boxes go into the maps' `stage`
+// entries.
 bool encode_sweep_tmaps(int precision, int order, void* const bufs[3], void* rhs, int nx, int ny, int nz,
                         SweepMaps maps[3][3], void* const shadows[3] = nullptr);
 

@@ -227,20 +227,8 @@ __device__ __forceinline__ double f2d(float f) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
-// Split in two: mixed_om forms the floored E (as FP32, negated when the floor
-// acted) and om; cons_to_prim_om recovers the primitives from them in FP32.
-__device__ __forceinline__ void mixed_om(double E, double Mx, double My, double Mz, double e_floor, float& Ef_signed,
-                                         float& om) {
-  double Ee = E;
-  const bool floored = !(Ee >= e_floor);
-  if (floored) Ee = e_floor;
-  const double D = Ee * Ee - (Mx * Mx + My * My + Mz * Mz);
-  const float Ef = d2f_rn(Ee), mx = d2f_rn(Mx), my = d2f_rn(My), mz = d2f_rn(Mz);
-  const float Mabs = sqrt_approx(mx * mx + my * my + mz * mz);
-  om = d2f_rn(D) * rcp_approx(Ef * (Ef + Mabs));
-  Ef_signed = floored ? -Ef : Ef;
-}
-
+// The FP32 part of the mixed recovery: primitives from the floored E (as FP32,
+// negated when the floor acted) and om = 1 - |M|/E (see mixed_shadow).
 __device__ __forceinline__ void cons_to_prim_om(float Ef_signed, float mx, float my, float mz, float om_in, float& e,
                                                 float& vx, float& vy, float& vz, int& hit) {
   if (Ef_signed < 0.0f) hit = 1;
@@ -283,30 +271,14 @@ __device__ __forceinline__ float mixed_om_of(double Ee, double Mx, double My, do
   return d2f_rn(D) * rcp_approx(Eef * (Eef + Mabs));
 }
 
-// The mixed recovery of the sweeps, given the state in FP64 and its FP32
-// roundings (converted once, on the integer pipe, and shared with the fluxes).
-__device__ __forceinline__ void cons_to_prim_mixed_f(double E, double Mx, double My, double Mz, float Ef, float mx,
-                                                     float my, float mz, double e_floor, float& e, float& vx,
-                                                     float& vy, float& vz, int& hit) {
-  double Ee = E;
-  const bool floored = mixed_floored(E, e_floor);
-  float Eef = Ef;
-  if (floored) {
-    Ee = e_floor;
-    Eef = d2f_rn(e_floor);
-  }
-  const float om = mixed_om_of(Ee, Mx, My, Mz, Eef, mx, my, mz);
-  cons_to_prim_om(floored ? -Eef : Eef, mx, my, mz, om, e, vx, vy, vz, hit);
-}
-
 // The FP32 shadow of an FP64 mixed-precision state, six values per cell that
 // carry everything the sweeps need from it: the roundings of E, M^x, M^y, M^z
 // and R, and om = 1 - |M|/E of the recovery (E^2 - |M|^2 in FP64).  The stored
 // E satisfies !(E_s >= e_floor_f) exactly when the FP64 recovery floors E
 // (E_s is moved by at most one FP32 ulp, and only for an E within one ulp below
 // the floor), so that a sweep reading the shadow takes the FP64 floor decision.
-// From a shadow, cons_to_prim_shadow returns the same primitives, bit for bit,
-// as cons_to_prim_mixed_f from the FP64 state; the sweeps use
+// From a shadow, cons_to_prim_shadow recovers the primitives (the FP64 floor
+// decision, om from E^2 - |M|^2 in FP64, the rest in FP32); the sweeps use
 // cons_to_prim_shadow_rho, the same closed form with s from a reciprocal
 // square root, which also serves the spectral radius.
 __device__ __forceinline__ void mixed_shadow(double E, double Mx, double My, double Mz, double R, double e_floor,

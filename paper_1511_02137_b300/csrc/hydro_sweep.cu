@@ -50,15 +50,15 @@ namespace hydro {
 // which the x sweep starts (b delta_k + b dt L_x), the y sweep continues and
 // the z sweep finishes, forming U_{k+1} = U0 + delta_{k+1} in FP64 for the
 // shadow and, at the last stage, as the new FP64 state.  The increments carry
-// FP32 accuracy relative to their own size, as HYDRO_MIXED's FP32 stage
-// increments do; no FP64 stage state other than U0 is stored.
+// FP32 accuracy relative to their own size; no FP64 stage state other than U0
+// is stored.  Every mixed-precision run (single grid, batch, the adjoint's
+// forward) takes this form.
 constexpr int kMixedShadow = 3;
 template <int PREC> struct Types;
 template <> struct Types<HYDRO_FP64> { using Store = double; using Flux = double; using Math = MathD; };
 template <> struct Types<HYDRO_FP32> { using Store = float; using Flux = float; using Math = MathF; };
-template <> struct Types<HYDRO_MIXED> { using Store = double; using Flux = float; using Math = MathF; };
 template <> struct Types<kMixedShadow> { using Store = double; using Flux = float; using Math = MathF; };
-template <int PREC> constexpr bool kIsMixed = PREC == HYDRO_MIXED || PREC == kMixedShadow;
+template <int PREC> constexpr bool kIsMixed = PREC == kMixedShadow;
 // Fields of a staged cell as stored: 5, or 6 for the mixed shadow (with om).
 template <int PREC> constexpr int kStagedFields = PREC == kMixedShadow ? 6 : 5;
 
@@ -209,8 +209,8 @@ __device__ __forceinline__ void publish_block(T vmax, unsigned hits, DevDiag* d,
 }
 
 // FP32 flux arithmetic issues fast enough that the phase-3 operands (the
-// accumulator of the y and z sweeps, the step state U0 and, in mixed precision,
-// the stage state) are fetched into shared memory asynchronously at the start
+// accumulator of the y and z sweeps and the step state U0) are fetched into
+// shared memory asynchronously at the start
 // of the tile, so that their latency hides behind phases 1 and 2.  FP64 tiles
 // are bound by the FP64 pipe and keep the direct loads (and their occupancy).
 // The mixed shadow's x sweep also fetches the accumulator (delta_k).
@@ -218,21 +218,19 @@ template <int PREC, int DIR>
 struct Prefetch {
   static constexpr bool on = sizeof(typename Types<PREC>::Flux) == 4 && (DIR != 0 || PREC == kMixedShadow);
   static constexpr int rhs = on ? 5 : 0;                      // accumulator fields
-  // step-state operands in flux-type words per cell: U0 (FP32), U0 and U (mixed,
-  // FP64), U0 (mixed shadow, FP64)
-  static constexpr int state_words =
-      on && DIR == 2 ? (PREC == kMixedShadow ? 10 : (PREC == HYDRO_MIXED ? 20 : 5)) : 0;
+  // step-state operands in flux-type words per cell: U0 (FP32, or FP64 in mixed
+  // precision)
+  static constexpr int state_words = on && DIR == 2 ? (PREC == kMixedShadow ? 10 : 5) : 0;
 };
 
 // Single-grid WENO7 sweeps stage interior tiles with one TMA copy.  FP64 copies
 // straight into the tile's U array; FP32 tiles interleave U with F_d/2, so their
 // copy lands in a separate staging box that phase 1 reads; the mixed shadow's x
 // and y sweeps copy the shadow the same way (its z tile keeps plain loads: the
-// staging box would cost it a resident block per SM).  HYDRO_MIXED tiles
-// convert every staged value and load through registers.
+// staging box would cost it a resident block per SM).
 template <int PREC, int DIR = 0>
 __host__ __device__ constexpr bool tma_staged() {
-  return PREC == kMixedShadow ? DIR != 2 : PREC != HYDRO_MIXED;
+  return PREC == kMixedShadow ? DIR != 2 : true;
 }
 
 // Shared memory of one tile, in units of the flux type (word offsets): U, F_d/2
@@ -333,7 +331,7 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   using PF = Prefetch<PREC, DIR>;
   using TL = TileLayout<PREC, ORDER, DIR, SEG, LANES>;
   F* sPr = reinterpret_cast<F*>(smem_raw) + TL::pr;                          // [5][NC] accumulator
-  Store* sP0 = reinterpret_cast<Store*>(reinterpret_cast<F*>(smem_raw) + TL::p0);   // [5][NC] U0, then (mixed) [5][NC] U
+  Store* sP0 = reinterpret_cast<Store*>(reinterpret_cast<F*>(smem_raw) + TL::p0);   // [5][NC] U0
   // every tile shape updates one cell per thread (phase 3 and its operands)
   static_assert(NC == kThreads, "one updated cell per thread");
   // the mixed shadow's z sweep needs U0 at every stage (U_{k+1} = U0 + delta_{k+1}),
@@ -346,15 +344,13 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
     // past the grid and is filled with zeros there, which phase 3 does not read)
     if (threadIdx.x == 0 && pf_want) {
       const unsigned bytes = (unsigned)(5 * NC * sizeof(F) +
-                                        (need_u0 ? 5 * NC * sizeof(Store) : 0) +
-                                        (FINAL && PREC == HYDRO_MIXED ? 5 * NC * sizeof(Store) : 0));
+                                        (need_u0 ? 5 * NC * sizeof(Store) : 0));
       mbar_expect_tx(tb->pf, bytes);
       if (!a.withhold) {
         const int c0 = DIR == 0 ? a0 : l0, c1 = DIR == 0 ? l0 : (DIR == 1 ? a0 : fixed),
                   c2 = DIR == 2 ? a0 : fixed;
         tma_load_4d(sPr, &maps->rhs, c0, c1, c2, 0, tb->pf);
         if (need_u0) tma_load_4d(sP0, &maps->u0, c0, c1, c2, 0, tb->pf);
-        if (FINAL && PREC == HYDRO_MIXED) tma_load_4d(sP0 + 5 * NC, &maps->ust, c0, c1, c2, 0, tb->pf);
       }
     }
   } else if constexpr (PF::on) {
@@ -374,11 +370,6 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
 #pragma unroll
           for (int q = 0; q < 5; ++q) cp_async_ca<sizeof(Store)>(sP0 + q * NC + c, U0_in + q * N + o);
         }
-        if constexpr (PREC == HYDRO_MIXED) {
-#pragma unroll
-          for (int q = 0; q < 5; ++q) cp_async_ca<sizeof(Store)>(sP0 + (5 + q) * NC + c, U + q * N + o);
-        }
-
       }
     }
     cp_async_commit();
@@ -495,26 +486,13 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
         const unsigned o = offset(map_along(ga, n_along, a.periodic), gl < n_lane ? gl : n_lane - 1);
         Es = U[o]; Mxs = U[N + o]; Mys = U[2 * N + o]; Mzs = U[3 * N + o]; Rs = U[4 * N + o];
       }
-      if constexpr (PREC == HYDRO_MIXED) {
-        // the x and y sweeps have FP64-pipe time to spare (E^2 - |M|^2 is their only
-        // FP64 arithmetic) and convert in hardware; the z sweep's FP64 pipe also
-        // carries the stage combination, so it converts on the integer pipe
-        if constexpr (DIR == 2) {
-          E = d2f_rn(Es); Mx = d2f_rn(Mxs); My = d2f_rn(Mys); Mz = d2f_rn(Mzs); R = d2f_rn(Rs);
-        } else {
-          E = (float)Es; Mx = (float)Mxs; My = (float)Mys; Mz = (float)Mzs; R = (float)Rs;
-        }
-        cons_to_prim_mixed_f(Es, Mxs, Mys, Mzs, E, Mx, My, Mz, a.e_floor, e, vx, vy, vz, hit);
-      } else {
-        cons_to_prim_rho<Math>(Es, Mxs, Mys, Mzs, kconst<F>(a.e_floor, a.k.e_floor_f), e, vx, vy, vz, v2, rden, hit);
-        E = (F)Es; Mx = (F)Mxs; My = (F)Mys; Mz = (F)Mzs; R = (F)Rs;
-      }
+      cons_to_prim_rho<Math>(Es, Mxs, Mys, Mzs, kconst<F>(a.e_floor, a.k.e_floor_f), e, vx, vy, vz, v2, rden, hit);
+      E = (F)Es; Mx = (F)Mxs; My = (F)Mys; Mz = (F)Mzs; R = (F)Rs;
     }
     if (!cached) {
       p = e * F(1.0 / 3.0);
       vd = DIR == 0 ? vx : (DIR == 1 ? vy : vz);
-      if constexpr (PREC == HYDRO_MIXED) rho = spectral_radius<Math>(vd, vx * vx + vy * vy + vz * vz);
-      else rho = spectral_radius_r<Math>(vd, v2, rden);
+      rho = spectral_radius_r<Math>(vd, v2, rden);
     }
     const F Md = DIR == 0 ? Mx : (DIR == 1 ? My : Mz);
     const F Fh[5] = {F(0.5) * Md, F(0.5) * (Mx * vd + (DIR == 0 ? p : F(0))),
@@ -750,14 +728,6 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
             // last stage the increment goes back into the accumulator for the next x sweep.
             out = sP0[q * NC + c] + f2d(Lq[q]);
             if (!Uout) rhs[q * N + o] = Lq[q];
-          } else if constexpr (PREC == HYDRO_MIXED) {
-            // a U0 + b (u + dt L) = u + a (U0 - u) + b dt L (a + b = 1): the FP64
-            // state takes an FP32 increment, which carries the FP32 accuracy of L
-            // anyway; two FP64 additions per field instead of three operations
-            const double u = PF::on ? sP0[(5 + q) * NC + c] : U[q * N + o];
-            float inc = a.k.bdt_f * Lq[q];
-            if (!a.k.first) inc = fmaf(a.k.a_f, d2f_rn((PF::on ? sP0[q * NC + c] : U0[q * N + o]) - u), inc);
-            out = u + f2d(inc);
           } else {
             // the cell's own state is staged already
             const Store u = IL ? (Store)sUF[q * NCS + sidx(lane, j + G)].x : (Store)sU[q * NCS + sidx(lane, j + G)];
@@ -821,8 +791,8 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const SweepArgs a, cons
 
 // The FP32 and mixed-shadow z sweeps held to 40 registers (six blocks of 256
 // threads per SM); left alone they take 46-48 and five blocks.  The other sweeps
-// stay at or below 40 by themselves; FP64 and HYDRO_MIXED tiles are limited by
-// shared memory first.
+// stay at or below 40 by themselves; FP64 tiles are limited by shared memory
+// first.
 template <int PREC, int ORDER, bool TMA>
 __global__ void __launch_bounds__(kThreads, 6) sweep_kernel_z6(const SweepArgs a, const __grid_constant__ SweepMaps maps) {
   sweep_block<PREC, ORDER, 2, true, TMA>(a, maps);
@@ -1002,8 +972,8 @@ cudaError_t launch_sweep(int precision, int order, int dir, const SweepArgs& arg
     case HYDRO_FP64: return launch_order<HYDRO_FP64>(order, dir, a, s, tmap);
     case HYDRO_FP32: return launch_order<HYDRO_FP32>(order, dir, a, s, tmap);
     default:
-      if (a.S) return launch_order<kMixedShadow>(order, dir, a, s, tmap);   // shadow given: stage it
-      return launch_order<HYDRO_MIXED>(order, dir, a, s, tmap);
+      // mixed precision stages the shadows of its stage states
+      return a.S ? launch_order<kMixedShadow>(order, dir, a, s, tmap) : cudaErrorInvalidValue;
   }
 }
 
@@ -1071,7 +1041,9 @@ static bool encode_grid(EncodeTiled encode, int precision, void* const bufs[3], 
       if (precision != HYDRO_MIXED) {   // staging box of the stage state
         box_of(d, lanes[d], seg[d] + 8, box);
         if (!enc(&maps[st][d].stage, bufs[st], es, box)) return false;
-      } else if (shadows && d != 2) {   // staging box of the stage state's FP32 shadow (6 fields)
+      } else if (!shadows) {
+        return false;                  // mixed precision stages shadows only
+      } else if (d != 2) {             // staging box of the stage state's FP32 shadow (6 fields)
         box_of(d, lanes[d], seg[d] + 8, box);
         box[3] = 6;
         if (!enc(&maps[st][d].stage, shadows[st], 4, box)) return false;
@@ -1081,7 +1053,6 @@ static bool encode_grid(EncodeTiled encode, int precision, void* const bufs[3], 
         if (!enc(&maps[st][d].rhs, rhs, fs, box)) return false;
         if (d == 2) {
           if (!enc(&maps[st][d].u0, bufs[0], es, box)) return false;
-          if (precision == HYDRO_MIXED && !shadows && !enc(&maps[st][d].ust, bufs[st], es, box)) return false;
         }
       }
     }

@@ -205,9 +205,15 @@ def test_adjoint_workspace_size_covers_every_buffer(hy, dims, precision, every):
     size = hy.hydro_adjoint_workspace_size(c, steps, every)
     n = dims[0] * dims[1] * dims[2]
     f5 = -(-5 * n * 8 // 256) * 256
+    f6 = -(-6 * n * 4 // 256) * 256
     every = min(every, steps)
-    nbuf = -(-steps // every) + 2 * ((every + 1) + 2 * every + 1) + 5
-    lower = nbuf * f5 + (-(-7 * n * 4 // 256) * 256 + -(-5 * n * 4 // 256) * 256 if precision == "mixed" else 0)
+    if precision == "mixed":   # per set: step states, shadows of 3 stages per step (+1), accumulator
+        per_set = (every + 2) * f5 + (3 * every + 1) * f6
+        extra = -(-5 * n * 4 // 256) * 256
+    else:                      # per set: step states, 2 stage states per step, primitive cache, accumulator
+        per_set = (every + 1 + 2 * every + 2) * f5
+        extra = 0
+    lower = -(-steps // every) * f5 + 2 * per_set + 5 * f5 + extra
     assert lower <= size <= lower + 16384
     bad = hy.hydro_config_default(*dims, precision=precision)
     bad.workspace = 0x1000 + 64
