@@ -93,8 +93,9 @@ typedef struct {
                            leaves the step's results invalid. */
   int32_t test_withhold_copies; /* fault injection for tests: 1 = tiles arm their copy barriers
                            but issue no TMA copy, so every such wait runs out and the step
-                           returns HYDRO_ETIMEOUT (nothing is in flight when the tiles exit).
-                           0 in normal use. */
+                           (hydro_step, hydro_batch_step) returns HYDRO_ETIMEOUT (nothing is
+                           in flight when the tiles exit).  0 in normal use; the adjoint
+                           rejects 1, the allocation-free step issues no TMA copy. */
   int32_t reserved_;    /* zero */
 } hydro_config;
 

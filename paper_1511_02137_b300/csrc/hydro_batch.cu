@@ -30,10 +30,8 @@ constexpr int kJetChunk = 64;   // steps per captured graph
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 // nx, ny, nz of cfg are ignored (dims give the grids); the batched kernels are
-// compiled for WENO7 only, and they never withhold their copies.
-bool config_ok(const hydro_config* c) {
-  return config_valid(c, kCheckWorkspace) && c->weno_order == 7 && c->test_withhold_copies == 0;
-}
+// compiled for WENO7 only.
+bool config_ok(const hydro_config* c) { return config_valid(c, kCheckWorkspace) && c->weno_order == 7; }
 
 // Every grid within the single-grid index limit, and the ensemble within the
 // 32-bit cell offsets of the tile list.
@@ -215,6 +213,7 @@ BatchArgs base_args(hydro_batch* b) {
   a.e_floor = g.e_floor;
   a.eps = g.weno_eps;
   a.wait_ns = wait_limit_ns(g);
+  a.withhold = g.test_withhold_copies;
   a.src.rad = g.k_rad * g.cr_over_cf / (g.hbarc * g.hbarc);
   a.src.coll = g.k_coll * g.cr_over_cf / g.hbarc;
   a.src.t4coef = g.hbarc * g.hbarc * g.hbarc / (M_PI * M_PI / 30.0 * g.dof);

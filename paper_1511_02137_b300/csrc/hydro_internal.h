@@ -140,6 +140,7 @@ struct BatchArgs {
   double inv_dx, dt, a, b, e_floor, eps;
   int reduce_speed, count_floors;
   unsigned long long wait_ns;   // limit of each bounded wait on a TMA copy (0: kDefaultWaitNs)
+  int withhold;     // fault injection: arm the copy barriers but issue no TMA copy
   SourceCoef src;
   LaunchConst k;    // filled by launch_batch_sweep
   const SweepMaps* maps;   // [nev] tensor maps of this launch's stage and axis, or NULL (plain loads)

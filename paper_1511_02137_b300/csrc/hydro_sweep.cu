@@ -841,7 +841,7 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<PREC>()) batch_swee
     g.reduce_speed = b.reduce_speed;
     g.count_floors = b.count_floors;
     g.wait_ns = b.wait_ns;
-    g.withhold = 0;
+    g.withhold = b.withhold;
     g.src = b.src;
     g.k = b.k;
     const int t0 = blockIdx.x;

@@ -59,3 +59,47 @@ def test_withheld_copies_make_the_bounded_wait_run_out(hy, precision):
     R = hy.hydro_read_fields(ref, hy.HYDRO_CONSERVED)
     assert hy.hydro_get_diag(good)["status"] == 0
     assert np.all(norm_rel_err(G, R) <= (1e-12 if precision == "fp64" else 1e-5))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed"])
+def test_withheld_copies_make_the_batched_wait_run_out(hy, precision):
+    """The batched sweeps (one launch over the tiles of every grid, replayed from
+    a CUDA graph) wait on the same bounded barriers: with the copies withheld,
+    hydro_batch_step returns HYDRO_ETIMEOUT after a bounded time in both launch
+    forms (a persistent block stops at its first late tile), and a batch made
+    afterwards steps to the same state as hydro_step on each grid."""
+    from paper_1511_02137_b300 import workloads as W
+    dims = [(72, 72, 72), (64, 72, 40)]
+    ws = [replace(W.ELLIPSOIDAL_32, n=d, sigma=(1.5, 1.5, 1.5), jets=()) for d in dims]
+    prims = [np.ascontiguousarray(W.ellipsoidal_primitives(w)).ravel() for w in ws]
+
+    def batch(**over):
+        w = ws[0]
+        cfg = hy.hydro_config_default(*dims[0], precision=precision, dx=w.dx, dt=w.dt, t0=w.t0, **over)
+        b = hy.hydro_batch_create(cfg, dims)
+        for e, p in enumerate(prims):
+            hy.hydro_batch_set_initial(b, e, hy.HYDRO_PRIMITIVE, p)
+        return b
+
+    for per_tile in (1, 0):
+        b = batch(wait_limit_s=1e-3, test_withhold_copies=1)
+        hy.hydro_batch_set_launch(b, (per_tile,) * 3)
+        t0 = time.perf_counter()
+        assert hy.hydro_batch_step(b, 1, allow=(hy.HYDRO_ETIMEOUT,)) == hy.HYDRO_ETIMEOUT
+        took = time.perf_counter() - t0
+        statuses = [hy.hydro_batch_get_diag(b, e)["status"] for e in range(len(dims))]
+        print(f"{precision}, {'one block per tile' if per_tile else 'persistent'}: HYDRO_ETIMEOUT after "
+              f"{took * 1e3:.1f} ms, statuses {statuses}")
+        assert hy.HYDRO_ETIMEOUT in statuses and set(statuses) <= {0, hy.HYDRO_ETIMEOUT}
+        assert took < 5.0
+        hy.hydro_batch_destroy(b)
+    # the CUDA context is intact: a batch without the fault equals each grid stepped alone
+    b = batch()
+    hy.hydro_batch_step(b, 2)
+    for e, w in enumerate(ws):
+        ctx = gpu_context(hy, w, precision)
+        hy.hydro_step(ctx, 2)
+        assert np.array_equal(hy.hydro_batch_read_fields(b, e), hy.hydro_read_fields(ctx, hy.HYDRO_CONSERVED))
+        assert hy.hydro_batch_get_diag(b, e)["status"] == 0
+        hy.hydro_destroy(ctx)
+    hy.hydro_batch_destroy(b)
