@@ -806,16 +806,22 @@ cudaError_t vjp(hydro_adjoint* a, int64_t n, int st, const double* Uk, const flo
 
 // Reverse of the stage combination of stage st; the reverse sweep that follows
 // is stage st - 1 of the same step, or stage 3 of the previous step.
+// The charge density R is passive (it feeds no other field) and the cone energy
+// does not depend on it, so its adjoint stays exactly zero: the stage
+// combinations carry the four fields E, M^x, M^y, M^z, and the R fields of the
+// adjoint arrays are zeroed once per backward.
+constexpr int kAdjFields = 4;
+
 cudaError_t combine(hydro_adjoint* a, int mode, int st) {
-  const size_t n5 = 5 * a->n;
+  const size_t nf = kAdjFields * a->n;
   const double fscale = kB[st == 0 ? 2 : st - 1] * a->cfg.dt;
   if (a->cfg.precision == HYDRO_MIXED)
-    adj_combine_kernel<float><<<grid_1d(n5), 256, 0, a->stream>>>(
-        mode, kA[st], kB[st], a->lamA, a->lamB, a->lam0, reinterpret_cast<const float*>(a->r), n5, a->lamf,
+    adj_combine_kernel<float><<<grid_1d(nf), 256, 0, a->stream>>>(
+        mode, kA[st], kB[st], a->lamA, a->lamB, a->lam0, reinterpret_cast<const float*>(a->r), nf, a->lamf,
         (float)fscale);
   else
-    adj_combine_kernel<double><<<grid_1d(n5), 256, 0, a->stream>>>(mode, kA[st], kB[st], a->lamA, a->lamB, a->lam0,
-                                                                   a->r, n5, nullptr, 0.0f);
+    adj_combine_kernel<double><<<grid_1d(nf), 256, 0, a->stream>>>(mode, kA[st], kB[st], a->lamA, a->lamB, a->lam0,
+                                                                   a->r, nf, nullptr, 0.0f);
   return cudaGetLastError();
 }
 
@@ -1012,6 +1018,10 @@ hydro_status hydro_adjoint_backward(hydro_adjoint* a, double dJ, double* grad_k_
   if (!a || !d_grad_e) return HYDRO_EINVAL;
   if (!a->forward_done) return HYDRO_ESTATE;
   cudaError_t err = cudaMemsetAsync(a->kbar, 0, 2 * kMaxJets * sizeof(double), a->stream);
+  // the fields past the combinations' kAdjFields stay zero (the seed zeroes lamA's)
+  for (double* l : {a->lamB, a->lam0})
+    if (err == cudaSuccess)
+      err = cudaMemsetAsync(l + kAdjFields * a->n, 0, (5 - kAdjFields) * a->n * sizeof(double), a->stream);
   if (err == cudaSuccess) {
     cone_seed_kernel<<<grid_1d(a->n), 256, 0, a->stream>>>(a->lamA, a->cone, dJ);
     err = cudaGetLastError();
