@@ -194,7 +194,8 @@ hydro_status hydro_profile_query(hydro_ctx* ctx, int32_t kind, double* total_ms,
 
 /* ---------------------------------------------------------------------------
  * Batched ensembles: nevents grids of uneven sizes advanced together (the
- * ensemble form of the same step; BASELINE's batched configuration).  All
+ * ensemble form of the same step, for many events with their own profiles and
+ * jet paths; the paper has no counterpart).  All
  * grids share the configuration (precision, boundary, dx, dt, t0, Eq. 3
  * constants, WENO7 only); nx/ny/nz of cfg are ignored, dims[3*e .. 3*e+2] give
  * grid e.  Each sweep of each RK3 stage is one launch over the tiles of all
