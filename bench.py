@@ -74,7 +74,7 @@ PEAK_FP32_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 PEAK_FP64_TFLOPS = PEAK_FP32_TFLOPS / 64
 
 # The paper's own performance statement, quoted as context (no number for this metric).
-PAPER_CONTEXT = "paper (Sec. 1): GPU more than two orders of magnitude faster than CPU; hardware not named"
+PAPER_CONTEXT = "paper (Sec. 1): its CUDA code ran over 100x faster than the same computation on a CPU; neither GPU nor CPU is named"
 
 
 def _peaks():
