@@ -226,12 +226,18 @@ struct Prefetch {
 // Single-grid WENO7 sweeps stage interior tiles with one TMA copy.  FP64 copies
 // straight into the tile's U array; FP32 tiles interleave U with F_d/2, so their
 // copy lands in a separate staging box that phase 1 reads; the mixed shadow's x
-// and y sweeps copy the shadow the same way (its z tile keeps plain loads: the
-// staging box would cost it a resident block per SM).
+// and y sweeps copy the shadow the same way.  The mixed z tile, which also holds
+// U0 in FP64, would lose a resident block per SM to a separate box: its box lands
+// on the (U, F_d/2) area instead, which phase 1 fills only after every thread has
+// read its staged cells into registers (see kBoxAliased).
 template <int PREC, int DIR = 0>
 __host__ __device__ constexpr bool tma_staged() {
-  return PREC == kMixedShadow ? DIR != 2 : true;
+  return true;
 }
+
+// The staging box of this tile shares the start of the (U, F_d/2) area.
+template <int PREC, int DIR>
+constexpr bool kBoxAliased = PREC == kMixedShadow && DIR == 2;
 
 // Shared memory of one tile, in units of the flux type (word offsets): U, F_d/2
 // (5 fields each) and rho_d per staged cell, 5 numerical fluxes per interface,
@@ -252,6 +258,7 @@ struct TileLayout {
   static constexpr int body = delta + ((sizeof(F) == 8 && ORDER == 7) ? 10 * NCS : 0);
   static constexpr int stage = up(body);
   __host__ __device__ static constexpr int words(bool stage_box) {
+    if (kBoxAliased<PREC, DIR>) return body;
     return (stage_box && sizeof(F) == 4) ? stage + kStagedFields<PREC> * NCS : body;
   }
 };
@@ -396,7 +403,8 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   // a tile whose halo lies inside the grid needs no ghost cells: one TMA box of all
   // 5 fields (6 shadow fields for kMixedShadow)
   bool staged = false;
-  F* sStage = IL ? reinterpret_cast<F*>(smem_raw) + TL::stage : sU;   // [5 or 6][NCS] as copied
+  F* sStage = kBoxAliased<PREC, DIR> ? reinterpret_cast<F*>(smem_raw)   // [5 or 6][NCS] as copied
+                                      : (IL ? reinterpret_cast<F*>(smem_raw) + TL::stage : sU);
   constexpr int NSF = kStagedFields<PREC>;
   if constexpr (TMA && tma_staged<PREC, DIR>()) {
     static_assert(PREC == kMixedShadow || sizeof(Store) == sizeof(F),
@@ -429,7 +437,28 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   constexpr bool CACHE = PREC == HYDRO_FP64;
   F* __restrict__ Pc = CACHE ? static_cast<F*>(a.P) : nullptr;
   const bool cached = CACHE && DIR != 0 && Pc != nullptr;
-  for (int c = threadIdx.x; c < NCS; c += kThreads) {
+  // a thread's staged cells c = threadIdx.x + r kThreads, r < NR; an aliased box is
+  // read into registers before the barrier after which phase 1 overwrites it
+  constexpr int NR = (NCS + kThreads - 1) / kThreads;
+  constexpr bool ALIAS = kBoxAliased<PREC, DIR>;
+  float box[ALIAS ? NR : 1][6];
+  if constexpr (ALIAS) {
+    if (staged) {
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        const int c = threadIdx.x + r * kThreads;
+        if (c < NCS) {
+#pragma unroll
+          for (int f = 0; f < 6; ++f) box[r][f] = sStage[f * NCS + c];
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    const int c = threadIdx.x + r * kThreads;
+    if (c >= NCS) break;
     int lane, s;
     if (DIR == 0) { lane = c / W; s = c - lane * W; }
     else { s = c / LANES; lane = c - s * LANES; }
@@ -442,7 +471,9 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
     if constexpr (PREC == kMixedShadow) {
       // the shadow written with the state: FP32 values and om, no FP64 work here
       float om;
-      if (staged) {
+      if (ALIAS && staged) {
+        E = box[r][0]; Mx = box[r][1]; My = box[r][2]; Mz = box[r][3]; R = box[r][4]; om = box[r][5];
+      } else if (staged) {
         E = sStage[c]; Mx = sStage[NCS + c]; My = sStage[2 * NCS + c]; Mz = sStage[3 * NCS + c];
         R = sStage[4 * NCS + c]; om = sStage[5 * NCS + c];
       } else {
@@ -1043,7 +1074,7 @@ static bool encode_grid(EncodeTiled encode, int precision, void* const bufs[3], 
         if (!enc(&maps[st][d].stage, bufs[st], es, box)) return false;
       } else if (!shadows) {
         return false;                  // mixed precision stages shadows only
-      } else if (d != 2) {             // staging box of the stage state's FP32 shadow (6 fields)
+      } else {                         // staging box of the stage state's FP32 shadow (6 fields)
         box_of(d, lanes[d], seg[d] + 8, box);
         box[3] = 6;
         if (!enc(&maps[st][d].stage, shadows[st], 4, box)) return false;
