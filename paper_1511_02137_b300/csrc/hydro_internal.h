@@ -48,7 +48,7 @@ struct LaunchConst {
   double eps_s;     // WENO epsilon in the scaled indicator form of the order in use
   float eps_s_f;    // the same rounded to FP32
   float inv_dx_f, dt_f, a_f, b_f, e_floor_f;
-  float bdt_f;      // b dt (mixed-precision stage increment)
+  float bdt_dx_f;   // b dt / dx (mixed precision: a flux difference's share of the stage increment)
   int first;        // a == 0: the stage result is U + dt L
 };
 

@@ -679,15 +679,17 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
       const unsigned o = offset(ga, gl);
       const int h0 = hidx(lane, j), h1 = hidx(lane, j + 1);
       F L[5];
-#pragma unroll
-      for (int q = 0; q < 5; ++q) L[q] = -(sH[q * NIF + h1] - sH[q * NIF + h0]) * inv_dx;
       if constexpr (SH) {
-        // the mixed shadow accumulates the stage increment b dt L (x: on top of b delta_k)
+        // the mixed shadow accumulates the stage increment b dt L (x: on top of b delta_k),
+        // one product with b dt / dx per flux difference
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
-          L[q] *= a.k.bdt_f;
+          L[q] = (sH[q * NIF + h0] - sH[q * NIF + h1]) * a.k.bdt_dx_f;
           if (DIR == 0 && !a.k.first) L[q] = fmaf(a.k.b_f, PF::on ? sPr[q * NC + c] : rhs[q * N + o], L[q]);
         }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) L[q] = -(sH[q * NIF + h1] - sH[q * NIF + h0]) * inv_dx;
       }
       if (!FINAL) {
         if constexpr (TST && DIR == 0) {
@@ -989,7 +991,7 @@ LaunchConst derive_constants(const GridArgs& g, int order) {
   k.a_f = (float)g.a;
   k.b_f = (float)g.b;
   k.e_floor_f = (float)g.e_floor;
-  k.bdt_f = (float)(g.b * g.dt);
+  k.bdt_dx_f = (float)(g.b * g.dt * g.inv_dx);
   k.first = g.a == 0.0;
   return k;
 }
