@@ -113,3 +113,19 @@ def test_err_per_field_is_norm_relative():
     a[2, 1, 1, 1] += 1e-6
     e = bench._err_per_field(a, b)
     assert e[2] == 1e-6 and e[0] == e[1] == e[3] == e[4] == 0.0
+
+
+def test_cpu_baseline_reports_the_all_core_run_and_the_labelled_single_core_extrapolation():
+    """The oracle baseline on a small grid: both runs report their rate, cores
+    and sample; the single-core entry extrapolates its per-cell rate to the
+    workload's steps and says that the full run was not made."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1511_02137_b300 import workloads as W
+    w = W.scaled(W.ELLIPSOIDAL_256, 24, steps=70)
+    out = bench._cpu_baseline(w, single_core_grid=16)
+    assert out["kind"] == "oracle" and out["cores"] >= 1 and out["value"] > 0
+    one = out["single_core"]
+    assert one["cores"] == 1 and one["value"] > 0 and "16^3" in one["sample"]
+    assert abs(one["full_run_s_extrapolated"] - w.cells * w.steps / one["value"]) <= 0.06
+    assert "extrapolated" in one["full_run"] and "not run" in one["full_run"]
