@@ -653,7 +653,9 @@ struct hydro_adjoint {
   AdjSet set[2];
   cudaStream_t side = nullptr;
   cudaEvent_t ev_ready[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr}, ev_start = nullptr;
-  double *lamA = nullptr, *lamB = nullptr, *lam0 = nullptr, *r = nullptr, *prim = nullptr;
+  double *lamA = nullptr, *lamB = nullptr, *lam0 = nullptr;   // adjoint states (roles rotate per step)
+  double* r = nullptr;           // J_L^T a of the stage under reverse, in the flux type
+  double* prim = nullptr;        // the forward's initial primitives (for dJ/de)
   float* lamf = nullptr;         // mixed: FP32 scaled adjoint input of the next reverse sweep [5][n]
   double* kbar = nullptr;        // [2]
   double* partial = nullptr;     // cone partial sums
