@@ -413,7 +413,8 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
       unsigned own = (mask >> (7 - k)) & 1u;
       if (gcell == 0) own += __popc(mask & ((1u << (7 - k)) - 1u));
       if (gcell == n_along - 1) own += __popc(mask >> (8 - k));
-      if (own) rhob += P(0.5) * (P)own * sAhb[x] / (P)__popc(mask);
+      // the equal share: one reciprocal of the tie count (1..8; exact for 1, 2, 4, 8)
+      if (own) rhob += P(0.5) * (P)own * sAhb[x] * Math::rcp((P)__popc(mask));
     }
     const int sc = sidx(lane, j + 8);
     const unsigned o = offset(gcell, gl);
