@@ -87,7 +87,16 @@ struct C2PTape {
 __device__ __forceinline__ void cons_to_prim_tape(double E, double Mx, double My, double Mz, double e_floor,
                                                   C2PTape<double>& t, double& e, double& vx, double& vy,
                                                   double& vz) {
-  const double Mabs = sqrt(Mx * Mx + My * My + Mz * Mz);
+  // |M| and 1/|M| from one Newton-Raphson reciprocal square root where |M|^2 is a
+  // normal double (always, for |M| above 1.5e-154), IEEE operations below that
+  const double M2 = Mx * Mx + My * My + Mz * Mz;
+  double Mabs = 0.0, im = 0.0;
+  if (M2 >= 2.2250738585072014e-308) {
+    sqrt_rsqrt_nr(M2, Mabs, im);
+  } else if (M2 > 0.0) {
+    Mabs = sqrt(M2);
+    im = 1.0 / Mabs;
+  }
   double Ee = E;
   t.floored = !(Ee >= e_floor);
   if (t.floored) Ee = e_floor;
@@ -100,7 +109,8 @@ __device__ __forceinline__ void cons_to_prim_tape(double E, double Mx, double My
     m_over_M = m / Mabs;
   }
   t.m = m;
-  t.s = sqrt(4.0 - 3.0 * m * m);
+  double ys;
+  sqrt_rsqrt_nr(4.0 - 3.0 * m * m, t.s, ys);   // the argument lies in [1, 4]
   t.r = rcp_nr(2.0 + t.s);
   t.v = 3.0 * m * t.r;
   e = Ee * (1.0 - m * t.v);
@@ -108,13 +118,9 @@ __device__ __forceinline__ void cons_to_prim_tape(double E, double Mx, double My
   vx = Mx * t.vs;
   vy = My * t.vs;
   vz = Mz * t.vs;
-  t.nx = t.ny = t.nz = 0.0;
-  if (Mabs > 0.0) {
-    const double im = 1.0 / Mabs;
-    t.nx = Mx * im;
-    t.ny = My * im;
-    t.nz = Mz * im;
-  }
+  t.nx = Mx * im;   // (0 for M = 0)
+  t.ny = My * im;
+  t.nz = Mz * im;
 }
 
 // Mixed recovery from the floored E and om (the arithmetic of cons_to_prim_om)
