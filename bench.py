@@ -54,6 +54,12 @@ FLOP_PER_CELL = {"sweep_x": FLOP_PER_INTERFACE + 10 + 23 + 5 + 14 + 10,
                  "sweep_y": FLOP_PER_INTERFACE + 15 + 14 + 10,
                  "sweep_z": FLOP_PER_INTERFACE + 15 + 14 + 10 + 20}
 FLOP_PER_CELL_STEP = 3 * sum(FLOP_PER_CELL.values())
+# The same count for the WENO5 variant: the split over 5 cells per side (5 x 10
+# FMAs + alpha/2 = 101), 10 WENO5 reconstructions of 64 (candidates 15, second
+# differences 9, first-derivative terms 12, beta 9, weights 18 and one division)
+# and the 5 flux sums, 746 per interface; the per-cell terms as for WENO7.
+FLOP_PER_INTERFACE_W5 = 101 + 10 * 64 + 5
+FLOP_PER_CELL_W5 = {k: v - FLOP_PER_INTERFACE + FLOP_PER_INTERFACE_W5 for k, v in FLOP_PER_CELL.items()}
 # Algorithmic HBM bytes per cell per step: 40 field accesses (stage 1 reads 5 and
 # writes 5; stages 2 and 3 read 10 and write 5) in storage precision.
 FIELD_ACCESSES_PER_CELL_STEP = 40
@@ -227,8 +233,8 @@ def _workload():
     return W.scaled(W.ELLIPSOIDAL_256, _GRID)
 
 
-def _make_ctx(hy, w, precision, prim_host):
-    cfg = hy.hydro_config_default(*w.n, precision=precision, dx=w.dx, dt=w.dt, t0=w.t0)
+def _make_ctx(hy, w, precision, prim_host, order=7):
+    cfg = hy.hydro_config_default(*w.n, precision=precision, dx=w.dx, dt=w.dt, t0=w.t0, weno_order=order)
     ctx = hy.hydro_create(cfg)
     hy.hydro_set_initial(ctx, hy.HYDRO_PRIMITIVE, prim_host)
     for j in w.jets:
@@ -263,14 +269,15 @@ def _time_device(hy, ctx, steps, warmup, ws, sampler_bus=None):
     return sec, prof, clk.summary()
 
 
-def _roofline(prof, cells, precision, peaks=None):
+def _roofline(prof, cells, precision, peaks=None, order=7):
     """Roofline of the dominant sweep: algorithmic FLOPs per launch over its mean
     CUDA-event launch time, against the measured FMA peak of the flux type (FP64
-    for the FP64 path, FP32 for FP32 and mixed)."""
+    for the FP64 path, FP32 for FP32 and mixed).  DRAM traffic from the ncu table
+    (WENO7 only)."""
     dom = max(prof, key=lambda k: prof[k]["ms"])
     p = prof[dom]
     avg_s = p["ms"] / 1e3 / max(p["launches"], 1)
-    flop = cells * FLOP_PER_CELL[dom]
+    flop = cells * (FLOP_PER_CELL if order == 7 else FLOP_PER_CELL_W5)[dom]
     achieved = flop / avg_s / 1e12
     key = "fp64_tflops" if precision == "fp64" else "fp32_tflops"
     if peaks and peaks.get(key):
@@ -283,7 +290,7 @@ def _roofline(prof, cells, precision, peaks=None):
     return {"bound": "alu", "kernel": dom, "achieved": round(achieved, 4), "peak": round(peak, 3),
             "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
             "traffic": (TRAFFIC_B_PER_CELL[(precision, dom)] * cells
-                        if TRAFFIC_B_PER_CELL.get((precision, dom)) is not None else None),
+                        if order == 7 and TRAFFIC_B_PER_CELL.get((precision, dom)) is not None else None),
             "peak_source": source, "flop_per_launch": flop, "avg_launch_ms": round(avg_s * 1e3, 4),
             "share": {k: round(v["ms"] / total_ms, 4) for k, v in prof.items()}}
 
@@ -488,6 +495,27 @@ def _adjoint(hy, grid=128, steps=50):
     return out
 
 
+def _weno5(hy, w, prim, args, ws, bus, peaks):
+    """The WENO5 variant of the step on the headline workload, each precision of
+    the run: W warm-up steps, then K steps (FP64) or max(K, 100) (FP32, mixed),
+    CUDA events on the library stream, the dominant sweep against the measured
+    FMA peak with the WENO5 FLOP count."""
+    res = {}
+    for prec in args.precisions:
+        steps = args.steps if prec == "fp64" else max(args.steps, 100)
+        ctx = _make_ctx(hy, w, prec, prim, order=5)
+        sec, prof, clk = _time_device(hy, ctx, steps, args.warmup, ws, bus)
+        sec = _max_over_ranks(sec, ws)
+        hy.hydro_destroy(ctx)
+        roof = _roofline(prof, w.cells, prec, peaks, order=5)
+        res[prec] = {"value": w.cells * steps * ws / sec, "ms_per_step": round(sec * 1e3 / steps, 4), "steps": steps,
+                     "roofline": {k: roof[k] for k in ("kernel", "achieved", "peak", "frac", "avg_launch_ms",
+                                                       "share")},
+                     "flop_per_cell_step": 3 * sum(FLOP_PER_CELL_W5.values()), "clocks": clk}
+    res["config"] = f"{w.name}, weno_order 5, same workload and timing as the WENO7 lines"
+    return res
+
+
 def _variant(hy, W, prec, args, ws, bus, peaks, ref_final, pinned=None):
     """One reduced-precision variant on the mixed-precision configuration (256^3,
     3 seeded jets): its error per field against the FP64 path after the 70
@@ -576,6 +604,8 @@ def run_cuda(args, rank, ws):
         out["adjoint"] = _adjoint(hy, args.adjoint_grid, args.adjoint_steps)
     if not args.no_batched:
         out["batched"] = _batched(hy, args.steps, args.warmup, peaks)
+    if not args.no_weno5:
+        out["weno5"] = _weno5(hy, w, prim_pinned, args, ws, bus, peaks)
     # reduced precisions last: their error against the FP64 path on the
     # mixed-precision configuration, their own timing and roofline
     variants = {}
@@ -641,6 +671,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-event batched ensemble measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the 128^3 adjoint timing")
+    ap.add_argument("--no-weno5", action="store_true", help="skip the WENO5 variant timing")
     ap.add_argument("--no-peaks", action="store_true", help="skip the ALU peak measurement (derived peaks instead)")
     ap.add_argument("--no-variant-error", action="store_true",
                     help="skip the 70-step FP64 reference run behind the variants' error columns")

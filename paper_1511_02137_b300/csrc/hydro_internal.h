@@ -188,7 +188,7 @@ cudaError_t launch_sweep(int precision, int order, int dir, const SweepArgs& a, 
 
 // Tensor maps for the three RK stages and the three sweep axes (maps[stage][axis]);
 // bufs[st] is the state stage st evaluates its right-hand side on (bufs[0] is also
-// the step state U0), rhs the accumulator.  WENO7 only.  Returns false (and leaves
+// the step state U0), rhs the accumulator.  WENO7 and WENO5.  Returns false (and leaves
 // maps unusable) when the grid does not meet the TMA layout rules (row pitch a
 // multiple of 16 bytes) or the driver entry point is missing; callers then use
 // plain loads.

@@ -503,7 +503,7 @@ __device__ __forceinline__ double weno5_combine(double Q0, double Q1, double Q2,
   s1 *= s1;
   s2 *= s2;
   const double t0 = s1 * s2, t1 = s0 * s2, t2 = s0 * s1;
-  return (t0 * Q0 + t1 * Q1 + t2 * Q2) / (t0 + 6.0 * t1 + 3.0 * t2);
+  return (t0 * Q0 + t1 * Q1 + t2 * Q2) * rcp_nr(t0 + 6.0 * t1 + 3.0 * t2);
 }
 
 __device__ __forceinline__ float weno5_combine(float Q0, float Q1, float Q2, float b0, float b1, float b2, float eps) {

@@ -235,6 +235,16 @@ __host__ __device__ constexpr bool tma_staged() {
   return true;
 }
 
+// Whether a tile of this sweep stages by TMA.  A box must start at an innermost
+// (x) coordinate whose byte offset is a multiple of 16: the x sweep's box starts at
+// a0 - G, aligned for WENO7 (G = 4, a0 a multiple of the segment) but not for
+// WENO5 (G = 3), whose x tiles therefore stage through plain loads; the y and z
+// boxes start at the lane origin l0, a multiple of LANES.
+template <int PREC, int ORDER, int DIR>
+__host__ __device__ constexpr bool stage_by_tma() {
+  return tma_staged<PREC, DIR>() && (ORDER == 7 || DIR != 0);
+}
+
 // The staging box of this tile shares the start of the (U, F_d/2) area.
 template <int PREC, int DIR>
 constexpr bool kBoxAliased = PREC == kMixedShadow && DIR == 2;
@@ -406,7 +416,7 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   F* sStage = kBoxAliased<PREC, DIR> ? reinterpret_cast<F*>(smem_raw)   // [5 or 6][NCS] as copied
                                       : (IL ? reinterpret_cast<F*>(smem_raw) + TL::stage : sU);
   constexpr int NSF = kStagedFields<PREC>;
-  if constexpr (TMA && tma_staged<PREC, DIR>()) {
+  if constexpr (TMA && stage_by_tma<PREC, ORDER, DIR>()) {
     static_assert(PREC == kMixedShadow || sizeof(Store) == sizeof(F),
                   "TMA staging copies the stored type into the flux-type tile");
     if (a0 - G >= 0 && a0 + SEG + G <= n_along && l0 + LANES <= n_lane) {
@@ -652,7 +662,7 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
   // area (free once phase 2 is done), the y sweep into the prefetched accumulator.
   // (The z sweep keeps per-thread stores of the stage result: a TMA store there
   // measured slower, 0.546 vs 0.534 ms per FP32 launch at 256^3.)
-  constexpr bool TST = TMA && IL && ORDER == 7 && !FINAL;
+  constexpr bool TST = TMA && IL && !FINAL;
   F* sOut = reinterpret_cast<F*>(smem_raw);   // [5][NC] (x sweep)
   F* __restrict__ rhs = static_cast<F*>(a.rhs);
   const F inv_dx = kconst<F>(a.inv_dx, a.k.inv_dx_f);
@@ -943,8 +953,8 @@ static cudaError_t launch_one(const SweepArgs& a, cudaStream_t s, const SweepMap
   constexpr int SEG = Tile<PREC, DIR>::SEG, LANES = Tile<PREC, DIR>::LANES;
   // tensor maps serve the staging copy (FP64, FP32, the mixed shadow's x and y
   // sweeps), and the phase-3 operands and results of FP32-flux tiles (FP32, mixed)
-  constexpr bool kStage = ORDER == 7 && tma_staged<PREC, DIR>();
-  constexpr bool kMapsUsed = kStage || (ORDER == 7 && sizeof(F) == 4);
+  constexpr bool kStage = stage_by_tma<PREC, ORDER, DIR>();
+  constexpr bool kMapsUsed = kStage || sizeof(F) == 4;
   constexpr size_t smem = sizeof(F) * (size_t)tile_smem_words<PREC, ORDER, DIR, SEG, LANES>();
   constexpr size_t smem_tma = sizeof(F) * (size_t)tile_smem_words<PREC, ORDER, DIR, SEG, LANES, kStage>();
   dim3 grid;
@@ -1043,9 +1053,12 @@ static EncodeTiled encode_entry() {
 
 // The maps of one grid for the three stages and axes, with tile shapes seg[d] x lanes[d];
 // shadows (mixed precision, may be NULL) give the staging boxes of the FP32 shadows.
+// order: the WENO order, whose halo of G = (order + 1) / 2 cells on each side sets
+// the staging boxes (none for the x sweep of WENO5, see stage_by_tma).
 static bool encode_grid(EncodeTiled encode, int precision, void* const bufs[3], void* rhs, int nx, int ny, int nz,
                         const int seg[3], const int lanes[3], SweepMaps maps[3][3],
-                        void* const shadows[3] = nullptr) {
+                        void* const shadows[3] = nullptr, int order = 7) {
+  const int halo2 = order + 1;   // staged cells beyond a tile's segment
   const size_t es = precision == HYDRO_FP32 ? 4 : 8;   // stored type
   const size_t fs = precision == HYDRO_FP64 ? 8 : 4;   // flux type
   // a 4-D (x, y, z, field) map of one array of box[3] fields with elements of `size` bytes
@@ -1071,13 +1084,14 @@ static bool encode_grid(EncodeTiled encode, int precision, void* const bufs[3], 
   for (int st = 0; st < 3; ++st)
     for (int d = 0; d < 3; ++d) {
       cuuint32_t box[4];
-      if (precision != HYDRO_MIXED) {   // staging box of the stage state
-        box_of(d, lanes[d], seg[d] + 8, box);
-        if (!enc(&maps[st][d].stage, bufs[st], es, box)) return false;
-      } else if (!shadows) {
+      const bool staged = order == 7 || d != 0;
+      if (precision == HYDRO_MIXED && !shadows) {
         return false;                  // mixed precision stages shadows only
-      } else {                         // staging box of the stage state's FP32 shadow (6 fields)
-        box_of(d, lanes[d], seg[d] + 8, box);
+      } else if (precision != HYDRO_MIXED && staged) {   // staging box of the stage state
+        box_of(d, lanes[d], seg[d] + halo2, box);
+        if (!enc(&maps[st][d].stage, bufs[st], es, box)) return false;
+      } else if (staged) {             // staging box of the stage state's FP32 shadow (6 fields)
+        box_of(d, lanes[d], seg[d] + halo2, box);
         box[3] = 6;
         if (!enc(&maps[st][d].stage, shadows[st], 4, box)) return false;
       }
@@ -1094,12 +1108,12 @@ static bool encode_grid(EncodeTiled encode, int precision, void* const bufs[3], 
 
 bool encode_sweep_tmaps(int precision, int order, void* const bufs[3], void* rhs, int nx, int ny, int nz,
                         SweepMaps maps[3][3], void* const shadows[3]) {
-  if (order != 7) return false;
+  if (order != 7 && order != 5) return false;
   EncodeTiled encode = encode_entry();
   if (!encode) return false;
   int seg[3], lanes[3];
   for (int d = 0; d < 3; ++d) tile_shape(precision, d, seg[d], lanes[d]);
-  return encode_grid(encode, precision, bufs, rhs, nx, ny, nz, seg, lanes, maps, shadows);
+  return encode_grid(encode, precision, bufs, rhs, nx, ny, nz, seg, lanes, maps, shadows, order);
 }
 
 bool encode_batch_tmaps(int precision, void* const bufs[3], void* rhs, int nev, const int32_t* dims,

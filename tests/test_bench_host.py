@@ -101,6 +101,12 @@ def test_algorithmic_counts_and_traffic_table():
             "sweep_z": {"ms": 2.0, "launches": 1}}
     t = bench.TRAFFIC_B_PER_CELL[("fp64", "sweep_z")]
     assert bench._roofline(prof, 8, "fp64")["traffic"] == (None if t is None else t * 8)
+    # WENO5: 64 per reconstruction, 746 per interface, the same per-cell terms;
+    # no DRAM table for it
+    assert bench.FLOP_PER_INTERFACE_W5 == 746
+    assert bench.FLOP_PER_CELL_W5 == {"sweep_x": 808, "sweep_y": 785, "sweep_z": 805}
+    r5 = bench._roofline(prof, 8, "fp64", order=5)
+    assert r5["flop_per_launch"] == 8 * 805 and r5["traffic"] is None
 
 
 def test_err_per_field_is_norm_relative():
