@@ -533,6 +533,32 @@ __device__ __forceinline__ F weno5(F f0, F f1, F f2, F f3, F f4, F eps_s) {
   return weno5_combine(Q0, Q1, Q2, d0 * d0 + g0 * g0, d1 * d1 + g1 * g1, d2 * d2 + g2 * g2, eps_s);
 }
 
+// weno5 for FP32 in the two lanes of packed FP32x2 instructions (the left-biased
+// reconstruction of an interface in x, the mirrored one in y), the same terms and
+// weights as the scalar form.
+__device__ __forceinline__ float2 weno5_pair(float2 f0, float2 f1, float2 f2, float2 f3, float2 f4, float eps_s) {
+  const float g = (float)kW5G;
+  const float2 Q0 = fma2(bc2((float)(11.0 / 6.0)), f2, fma2(bc2((float)(-7.0 / 6.0)), f1,
+                                                              mul2(bc2((float)(2.0 / 6.0)), f0)));
+  const float2 Q1 = fma2(bc2(2.0f), f3, fma2(bc2(5.0f), f2, mul2(bc2(-1.0f), f1)));
+  const float2 Q2 = fma2(bc2(-0.5f), f4, fma2(bc2(2.5f), f3, f2));
+  const float2 d0 = add2(fma2(bc2(-2.0f), f1, f0), f2), d1 = add2(fma2(bc2(-2.0f), f2, f1), f3),
+               d2 = add2(fma2(bc2(-2.0f), f3, f2), f4);
+  const float2 g0 = fma2(bc2(3.0f * g), f2, fma2(bc2(-4.0f * g), f1, mul2(bc2(g), f0)));
+  const float2 g1 = mul2(bc2(g), sub2(f1, f3));
+  const float2 g2 = fma2(bc2(g), f4, fma2(bc2(-4.0f * g), f3, mul2(bc2(3.0f * g), f2)));
+  const float2 e = bc2(eps_s);
+  float2 t0 = rcp2(add2(e, fma2(d0, d0, mul2(g0, g0))));
+  float2 t1 = rcp2(add2(e, fma2(d1, d1, mul2(g1, g1))));
+  float2 t2 = rcp2(add2(e, fma2(d2, d2, mul2(g2, g2))));
+  t0 = mul2(t0, t0);
+  t1 = mul2(t1, t1);
+  t2 = mul2(t2, t2);
+  const float2 num = fma2(t2, Q2, fma2(t1, Q1, mul2(t0, Q0)));
+  const float2 den = fma2(bc2(3.0f), t2, fma2(bc2(6.0f), t1, t0));
+  return mul2(num, rcp2(den));
+}
+
 // Temperature from e = (pi^2/30) dof T^4 / (hbar c)^3: T = (e t4coef)^(1/4).
 __device__ __forceinline__ double temperature(double e, double t4coef) {
   double x = e * t4coef;

@@ -630,6 +630,13 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
           dm[k] = fma(-ah, sDU[q * NCS + sidx(lane, j + 6 - k)], sDF[q * NCS + sidx(lane, j + 6 - k)]);
         }
         h = weno7_sum_d1(fma(ah, u[3], f[3]), dp, fma(ah, u[4], -f[4]), dm, eps);
+      } else if constexpr (sizeof(F) == 4) {
+        // WENO5, FP32: lane x f+ from cells i-2..i+2, lane y f- mirrored from i+3..i-1
+        float2 g[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) g[k] = make_float2(fmaf(ah, u[k], f[k]), fmaf(-ah, u[5 - k], f[5 - k]));
+        const float2 hh = weno5_pair(g[0], g[1], g[2], g[3], g[4], eps);
+        h = hh.x + hh.y;
       } else {
         h = weno5<F>(fma(ah, u[0], f[0]), fma(ah, u[1], f[1]), fma(ah, u[2], f[2]), fma(ah, u[3], f[3]),
                      fma(ah, u[4], f[4]), eps) +
