@@ -672,6 +672,8 @@ def main(argv=None):
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-event batched ensemble measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the 128^3 adjoint timing")
     ap.add_argument("--no-weno5", action="store_true", help="skip the WENO5 variant timing")
+    ap.add_argument("--weno5-only", action="store_true",
+                    help="run only the WENO5 section (for profiling its kernels)")
     ap.add_argument("--no-peaks", action="store_true", help="skip the ALU peak measurement (derived peaks instead)")
     ap.add_argument("--no-variant-error", action="store_true",
                     help="skip the 70-step FP64 reference run behind the variants' error columns")
@@ -703,6 +705,15 @@ def main(argv=None):
         build.build()
         from paper_1511_02137_b300 import hydro as hy
         out = {"adjoint": _adjoint(hy, args.adjoint_grid, args.adjoint_steps)} if rank == 0 else None
+    elif args.weno5_only:
+        from paper_1511_02137_b300 import build
+        build.build()
+        from paper_1511_02137_b300 import hydro as hy
+        from paper_1511_02137_b300 import workloads as W
+        w = _workload()
+        prim = W.ellipsoidal_primitives(w).ravel()
+        peaks = _alu_peaks(hy, _bus_id()) if not args.no_peaks else {}
+        out = {"weno5": _weno5(hy, w, prim, args, ws, _bus_id(), peaks)}
     elif args.impl == "reference":
         out = run_reference(args, rank, ws)
     else:
