@@ -5,10 +5,11 @@ arena it does not own, plugins whose host forbids cudaMalloc, real-time loops)
 step a state they own, with scratch kept in a fixed array inside the library.
 The test drives it through the C ABI on a caller-owned device buffer and
 checks two calls in a row against the regular context API (hydro_create /
-hydro_step): the state must be bit for bit the same in every precision (the
-same kernels and arithmetic; this entry point stages its tiles with plain
-loads where hydro_step uses TMA copies, which move the same values).  This
-file is named so that pytest collects it last.
+hydro_step): the state must be bit for bit the same in every precision and for
+both reconstructions, WENO7 and WENO5 (the same kernels and arithmetic; this
+entry point stages its tiles with plain loads where hydro_step uses TMA copies,
+which move the same values).  This file is named so that pytest collects it
+last.
 """
 import ctypes
 from dataclasses import replace
@@ -43,12 +44,13 @@ def _rel(a, b):
     return np.abs(a - b).max(axis=1) / np.abs(b).max(axis=1)
 
 
+@pytest.mark.parametrize("order", [7, 5])
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed"])
-def test_noalloc_matches_context_api_on_two_calls(env, precision):
+def test_noalloc_matches_context_api_on_two_calls(env, precision, order):
     torch, hy, W, fn = env
     w = replace(W.ELLIPSOIDAL_32, n=(40, 36, 30), sigma=(0.9, 1.0, 1.1))   # 43200 cells, ragged tiles
     prim = W.ellipsoidal_primitives(w).ravel()
-    cfg = hy.hydro_config_default(*w.n, precision=precision)
+    cfg = hy.hydro_config_default(*w.n, precision=precision, weno_order=order)
 
     ref = hy.hydro_create(cfg)
     hy.hydro_set_initial(ref, hy.HYDRO_PRIMITIVE, prim)
