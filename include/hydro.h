@@ -135,10 +135,12 @@ hydro_status hydro_workspace_size(const hydro_config* cfg, size_t* bytes);
  * cudaMalloc failed; HYDRO_ECUDA: other CUDA failure.  On failure *out = NULL. */
 hydro_status hydro_create(const hydro_config* cfg, hydro_ctx** out);
 
-/* Uploads the state at t0 from host memory.  kind = HYDRO_PRIMITIVE takes
- * (e, u^x, u^y, u^z, n) and converts to conserved variables on the device
- * (Eq. 1 with p = e/3); kind = HYDRO_CONSERVED takes (E, M^x, M^y, M^z, R).
- * host5 holds 5*nx*ny*nz doubles (pinned memory makes the copy asynchronous).
+/* Uploads the state at t0.  kind = HYDRO_PRIMITIVE takes (e, u^x, u^y, u^z, n)
+ * and converts to conserved variables on the device (Eq. 1 with p = e/3);
+ * kind = HYDRO_CONSERVED takes (E, M^x, M^y, M^z, R).  host5 holds 5*nx*ny*nz
+ * doubles in host memory (pinned memory makes the copy asynchronous) or in
+ * device memory of the context's device (unified addressing picks the copy's
+ * direction; a state built on the GPU needs no host copy of its own).
  * Resets time to t0 and the step counter to 0; keeps the jets.
  * HYDRO_EINVAL: NULL pointer, unknown kind, or e < 0 / non-finite values. */
 hydro_status hydro_set_initial(hydro_ctx* ctx, int32_t kind, const double* host5);
@@ -161,13 +163,14 @@ hydro_status hydro_add_jet(hydro_ctx* ctx, const double x0[3], const double dir[
  * hydro_set_initial; HYDRO_EINVAL for nsteps < 0. */
 hydro_status hydro_step(hydro_ctx* ctx, int32_t nsteps);
 
-/* Copies the current state to host memory as FP64 (FP32 storage is widened):
+/* Copies the current state to host5 as FP64 (FP32 storage is widened):
  * kind = HYDRO_CONSERVED gives (E, M^x, M^y, M^z, R), the conserved densities
  * of Eq. 1; kind = HYDRO_PRIMITIVE gives (e, u^x, u^y, u^z, n), Eq. 1 with
  * p = e/3 inverted on the device in FP64 with the same closed form the step
  * uses.  The paper names no read-back call; this is library plumbing (with
  * hydro_set_initial(HYDRO_CONSERVED) it also checkpoints and resumes a run).
- * host5 holds 5*nx*ny*nz doubles. */
+ * host5 holds 5*nx*ny*nz doubles, in host or device memory as for
+ * hydro_set_initial. */
 hydro_status hydro_read_fields(hydro_ctx* ctx, int32_t kind, double* host5);
 
 /* Fills *out with the context's diagnostics (synchronises the stream): the
@@ -217,7 +220,8 @@ hydro_status hydro_batch_workspace_size(const hydro_config* cfg, int32_t nevents
  * 256-byte aligned, caller-owned) or from cudaMalloc.  Errors as hydro_create. */
 hydro_status hydro_batch_create(const hydro_config* cfg, int32_t nevents, const int32_t* dims, hydro_batch** out);
 
-/* Initial state of grid `event` (as hydro_set_initial); resets the batch's
+/* Initial state of grid `event` (as hydro_set_initial, from host or device
+ * memory); resets the batch's
  * step counter.  Every grid needs one before stepping (else HYDRO_ESTATE). */
 hydro_status hydro_batch_set_initial(hydro_batch* b, int32_t event, int32_t kind, const double* host5);
 

@@ -236,7 +236,7 @@ hydro_status hydro_set_initial(hydro_ctx* c, int32_t kind, const double* host5) 
   std::memset(&zero, 0, sizeof(zero));
   cudaError_t e = cudaMemcpyAsync(c->diag(), &zero, sizeof(zero), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(c->staging(), host5, 5 * n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    e = cudaMemcpyAsync(c->staging(), host5, 5 * n * sizeof(double), cudaMemcpyDefault, c->stream);   // host or device
   if (e != cudaSuccess) return HYDRO_ECUDA;
   prof_mark(c, HYDRO_KERNEL_OTHER);
   e = launch_init(c->cfg.precision, kind, c->staging(), c->U(c->lay.u0), n, c->diag(), c->stream);
@@ -361,7 +361,7 @@ hydro_status hydro_read_fields(hydro_ctx* c, int32_t kind, double* host5) {
                                   c->stream);
   prof_mark(c, HYDRO_KERNEL_OTHER);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(host5, c->staging(), 5 * c->n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    e = cudaMemcpyAsync(host5, c->staging(), 5 * c->n * sizeof(double), cudaMemcpyDefault, c->stream);   // host or device
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   return cuda_status(e);
 }

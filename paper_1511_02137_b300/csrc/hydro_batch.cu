@@ -375,7 +375,7 @@ hydro_status hydro_batch_set_initial(hydro_batch* b, int32_t event, int32_t kind
   DevDiag* d = b->diags() + event;
   cudaError_t e = cudaStreamSynchronize(b->user);
   if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, sizeof(DevDiag), b->cs);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(staging, host5, 5 * n * sizeof(double), cudaMemcpyHostToDevice, b->cs);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(staging, host5, 5 * n * sizeof(double), cudaMemcpyDefault, b->cs);
   if (e == cudaSuccess)
     e = launch_init(b->cfg.precision, kind, staging, b->at(b->lay.u0) + b->off[event] * b->store(), n, d, b->cs);
   if (e == cudaSuccess && b->cfg.precision == HYDRO_MIXED)
@@ -584,7 +584,7 @@ hydro_status hydro_batch_read_fields(hydro_batch* b, int32_t event, int32_t kind
   if (e == cudaSuccess)
     e = launch_readback(b->cfg.precision, kind, b->at(b->lay.u0) + b->off[event] * b->store(), staging, n,
                         b->cfg.e_floor, b->cs);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(host5, staging, 5 * n * sizeof(double), cudaMemcpyDeviceToHost, b->cs);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host5, staging, 5 * n * sizeof(double), cudaMemcpyDefault, b->cs);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->cs);
   return e == cudaSuccess ? HYDRO_OK : HYDRO_ECUDA;
 }

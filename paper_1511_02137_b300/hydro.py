@@ -135,6 +135,11 @@ class Context:
         self.workspace = workspace
         self.cells = cfg.nx * cfg.ny * cfg.nz
 
+    @property
+    def device(self):
+        """The CUDA device of the workspace (field buffers may be tensors on it)."""
+        return None if self.workspace is None else self.workspace.device
+
     def __del__(self):
         if getattr(self, "handle", None):
             hydro_destroy(self)
@@ -179,7 +184,9 @@ def hydro_create(cfg: hydro_config, device=None, stream=None) -> Context:
     return ctx
 
 
-def _host_ptr(buf, n: int, writable: bool):
+def _host_ptr(buf, n: int, writable: bool, device=None):
+    """Address of a field buffer: a numpy array or CPU tensor, or (where the
+    call takes one, `device` set) a CUDA tensor on that device."""
     if isinstance(buf, np.ndarray):
         if buf.dtype != np.float64 or not buf.flags.c_contiguous or buf.size != n:
             raise ValueError(f"expected a C-contiguous float64 array of {n} values")
@@ -188,14 +195,21 @@ def _host_ptr(buf, n: int, writable: bool):
         return buf.ctypes.data
     import torch
     if isinstance(buf, torch.Tensor):
-        if buf.device.type != "cpu" or buf.dtype != torch.float64 or not buf.is_contiguous() or buf.numel() != n:
-            raise ValueError(f"expected a contiguous CPU float64 tensor of {n} values")
+        if buf.device.type == "cuda" and device is not None:
+            if buf.device != device:
+                raise ValueError(f"expected a tensor on {device}, got one on {buf.device}")
+        elif buf.device.type != "cpu":
+            raise ValueError("expected a CPU tensor")
+        if buf.dtype != torch.float64 or not buf.is_contiguous() or buf.numel() != n:
+            raise ValueError(f"expected a contiguous float64 tensor of {n} values")
         return buf.data_ptr()
-    raise TypeError("host buffer must be a numpy array or a CPU torch tensor")
+    raise TypeError("field buffer must be a numpy array or a torch tensor")
 
 
 def hydro_set_initial(ctx: Context, kind: int, host5) -> None:
-    _check(_lib().hydro_set_initial(ctx.handle, kind, _host_ptr(host5, 5 * ctx.cells, False)), "hydro_set_initial")
+    """host5: numpy array, CPU tensor or CUDA tensor on the context's device."""
+    _check(_lib().hydro_set_initial(ctx.handle, kind, _host_ptr(host5, 5 * ctx.cells, False, ctx.device)),
+           "hydro_set_initial")
 
 
 def hydro_add_jet(ctx: Context, x0, direction, t_start: float) -> int:
@@ -213,7 +227,8 @@ def hydro_step(ctx: Context, nsteps: int, allow=()) -> int:
 def hydro_read_fields(ctx: Context, kind: int = HYDRO_CONSERVED, out=None):
     if out is None:
         out = np.empty((5, ctx.cfg.nz, ctx.cfg.ny, ctx.cfg.nx), dtype=np.float64)
-    _check(_lib().hydro_read_fields(ctx.handle, kind, _host_ptr(out, 5 * ctx.cells, True)), "hydro_read_fields")
+    _check(_lib().hydro_read_fields(ctx.handle, kind, _host_ptr(out, 5 * ctx.cells, True, ctx.device)),
+           "hydro_read_fields")
     return out
 
 
@@ -255,6 +270,10 @@ class Batch:
         self.workspace = workspace
         self.cells = [d[0] * d[1] * d[2] for d in self.dims]
 
+    @property
+    def device(self):
+        return None if self.workspace is None else self.workspace.device
+
     def __del__(self):
         if getattr(self, "handle", None):
             hydro_batch_destroy(self)
@@ -293,8 +312,8 @@ def hydro_batch_create(cfg: hydro_config, dims, device=None, stream=None) -> Bat
 
 
 def hydro_batch_set_initial(b: Batch, event: int, kind: int, host5) -> None:
-    _check(_lib().hydro_batch_set_initial(b.handle, event, kind, _host_ptr(host5, 5 * b.cells[event], False)),
-           "hydro_batch_set_initial")
+    ptr = _host_ptr(host5, 5 * b.cells[event], False, b.device)
+    _check(_lib().hydro_batch_set_initial(b.handle, event, kind, ptr), "hydro_batch_set_initial")
 
 
 def hydro_batch_add_jet(b: Batch, event: int, x0, direction, t_start: float) -> int:
@@ -339,8 +358,8 @@ def hydro_batch_read_fields(b: Batch, event: int, kind: int = HYDRO_CONSERVED, o
     nx, ny, nz = b.dims[event]
     if out is None:
         out = np.empty((5, nz, ny, nx), dtype=np.float64)
-    _check(_lib().hydro_batch_read_fields(b.handle, event, kind, _host_ptr(out, 5 * b.cells[event], True)),
-           "hydro_batch_read_fields")
+    ptr = _host_ptr(out, 5 * b.cells[event], True, b.device)
+    _check(_lib().hydro_batch_read_fields(b.handle, event, kind, ptr), "hydro_batch_read_fields")
     return out
 
 
