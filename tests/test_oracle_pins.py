@@ -5,7 +5,8 @@ definition of T^{mu nu} (Eq. 1), a generic root solve, flux-Jacobian
 eigenvalues, exact polynomial reconstruction, the integral definition of the
 WENO smoothness indicators (sympy), invariants of the discrete scheme, the
 exact p = e/3 shock tube, Simpson's rule for the source (Eq. 3 integrated
-along the light-speed path) and the run parameters printed in the paper.
+along the light-speed path), an independent ODE solution for the time
+integrator's order and the run parameters printed in the paper.
 """
 import json
 import math
@@ -288,6 +289,45 @@ def test_source_only_state_change_matches_reported_deposit(orc):
     assert abs(dU[0].sum() * vol / diag.dep_E - 1.0) < 1e-12
     assert abs(dU[1].sum() * vol / diag.dep_E - 1.0) < 1e-12
     assert np.all(dU[2:] == 0)
+
+
+def test_rk3_is_third_order_in_time_on_the_jet_source_ode(orc):
+    """Fluid off, so that the jet's cell obeys the ODE dE/dt = dM^x/dt = S^0 of
+    Eq. 2-3, with T taken from the cell's state (the deposit heats and moves it:
+    the ODE is nonlinear, unlike the constant-T case where any rule exact for
+    linear integrands would pass).  The oracle's RK3 steps converge to an
+    independent solution of the same ODE (scipy DOP853, primitives by a generic
+    root solve, T from the EOS e = (pi^2/30) dof T^4/(hbar c)^3) at third order in
+    dt: a second-order combination or wrong stage times give order 2 or less."""
+    import warnings
+    from scipy.integrate import solve_ivp
+    hc, dof, kr, kc = 0.1973, 47.5, 4.0, 2.5
+    dx, t0, span, e0, n0 = 1.0, 1.0, 0.4, 1.0, 0.1
+
+    def rhs(t, y):
+        with warnings.catch_warnings():
+            warnings.simplefilter("ignore", RuntimeWarning)
+            e, _, _ = ref.primitives_by_solve(np.array([y[0], y[1], 0.0, 0.0, 0.0]))
+        T = (e * hc ** 3 / (math.pi ** 2 / 30.0 * dof)) ** 0.25
+        S0 = (kr * T ** 3 * (t - t0) / hc ** 2 + kc * T ** 2 / hc) / dx ** 3
+        return [S0, S0]
+
+    U0 = ref.conserved(e0, np.zeros(3), n0)
+    sol = solve_ivp(rhs, (t0, t0 + span), [U0[0], U0[1]], method="DOP853", rtol=1e-13, atol=1e-15)
+    want = sol.y[:, -1]
+    assert want[0] > 1.1 * U0[0]                 # the deposit is not a perturbation
+    U = _uniform_U(orc, (4, 4, 4), e0, (0.0, 0.0, 0.0), n0)
+    jet = orc.Jet((0.3, 0.5, 0.5), (1.0, 0.0, 0.0), t0)   # stays in cell (2, 2, 2): x in [0.3, 0.7]
+    errs = []
+    for nsteps in (4, 8, 16, 32):
+        c = orc.Config(4, 4, 4, dx=dx, dt=span / nsteps, t0=t0, fluid=False, k_rad=kr, k_coll=kc)
+        U1, diag = orc.run(c, U, nsteps, [jet])
+        assert diag.jet_cells[0] == (2, 2, 2)
+        got = np.array([U1[0, 2, 2, 2], U1[1, 2, 2, 2]])
+        errs.append(np.max(np.abs(got - want) / np.abs(want)))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert all(2.85 < q < 3.15 for q in orders), (errs, orders)   # measured 3.01, 3.01, 3.00
+    assert errs[-1] < 2e-8, errs
 
 
 # --------------------------------------------------------------- whole operator
