@@ -347,6 +347,32 @@ def test_uniform_state_has_zero_rhs_bitwise(orc, boundary, u3):
     np.testing.assert_allclose(U1, U, rtol=1e-15, atol=0)
 
 
+@pytest.mark.parametrize("boundary,pad_mode", [("outflow", "edge"), ("periodic", "wrap")])
+def test_boundaries_equal_explicit_ghost_layers(orc, boundary, pad_mode):
+    """The ghost fill by definition: outflow copies the edge cell into every
+    ghost layer (zero gradient), periodic wraps.  L of a grid with that boundary
+    equals, bit for bit, L on the interior of the same grid padded by 4 explicit
+    layers (numpy's 'edge' / 'wrap' padding; 4 = the reach of the interface
+    stencils) and stepped with outflow boundaries, whose own ghosts the interior
+    never reaches."""
+    rng = np.random.default_rng(11)
+    shape = (8, 9, 10)   # (nz, ny, nx)
+    prim = np.empty((5,) + shape)
+    prim[0] = 10 ** rng.uniform(-1, 1, shape)
+    prim[1:4] = rng.uniform(-0.8, 0.8, (3,) + shape)
+    prim[4] = rng.uniform(0.05, 0.2, shape)
+    U = orc.prim_to_cons(prim)
+    Up = np.pad(U, ((0, 0), (4, 4), (4, 4), (4, 4)), mode=pad_mode)
+    L, _, _ = orc.rhs(orc.Config(10, 9, 8, boundary=boundary), U, 1.0)
+    Lp, _, _ = orc.rhs(orc.Config(18, 17, 16, boundary="outflow"), Up, 1.0)
+    assert np.array_equal(L, Lp[:, 4:-4, 4:-4, 4:-4])
+    assert np.any(L != 0.0)
+    if boundary == "outflow":   # not what a mirror (reflecting) fill would give
+        Um = np.pad(U, ((0, 0), (4, 4), (4, 4), (4, 4)), mode="symmetric")
+        Lm, _, _ = orc.rhs(orc.Config(18, 17, 16, boundary="outflow"), Um, 1.0)
+        assert not np.array_equal(L, Lm[:, 4:-4, 4:-4, 4:-4])
+
+
 def test_conservation_with_periodic_boundaries(orc):
     """Periodic box: sum(E) and sum(M) change only by the RK3-weighted jet deposit."""
     rng = np.random.default_rng(9)
