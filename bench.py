@@ -49,16 +49,18 @@ UNIT = "cell-updates/s"
 # flux difference (10), the primitive recovery (23), |v|^2 (5), rho_x (14) and
 # F_x (10); y and z add difference and accumulation (15), rho_d and F_d; z adds
 # the stage combination (20, averaged over the three stages).
-FLOP_PER_INTERFACE = 141 + 10 * 122 + 5
+FLOP_RECON_W7 = 122
+FLOP_RECON_W5 = 65
+FLOP_PER_INTERFACE = 141 + 10 * FLOP_RECON_W7 + 5
 FLOP_PER_CELL = {"sweep_x": FLOP_PER_INTERFACE + 10 + 23 + 5 + 14 + 10,
                  "sweep_y": FLOP_PER_INTERFACE + 15 + 14 + 10,
                  "sweep_z": FLOP_PER_INTERFACE + 15 + 14 + 10 + 20}
 FLOP_PER_CELL_STEP = 3 * sum(FLOP_PER_CELL.values())
 # The same count for the WENO5 variant: the split over 5 cells per side (5 x 10
-# FMAs + alpha/2 = 101), 10 WENO5 reconstructions of 64 (candidates 15, second
-# differences 9, first-derivative terms 12, beta 9, weights 18 and one division)
-# and the 5 flux sums, 746 per interface; the per-cell terms as for WENO7.
-FLOP_PER_INTERFACE_W5 = 101 + 10 * 64 + 5
+# FMAs + alpha/2 = 101), 10 WENO5 reconstructions of 65 (candidates 15, second
+# differences 9, first-derivative terms 9, beta 15, weights 17) and the 5 flux
+# sums, 756 per interface; the per-cell terms as for WENO7.
+FLOP_PER_INTERFACE_W5 = 101 + 10 * FLOP_RECON_W5 + 5
 FLOP_PER_CELL_W5 = {k: v - FLOP_PER_INTERFACE + FLOP_PER_INTERFACE_W5 for k, v in FLOP_PER_CELL.items()}
 # Algorithmic HBM bytes per cell per step: 40 field accesses (stage 1 reads 5 and
 # writes 5; stages 2 and 3 read 10 and write 5) in storage precision.

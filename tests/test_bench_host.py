@@ -1,5 +1,6 @@
 """Host-side logic of bench.py without a GPU: multi-rank timing reduction over
-gloo (world size 2), clock-sample parsing and the roofline arithmetic."""
+gloo (world size 2), clock-sample parsing, the roofline arithmetic and the
+FLOP counts behind it."""
 import os
 import socket
 import sys
@@ -101,12 +102,123 @@ def test_algorithmic_counts_and_traffic_table():
             "sweep_z": {"ms": 2.0, "launches": 1}}
     t = bench.TRAFFIC_B_PER_CELL[("fp64", "sweep_z")]
     assert bench._roofline(prof, 8, "fp64")["traffic"] == (None if t is None else t * 8)
-    # WENO5: 64 per reconstruction, 746 per interface, the same per-cell terms;
+    # WENO5: 65 per reconstruction, 756 per interface, the same per-cell terms;
     # no DRAM table for it
-    assert bench.FLOP_PER_INTERFACE_W5 == 746
-    assert bench.FLOP_PER_CELL_W5 == {"sweep_x": 808, "sweep_y": 785, "sweep_z": 805}
+    assert bench.FLOP_PER_INTERFACE_W5 == 756
+    assert bench.FLOP_PER_CELL_W5 == {"sweep_x": 818, "sweep_y": 795, "sweep_z": 815}
     r5 = bench._roofline(prof, 8, "fp64", order=5)
-    assert r5["flop_per_launch"] == 8 * 805 and r5["traffic"] is None
+    assert r5["flop_per_launch"] == 8 * 815 and r5["traffic"] is None
+
+
+class _Counted:
+    """A float that counts the arithmetic operations applied to it (+, -, *, /:
+    one FLOP each, so an FMA's multiply and add count 2)."""
+    ops = 0
+
+    def __init__(self, v):
+        self.v = float(v)
+
+    @staticmethod
+    def _val(o):
+        return o.v if isinstance(o, _Counted) else float(o)
+
+    def _new(self, v):
+        _Counted.ops += 1
+        return _Counted(v)
+
+    def __add__(self, o):
+        return self._new(self.v + self._val(o))
+
+    __radd__ = __add__
+
+    def __sub__(self, o):
+        return self._new(self.v - self._val(o))
+
+    def __rsub__(self, o):
+        return self._new(self._val(o) - self.v)
+
+    def __mul__(self, o):
+        return self._new(self.v * self._val(o))
+
+    __rmul__ = __mul__
+
+    def __truediv__(self, o):
+        return self._new(self.v / self._val(o))
+
+    def __rtruediv__(self, o):
+        return self._new(self._val(o) / self.v)
+
+
+def _js_weights(q, beta, dk, eps):
+    """Jiang-Shu: sum_k alpha_k q_k / sum_k alpha_k, alpha_k = d_k / (eps + beta_k)^2."""
+    alpha = []
+    for b, d in zip(beta, dk):
+        s = b + eps
+        alpha.append(d / (s * s))
+    num, den = alpha[0] * q[0], alpha[0]
+    for a, qq in zip(alpha[1:], q[1:]):
+        num = num + a * qq
+        den = den + a
+    return num / den
+
+
+def _weno7_canonical(f, eps):
+    """WENO7 at x_{i+1/2} from f_{i-3..i+3}: the four candidate cubics from the
+    stencil values, Balsara-Shu indicators as 720 beta = 20 A^2 + 780 B^2 + 781 C^2
+    over the first, second and third differences, Jiang-Shu weights (1, 12, 18, 4)/35."""
+    qc = [(-3, 13, -23, 25), (1, -5, 13, 3), (-1, 7, 7, -1), (3, 13, -5, 1)]
+    q = []
+    for k, c in enumerate(qc):
+        acc = f[k] * (c[0] / 12)
+        for j in range(1, 4):
+            acc = acc + f[k + j] * (c[j] / 12)
+        q.append(acc)
+    d1 = [f[j + 1] - f[j] for j in range(6)]
+    d2 = [d1[j + 1] - d1[j] for j in range(5)]
+    d3 = [d2[j + 1] - d2[j] for j in range(4)]
+    ac = [(2, -7, 11), (-1, 5, 2), (2, 5, -1), (11, -7, 2)]
+    A = [d1[k] * ac[k][0] + d1[k + 1] * ac[k][1] + d1[k + 2] * ac[k][2] for k in range(4)]
+    B = [d2[1] * 2 - d2[0], d2[2], d2[2], d2[3] * 2 - d2[4]]
+    beta = [A[k] * A[k] * (20 / 720) + B[k] * B[k] * (780 / 720) + d3[k] * d3[k] * (781 / 720) for k in range(4)]
+    return _js_weights(q, beta, (1 / 35, 12 / 35, 18 / 35, 4 / 35), eps), beta
+
+
+def _weno5_canonical(f, eps):
+    """WENO5 at x_{i+1/2} from f_{i-2..i+2}: three candidate parabolas, Jiang-Shu
+    indicators 13/12 D^2 + 1/4 T^2 (second differences D, first-derivative terms
+    T), linear weights (1, 6, 3)/10."""
+    q = [f[0] * (2 / 6) + f[1] * (-7 / 6) + f[2] * (11 / 6), f[1] * (-1 / 6) + f[2] * (5 / 6) + f[3] * (2 / 6),
+         f[2] * (2 / 6) + f[3] * (5 / 6) + f[4] * (-1 / 6)]
+    D = [f[k] + f[k + 1] * (-2) + f[k + 2] for k in range(3)]
+    T = [f[0] + f[1] * (-4) + f[2] * 3, f[1] - f[3], f[2] * 3 + f[3] * (-4) + f[4]]
+    beta = [D[k] * D[k] * (13 / 12) + T[k] * T[k] * 0.25 for k in range(3)]
+    return _js_weights(q, beta, (0.1, 0.6, 0.3), eps), beta
+
+
+@pytest.mark.parametrize("order", [7, 5])
+def test_reconstruction_flop_counts_are_those_of_the_canonical_evaluation(orc, order):
+    """The per-reconstruction FLOPs behind roofline.achieved are counted by
+    running the canonical evaluation (candidates from the stencil values,
+    indicators from differences, Jiang-Shu weights) on counting scalars, and that
+    evaluation is checked against the oracle's reconstruction: same value and
+    indicators to rounding, so the count is of the method the kernels compute."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+
+    import bench
+    fn, ofn, n, want = ((_weno7_canonical, orc.weno7, 7, bench.FLOP_RECON_W7) if order == 7
+                        else (_weno5_canonical, orc.weno5, 5, bench.FLOP_RECON_W5))
+    rng = np.random.default_rng(order)
+    for trial in range(20):
+        f = rng.normal(size=n) * 10.0 ** rng.uniform(-3, 3)
+        if trial == 0:
+            f[n // 2 + 1:] += 5.0   # a step: weights far from linear
+        _Counted.ops = 0
+        val, beta = fn([_Counted(x) for x in f], 1e-6)
+        assert _Counted.ops == want
+        ov, _, obeta, _ = ofn(f, 1e-6)
+        assert abs(val.v - ov) <= 1e-12 * max(abs(ov), np.abs(f).max())
+        np.testing.assert_allclose([b.v for b in beta], obeta, rtol=1e-12, atol=1e-14 * np.abs(f).max() ** 2)
 
 
 def test_err_per_field_is_norm_relative():
