@@ -42,19 +42,24 @@ METRIC = "cell-updates/s per RK3 step at 256^3 (FP64 vs FP32); % of HBM roofline
 UNIT = "cell-updates/s"
 
 # Algorithmic work per cell of one directional sweep of one RK3 stage (FLOPs
-# with FMA = 2, division and square root = 1), counted on the textbook
-# evaluation: one interface is the LLF split (5 x 14 FMAs + alpha/2 = 141), 10
-# WENO7 reconstructions of 122 (candidates 28, differences 15, A 20, B 4,
-# beta 32, weights 23) and the 5 flux sums, 1366 in all; the x sweep adds the
-# flux difference (10), the primitive recovery (23), |v|^2 (5), rho_x (14) and
-# F_x (10); y and z add difference and accumulation (15), rho_d and F_d; z adds
-# the stage combination (20, averaged over the three stages).
+# with FMA = 2, division and square root = 1), counted on the canonical
+# evaluation of each term: one interface is the LLF split (5 fields x 14 FMAs +
+# alpha/2 = 141), 10 WENO7 reconstructions of 122 (candidates 28, differences
+# 15, A 20, B 4, beta 32, weights 23) and the 5 flux sums, 1366 in all; the x
+# sweep adds the flux difference (10), the primitive recovery (21), |v|^2 (5),
+# rho_x (12) and F_x / 2 (10); y and z add difference and accumulation (15),
+# rho_d and F_d / 2; z adds the stage combination (20, averaged over the three
+# stages).
 FLOP_RECON_W7 = 122
 FLOP_RECON_W5 = 65
-FLOP_PER_INTERFACE = 141 + 10 * FLOP_RECON_W7 + 5
-FLOP_PER_CELL = {"sweep_x": FLOP_PER_INTERFACE + 10 + 23 + 5 + 14 + 10,
-                 "sweep_y": FLOP_PER_INTERFACE + 15 + 14 + 10,
-                 "sweep_z": FLOP_PER_INTERFACE + 15 + 14 + 10 + 20}
+FLOP_SPLIT, FLOP_FSUM = 141, 5
+FLOP_DIFF, FLOP_DIFF_ACC, FLOP_STAGE = 10, 15, 20
+FLOP_C2P, FLOP_V2, FLOP_RHO, FLOP_HALF_FLUX = 21, 5, 12, 10
+FLOP_PER_INTERFACE = FLOP_SPLIT + 10 * FLOP_RECON_W7 + FLOP_FSUM
+FLOP_PER_CELL = {
+    "sweep_x": FLOP_PER_INTERFACE + FLOP_DIFF + FLOP_C2P + FLOP_V2 + FLOP_RHO + FLOP_HALF_FLUX,
+    "sweep_y": FLOP_PER_INTERFACE + FLOP_DIFF_ACC + FLOP_RHO + FLOP_HALF_FLUX,
+    "sweep_z": FLOP_PER_INTERFACE + FLOP_DIFF_ACC + FLOP_RHO + FLOP_HALF_FLUX + FLOP_STAGE}
 FLOP_PER_CELL_STEP = 3 * sum(FLOP_PER_CELL.values())
 # The same count for the WENO5 variant: the split over 5 cells per side (5 x 10
 # FMAs + alpha/2 = 101), 10 WENO5 reconstructions of 65 (candidates 15, second

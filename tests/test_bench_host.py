@@ -83,16 +83,16 @@ def test_roofline_arithmetic():
 
 def test_algorithmic_counts_and_traffic_table():
     """The FLOP counts behind roofline.achieved, assembled from their per-unit
-    terms (122 per WENO7 reconstruction, 1366 per interface; 1428 / 1405 / 1425
-    per cell for the x / y / z sweeps, 12774 per cell and RK3 step), and a DRAM
+    terms (122 per WENO7 reconstruction, 1366 per interface; 1424 / 1403 / 1423
+    per cell for the x / y / z sweeps, 12750 per cell and RK3 step), and a DRAM
     entry for every sweep of every precision: null (stale) or at least the
     sweep's own stored-field accesses per cell (x: 5 staged fields read and 5
     accumulator fields written; y: also 5 read; z: also the step state)."""
     sys.path.insert(0, ROOT)
     import bench
     assert bench.FLOP_PER_INTERFACE == 1366
-    assert bench.FLOP_PER_CELL == {"sweep_x": 1428, "sweep_y": 1405, "sweep_z": 1425}
-    assert bench.FLOP_PER_CELL_STEP == 12774
+    assert bench.FLOP_PER_CELL == {"sweep_x": 1424, "sweep_y": 1403, "sweep_z": 1423}
+    assert bench.FLOP_PER_CELL_STEP == 12750
     own = {"sweep_x": 10, "sweep_y": 15, "sweep_z": 15}   # 4-byte field accesses at least
     for p in ("fp64", "fp32", "mixed"):
         for k in ("sweep_x", "sweep_y", "sweep_z"):
@@ -105,9 +105,9 @@ def test_algorithmic_counts_and_traffic_table():
     # WENO5: 65 per reconstruction, 756 per interface, the same per-cell terms;
     # no DRAM table for it
     assert bench.FLOP_PER_INTERFACE_W5 == 756
-    assert bench.FLOP_PER_CELL_W5 == {"sweep_x": 818, "sweep_y": 795, "sweep_z": 815}
+    assert bench.FLOP_PER_CELL_W5 == {"sweep_x": 814, "sweep_y": 793, "sweep_z": 813}
     r5 = bench._roofline(prof, 8, "fp64", order=5)
-    assert r5["flop_per_launch"] == 8 * 815 and r5["traffic"] is None
+    assert r5["flop_per_launch"] == 8 * 813 and r5["traffic"] is None
 
 
 class _Counted:
@@ -247,3 +247,81 @@ def test_cpu_baseline_reports_the_all_core_run_and_the_labelled_single_core_extr
     assert one["cores"] == 1 and one["value"] > 0 and "16^3" in one["sample"]
     assert abs(one["full_run_s_extrapolated"] - w.cells * w.steps / one["value"]) <= 0.06
     assert "extrapolated" in one["full_run"] and "not run" in one["full_run"]
+
+
+def _csqrt(x):
+    _Counted.ops += 1
+    return _Counted(x.v ** 0.5)
+
+
+def test_per_cell_flop_terms_are_those_of_the_canonical_evaluation(orc):
+    """The per-cell terms of the FLOP count, each executed on counting scalars:
+    the closed-form recovery (Eq. 1 with p = e/3 inverted: m = abs(M)/E,
+    v = 3m / (2 + sqrt(4 - 3m^2)), e = E - abs(M) v), abs(v)^2, the spectral
+    radius max abs(lambda_pm) and the half fluxes F_d / 2, checked against the
+    oracle's recovery and characteristic speeds and the flux built from the
+    stress tensor's definition; then the split, sums, differences and stage
+    combinations, which assemble the per-cell totals of the bench."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+
+    import bench
+    import physics_ref as ref
+    rng = np.random.default_rng(5)
+    c2 = 1.0 / 3.0
+    for _ in range(10):
+        e0, n0 = 10 ** rng.uniform(-2, 2), rng.uniform(0.01, 0.3)
+        u3 = rng.normal(size=3) * rng.uniform(0.1, 3.0)
+        U = ref.conserved(e0, u3, n0)
+        E, Mx, My, Mz, R = (_Counted(x) for x in U)
+        _Counted.ops = 0
+        Mabs = _csqrt(Mx * Mx + My * My + Mz * Mz)
+        m = Mabs / E
+        v = m * 3 / (_csqrt(4 - m * m * 3) + 2)
+        e = E - Mabs * v
+        p = e / 3
+        vm = v / Mabs
+        vel = (vm * Mx, vm * My, vm * Mz)
+        assert _Counted.ops == bench.FLOP_C2P
+        want, _ = orc.cons_to_prim(U.reshape(5, 1))
+        np.testing.assert_allclose([e.v, *(a.v for a in vel), p.v], want[:5, 0], rtol=1e-13, atol=1e-15)
+        _Counted.ops = 0
+        v2 = vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]
+        assert _Counted.ops == bench.FLOP_V2
+        M = (Mx, My, Mz)
+        for d in range(3):
+            vd = vel[d]
+            _Counted.ops = 0
+            den = 1 - v2 * c2
+            disc = (1 - v2) * (den - vd * vd * (1 - c2))
+            rho = (_Counted(abs(vd.v)) * (1 - c2) + _csqrt(disc) * c2 ** 0.5) / den
+            assert _Counted.ops == bench.FLOP_RHO
+            lm, lp = orc.char_speeds(np.array([a.v for a in vel]), d)
+            assert abs(rho.v - max(abs(lm), abs(lp))) <= 1e-14
+            _Counted.ops = 0
+            half = [M[d] * 0.5] + [(M[i] * vd + p) * 0.5 if i == d else M[i] * vd * 0.5 for i in range(3)]
+            half.append(R * vd * 0.5)
+            assert _Counted.ops == bench.FLOP_HALF_FLUX
+            np.testing.assert_allclose([h.v for h in half], ref.flux(e0, u3, n0, d) / 2, rtol=1e-12, atol=1e-14)
+    # the linear terms: split (7 cells per side, 5 fields, and alpha / 2), flux
+    # sums, differences (x) or differences accumulated (y, z), stage combinations
+    x = [_Counted(v) for v in rng.normal(size=8)]
+    _Counted.ops = 0
+    ah = x[0] * 0.5
+    for _ in range(5):
+        [x[1] + ah * x[2] for _ in range(7)], [x[1] - ah * x[2] for _ in range(7)]
+    assert _Counted.ops == bench.FLOP_SPLIT
+    _Counted.ops = 0
+    [x[3] + x[4] for _ in range(5)]
+    assert _Counted.ops == bench.FLOP_FSUM
+    _Counted.ops = 0
+    [(x[3] - x[4]) * -10.0 for _ in range(5)]
+    assert _Counted.ops == bench.FLOP_DIFF
+    _Counted.ops = 0
+    [x[5] + (x[3] - x[4]) * -10.0 for _ in range(5)]
+    assert _Counted.ops == bench.FLOP_DIFF_ACC
+    _Counted.ops = 0
+    [x[6] + x[7] * 0.02 for _ in range(5)]                            # U + dt L
+    [x[5] * 0.75 + (x[6] + x[7] * 0.02) * 0.25 for _ in range(10)]    # a U0 + b (U + dt L), stages 2 and 3
+    assert _Counted.ops == 3 * bench.FLOP_STAGE
+    assert bench.FLOP_PER_INTERFACE == bench.FLOP_SPLIT + 10 * bench.FLOP_RECON_W7 + bench.FLOP_FSUM
