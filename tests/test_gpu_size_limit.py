@@ -142,3 +142,41 @@ def test_grid_at_the_size_limit_matches_a_small_grid_cell_for_cell(hy, orc, prec
     assert mismatched == [0] * 5, mismatched
     assert db["status"] == ds["status"] == 0
     assert db["max_speed"] == ds["max_speed"] and db["floor_hits"] == ds["floor_hits"]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed"])
+def test_device_field_buffers_match_host_buffers(hy, precision):
+    """hydro_set_initial and hydro_read_fields (and their batch forms) take
+    device pointers as well as host pointers: the same state, uploaded from a
+    CUDA tensor and from a numpy array, steps to the same fields bit for bit, and
+    a read into a CUDA tensor equals the read into host memory."""
+    import torch
+    shape = (20, 18, 16)
+    prim = _primitives(shape)
+    prim[0] *= 1.0 + 0.1 * np.random.default_rng(7).random(prim[0].shape)
+    dev = torch.device("cuda")
+    out = []
+    for src in (prim.ravel(), torch.from_numpy(prim.ravel()).to(dev)):
+        ctx = hy.hydro_create(_config(hy, shape, precision))
+        hy.hydro_set_initial(ctx, hy.HYDRO_PRIMITIVE, src)
+        hy.hydro_step(ctx, 2)
+        host = hy.hydro_read_fields(ctx, hy.HYDRO_CONSERVED)
+        d = torch.empty(host.size, dtype=torch.float64, device=dev)
+        hy.hydro_read_fields(ctx, hy.HYDRO_CONSERVED, d)
+        assert np.array_equal(d.cpu().numpy(), host.ravel())
+        out.append(host)
+        del ctx
+    assert np.array_equal(out[0], out[1])
+    cfg = _config(hy, (1, 1, 1), precision)
+    b = hy.hydro_batch_create(cfg, [shape, shape])
+    hy.hydro_batch_set_initial(b, 0, hy.HYDRO_PRIMITIVE, prim.ravel())
+    hy.hydro_batch_set_initial(b, 1, hy.HYDRO_PRIMITIVE, torch.from_numpy(prim.ravel()).to(dev))
+    hy.hydro_batch_step(b, 2)
+    d = torch.empty(prim.size, dtype=torch.float64, device=dev)
+    hy.hydro_batch_read_fields(b, 1, hy.HYDRO_CONSERVED, d)
+    assert np.array_equal(hy.hydro_batch_read_fields(b, 0), d.cpu().numpy().reshape(out[0].shape))
+    assert np.array_equal(d.cpu().numpy(), out[0].ravel())
+    with pytest.raises(ValueError):   # a tensor of the wrong type is refused before the call
+        hy.hydro_batch_read_fields(b, 0, hy.HYDRO_CONSERVED, d.float())
+    hy.hydro_batch_destroy(b)
