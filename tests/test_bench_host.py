@@ -325,3 +325,24 @@ def test_per_cell_flop_terms_are_those_of_the_canonical_evaluation(orc):
     [x[5] * 0.75 + (x[6] + x[7] * 0.02) * 0.25 for _ in range(10)]    # a U0 + b (U + dt L), stages 2 and 3
     assert _Counted.ops == 3 * bench.FLOP_STAGE
     assert bench.FLOP_PER_INTERFACE == bench.FLOP_SPLIT + 10 * bench.FLOP_RECON_W7 + bench.FLOP_FSUM
+
+
+def test_reference_arm_under_torchrun_with_two_ranks_prints_one_line():
+    """The launch the multi-GPU contract uses (torch.distributed.run, one
+    process per rank, rendezvous on 127.0.0.1), here with two gloo ranks on the
+    CPU and the reference arm: rank 0 alone runs the oracle and prints one JSON
+    line naming both ranks; the other rank exits 0 without work."""
+    import json
+    import subprocess
+    port = _free_port()
+    env = dict(os.environ, OMP_NUM_THREADS="4")
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
+           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "3"]
+    r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout[-2000:]
+    out = json.loads(lines[0])
+    assert out["impl"] == "reference" and out["n_gpus"] == 2 and out["value"] > 0
+    assert out["warmup"] == 3 and out["steps"] == 1 and out["cpu_baseline"]["kind"] == "oracle"
