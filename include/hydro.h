@@ -47,7 +47,12 @@ typedef enum {
   HYDRO_ECFL = 5,        /* max signal speed * dt / dx exceeded cfl_limit */
   HYDRO_ETIMEOUT = 6,    /* a bounded device-side wait expired (hydro_config.wait_limit_s); the
                             fields written by that step are invalid: set a new initial state */
-  HYDRO_ESTATE = 7       /* call out of order (e.g. hydro_step before hydro_set_initial) */
+  HYDRO_ESTATE = 7,      /* call out of order (e.g. hydro_step before hydro_set_initial) */
+  HYDRO_ECHECK = 8       /* bounds-checked build only (libhydro_check.so, compiled with
+                            -DHYDRO_CHECK): a sweep kernel computed a global-memory index outside
+                            its buffer or a TMA coordinate the copy rules forbid; the access was
+                            redirected inside the buffer or the copy skipped, hydro_diag names the
+                            first one (check_site, check_index), and the step's results are invalid */
 } hydro_status;
 
 enum { HYDRO_FP64 = 0, HYDRO_FP32 = 1, HYDRO_MIXED = 2 };     /* hydro_config.precision */
@@ -96,7 +101,11 @@ typedef struct {
                            (hydro_step, hydro_batch_step) returns HYDRO_ETIMEOUT (nothing is
                            in flight when the tiles exit).  0 in normal use; the adjoint
                            rejects 1, the allocation-free step issues no TMA copy. */
-  int32_t reserved_;    /* zero */
+  int32_t test_check_tighten; /* test hook of the bounds-checked build: 1 = every checked bound
+                           is halved, so that accesses to the upper half of each buffer are
+                           recorded (and redirected into the lower half: no access leaves its
+                           buffer) and the step returns HYDRO_ECHECK.  Must be 0 in the regular
+                           build (HYDRO_EINVAL otherwise) and for the adjoint. */
 } hydro_config;
 
 typedef struct hydro_ctx hydro_ctx;
@@ -114,6 +123,10 @@ typedef struct {
   int32_t jet_cell[HYDRO_MAX_JETS][3]; /* cell where each jet deposited at the last stage, as
                                           recorded by the device; -1 if it deposited nothing */
   int32_t status;               /* first error status raised on the device since creation */
+  int32_t check_site;           /* bounds-checked build: the first failed check's site, 0 if none:
+                                   1-3 a cell offset formed for the phase-3 operand copies, a
+                                   staged cell or an updated cell; 4 a TMA load, 5 a TMA store */
+  uint32_t check_index;         /* ... and the index it computed (for a TMA site: the coordinate) */
 } hydro_diag;
 
 /* Paper defaults (Sec. 1, Sec. 2, Fig. 3 caption) for an nx x ny x nz grid, FP64,

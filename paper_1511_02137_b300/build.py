@@ -1,6 +1,6 @@
 """Builds the CUDA library ``libhydro.so`` in-tree for sm_103a (B300).
 
-    python -m paper_1511_02137_b300.build [--verbose]
+    python -m paper_1511_02137_b300.build [--verbose] [--checked]
 
 nvcc compiles the kernels and the C ABI into one shared library next to this
 file.  Host code is compiled without floating-point contraction so that the
@@ -18,6 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libhydro.so")
+LIB_CHECKED = os.path.join(HERE, "libhydro_check.so")   # -DHYDRO_CHECK: bounds-checked sweeps
 SOURCES = ["hydro_api.cu", "hydro_sweep.cu", "hydro_noalloc.cu", "hydro_batch.cu", "hydro_adjoint.cu",
            "hydro_mathcheck.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -37,27 +38,36 @@ def _inputs():
     return files
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
-    tmp = LIB + ".tmp%d" % os.getpid()
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Builds libhydro.so, or with `checked` the bounds-checked libhydro_check.so
+    (-DHYDRO_CHECK: the sweep tiles check every global cell offset and TMA
+    coordinate and report a failure as HYDRO_ECHECK; for tests, not for timing)."""
+    lib = LIB_CHECKED if checked else LIB
+    if not force and up_to_date(lib):
+        return lib
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC,-ffp-contract=off",
            "-I", INCLUDE, "-I", CSRC, "-o", tmp]
+    if checked:
+        cmd.append("-DHYDRO_CHECK")
     if verbose:
         cmd += ["-Xptxas", "-v"]
     cmd += [os.path.join(CSRC, s) for s in SOURCES]
     subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
+
+
+def build_checked(force: bool = False) -> str:
+    return build(force=force, checked=True)
 
 
 if __name__ == "__main__":
-    build(force=True, verbose="--verbose" in sys.argv)
-    print(LIB)
+    print(build(force=True, verbose="--verbose" in sys.argv, checked="--checked" in sys.argv))

@@ -833,7 +833,7 @@ cudaError_t combine(hydro_adjoint* a, int mode, int st) {
 bool adjoint_config_ok(const hydro_config* cfg, int32_t nsteps, int32_t checkpoint_every) {
   if (!config_valid(cfg, kCheckGrid | kCheckWorkspace)) return false;
   if ((cfg->precision != HYDRO_FP64 && cfg->precision != HYDRO_MIXED) || cfg->boundary != HYDRO_OUTFLOW ||
-      cfg->weno_order != 7 || cfg->test_withhold_copies != 0)
+      cfg->weno_order != 7 || cfg->test_withhold_copies != 0 || cfg->test_check_tighten != 0)
     return false;
   return nsteps >= 1 && checkpoint_every >= 1;
 }

@@ -28,6 +28,11 @@ bool hydro::config_valid(const hydro_config* c, unsigned what) {
   if (!std::isfinite(c->k_rad) || !std::isfinite(c->k_coll) || !std::isfinite(c->cr_over_cf)) return false;
   if (!(c->wait_limit_s >= 0.0 && c->wait_limit_s <= 10.0)) return false;
   if (c->test_withhold_copies != 0 && c->test_withhold_copies != 1) return false;
+#ifdef HYDRO_CHECK
+  if (c->test_check_tighten != 0 && c->test_check_tighten != 1) return false;
+#else
+  if (c->test_check_tighten != 0) return false;   // a hook of the bounds-checked build only
+#endif
   if ((what & kCheckWorkspace) && c->workspace && ((uintptr_t)c->workspace % 256) != 0) return false;
   return true;
 }
@@ -305,6 +310,7 @@ hydro_status hydro_step(hydro_ctx* c, int32_t nsteps) {
   a.src.inv_vol = 1.0 / vol;
   a.wait_ns = wait_limit_ns(g);
   a.withhold = g.test_withhold_copies;
+  a.check_tighten = g.test_check_tighten;
   cudaError_t err = cudaSuccess;
   for (int32_t s = 0; s < nsteps && err == cudaSuccess; ++s) {
     const int64_t n = c->steps;
@@ -388,6 +394,8 @@ hydro_status hydro_get_diag(hydro_ctx* c, hydro_diag* out) {
   for (int j = c->njet; j < kMaxJets; ++j)
     for (int a = 0; a < 3; ++a) out->jet_cell[j][a] = -1;
   out->status = d.status;
+  out->check_site = d.check_site;
+  out->check_index = d.check_index;
   return HYDRO_OK;
 }
 
@@ -425,6 +433,7 @@ const char* hydro_status_string(hydro_status s) {
     case HYDRO_ECFL: return "HYDRO_ECFL: CFL limit exceeded";
     case HYDRO_ETIMEOUT: return "HYDRO_ETIMEOUT: bounded wait expired";
     case HYDRO_ESTATE: return "HYDRO_ESTATE: call out of order";
+    case HYDRO_ECHECK: return "HYDRO_ECHECK: a bounds check of the checked build failed";
     default: return "unknown hydro_status";
   }
 }

@@ -214,6 +214,7 @@ BatchArgs base_args(hydro_batch* b) {
   a.eps = g.weno_eps;
   a.wait_ns = wait_limit_ns(g);
   a.withhold = g.test_withhold_copies;
+  a.check_tighten = g.test_check_tighten;
   a.src.rad = g.k_rad * g.cr_over_cf / (g.hbarc * g.hbarc);
   a.src.coll = g.k_coll * g.cr_over_cf / g.hbarc;
   a.src.t4coef = g.hbarc * g.hbarc * g.hbarc / (M_PI * M_PI / 30.0 * g.dof);
@@ -609,6 +610,8 @@ hydro_status hydro_batch_get_diag(hydro_batch* b, int32_t event, hydro_diag* out
     for (int a = 0; a < 3; ++a) out->dep_M[a] += J[j].n[a] * d.dep[j];
   }
   out->status = d.status;
+  out->check_site = d.check_site;
+  out->check_index = d.check_index;
   return HYDRO_OK;
 }
 

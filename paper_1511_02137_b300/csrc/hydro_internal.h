@@ -22,6 +22,8 @@ struct DevDiag {
   int bad_input;                  // set by the initial-state conversion for e < 0 or non-finite input
   double dep[kMaxJets];           // per-jet RK3-weighted deposited energy [GeV]
   int cell[kMaxJets][3];          // cell where each jet deposited at its last deposit
+  int check_site;                 // bounds-checked build: site of the first failed check (0 = none)
+  unsigned check_index;           // and the index or coordinate it computed
 };
 
 // Jet positions for one RK stage, computed on the host in FP64.
@@ -102,6 +104,7 @@ struct GridArgs {
   int count_floors; // 1: count floor hits (x sweep of each stage)
   unsigned long long wait_ns;  // limit of each bounded wait on a TMA copy (0: kDefaultWaitNs)
   int withhold;     // fault injection: arm the copy barriers but issue no TMA copy
+  int check_tighten;  // bounds-checked build: halve every checked bound (test hook)
   SourceCoef src;
   LaunchConst k;    // filled by the launchers from the fields above
 };
@@ -141,6 +144,7 @@ struct BatchArgs {
   int reduce_speed, count_floors;
   unsigned long long wait_ns;   // limit of each bounded wait on a TMA copy (0: kDefaultWaitNs)
   int withhold;     // fault injection: arm the copy barriers but issue no TMA copy
+  int check_tighten;  // bounds-checked build: halve every checked bound (test hook)
   SourceCoef src;
   LaunchConst k;    // filled by launch_batch_sweep
   const SweepMaps* maps;   // [nev] tensor maps of this launch's stage and axis, or NULL (plain loads)

@@ -146,6 +146,7 @@ extern "C" hydro_status hydro_step_noalloc(const hydro_config* cfg, void* d_stat
   const double vol = cfg->dx * cfg->dx * cfg->dx;
   a.src.inv_vol = 1.0 / vol;
   a.wait_ns = hydro::wait_limit_ns(*cfg);   // (plain loads: no TMA copy waits here)
+  a.check_tighten = cfg->test_check_tighten;
   const int N[3] = {cfg->nx, cfg->ny, cfg->nz};
   for (int32_t s = 0; s < nsteps && err == cudaSuccess; ++s) {
     const int64_t step = step0 + s;
@@ -204,6 +205,8 @@ extern "C" hydro_status hydro_step_noalloc(const hydro_config* cfg, void* d_stat
       for (int ax = 0; ax < 3; ++ax) diag_out->dep_M[ax] += jn[j][ax] * d.dep[j];
     }
     diag_out->status = d.status;
+    diag_out->check_site = d.check_site;
+    diag_out->check_index = d.check_index;
   }
   if (d.status != 0) return (hydro_status)d.status;
   if (cfg->cfl_limit > 0.0 && nsteps > 0) {

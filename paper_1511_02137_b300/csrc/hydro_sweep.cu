@@ -32,6 +32,7 @@
 #include <cstring>
 
 #include "hydro.h"
+#include "hydro_check.cuh"
 #include "hydro_internal.h"
 #include "hydro_math.cuh"
 
@@ -366,8 +367,9 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
       if (!a.withhold) {
         const int c0 = DIR == 0 ? a0 : l0, c1 = DIR == 0 ? l0 : (DIR == 1 ? a0 : fixed),
                   c2 = DIR == 2 ? a0 : fixed;
-        tma_load_4d(sPr, &maps->rhs, c0, c1, c2, 0, tb->pf);
-        if (need_u0) tma_load_4d(sP0, &maps->u0, c0, c1, c2, 0, tb->pf);
+        if (HYDRO_TMA_OK(c0, (int)sizeof(F), c1, c2, false)) tma_load_4d(sPr, &maps->rhs, c0, c1, c2, 0, tb->pf);
+        if (need_u0 && HYDRO_TMA_OK(c0, (int)sizeof(Store), c1, c2, false))
+          tma_load_4d(sP0, &maps->u0, c0, c1, c2, 0, tb->pf);
       }
     }
   } else if constexpr (PF::on) {
@@ -379,7 +381,7 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
     else { j = c / LANES; lane = c - j * LANES; }
     const int ga = a0 + j, gl = l0 + lane;
     if (ga < n_along && gl < n_lane && pf_want) {
-      const unsigned o = offset(ga, gl);
+      const unsigned o = HYDRO_CELL(offset(ga, gl), N, kSiteOperands);
 #pragma unroll
       for (int q = 0; q < 5; ++q) cp_async_ca<sizeof(F)>(sPr + q * NC + c, rhs_in + q * N + o);
       if constexpr (FINAL) {
@@ -424,9 +426,15 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
         mbar_expect_tx(tb->stage, (unsigned)(NSF * NCS * sizeof(F)));
         if (a.withhold) {
           // fault injection: the barrier is armed but no copy is issued
-        } else if (DIR == 0) tma_load_4d(sStage, &maps->stage, a0 - G, l0, fixed, 0, tb->stage);
-        else if (DIR == 1) tma_load_4d(sStage, &maps->stage, l0, a0 - G, fixed, 0, tb->stage);
-        else tma_load_4d(sStage, &maps->stage, l0, fixed, a0 - G, 0, tb->stage);
+        } else if (DIR == 0) {
+          if (HYDRO_TMA_OK(a0 - G, (int)sizeof(F), l0, fixed, false))
+            tma_load_4d(sStage, &maps->stage, a0 - G, l0, fixed, 0, tb->stage);
+        } else if (DIR == 1) {
+          if (HYDRO_TMA_OK(l0, (int)sizeof(F), a0 - G, fixed, false))
+            tma_load_4d(sStage, &maps->stage, l0, a0 - G, fixed, 0, tb->stage);
+        } else if (HYDRO_TMA_OK(l0, (int)sizeof(F), fixed, a0 - G, false)) {
+          tma_load_4d(sStage, &maps->stage, l0, fixed, a0 - G, 0, tb->stage);
+        }
       }
       if (!mbar_wait_bounded(tb->stage, tb->ph_stage, a.wait_ns)) {
         atomicCAS(&a.diag->status, 0, (int)HYDRO_ETIMEOUT);
@@ -488,12 +496,14 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
         R = sStage[4 * NCS + c]; om = sStage[5 * NCS + c];
       } else {
         const float* __restrict__ S = a.S;
-        const unsigned o = offset(map_along(ga, n_along, a.periodic), gl < n_lane ? gl : n_lane - 1);
+        const unsigned o =
+            HYDRO_CELL(offset(map_along(ga, n_along, a.periodic), gl < n_lane ? gl : n_lane - 1), N, kSiteStaging);
         E = S[o]; Mx = S[N + o]; My = S[2 * N + o]; Mz = S[3 * N + o]; R = S[4 * N + o]; om = S[5 * N + o];
       }
       cons_to_prim_shadow_rho(E, Mx, My, Mz, om, a.k.e_floor_f, e, vx, vy, vz, v2, rden, hit);
     } else if constexpr (CACHE) {
-      const unsigned og = offset(map_along(ga, n_along, a.periodic), gl < n_lane ? gl : n_lane - 1);
+      const unsigned og =
+          HYDRO_CELL(offset(map_along(ga, n_along, a.periodic), gl < n_lane ? gl : n_lane - 1), N, kSiteStaging);
       Store Es, Mxs, Mys, Mzs, Rs;
       if (staged) {
         Es = (Store)sStage[c]; Mxs = (Store)sStage[NCS + c]; Mys = (Store)sStage[2 * NCS + c];
@@ -524,7 +534,8 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
         Es = (Store)sStage[c]; Mxs = (Store)sStage[NCS + c]; Mys = (Store)sStage[2 * NCS + c];
         Mzs = (Store)sStage[3 * NCS + c]; Rs = (Store)sStage[4 * NCS + c];
       } else {
-        const unsigned o = offset(map_along(ga, n_along, a.periodic), gl < n_lane ? gl : n_lane - 1);
+        const unsigned o =
+            HYDRO_CELL(offset(map_along(ga, n_along, a.periodic), gl < n_lane ? gl : n_lane - 1), N, kSiteStaging);
         Es = U[o]; Mxs = U[N + o]; Mys = U[2 * N + o]; Mzs = U[3 * N + o]; Rs = U[4 * N + o];
       }
       cons_to_prim_rho<Math>(Es, Mxs, Mys, Mzs, kconst<F>(a.e_floor, a.k.e_floor_f), e, vx, vy, vz, v2, rden, hit);
@@ -693,7 +704,7 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
     else { j = c / LANES; lane = c - j * LANES; }
     const int ga = a0 + j, gl = l0 + lane;
     if (ga < n_along && gl < n_lane) {
-      const unsigned o = offset(ga, gl);
+      const unsigned o = HYDRO_CELL(offset(ga, gl), N, kSiteUpdate);
       const int h0 = hidx(lane, j), h1 = hidx(lane, j + 1);
       F L[5];
       if constexpr (SH) {
@@ -810,8 +821,11 @@ __device__ __forceinline__ void sweep_tile(const GridArgs& a, const JetStage& je
     fence_proxy_async_smem();
     __syncthreads();
     if (threadIdx.x == 0) {
-      if (DIR == 0) tma_store_4d(&maps->rhs, sOut, a0, l0, fixed, 0);
-      else tma_store_4d(&maps->rhs, sPr, l0, a0, fixed, 0);
+      if (DIR == 0) {
+        if (HYDRO_TMA_OK(a0, (int)sizeof(F), l0, fixed, true)) tma_store_4d(&maps->rhs, sOut, a0, l0, fixed, 0);
+      } else if (HYDRO_TMA_OK(l0, (int)sizeof(F), a0, fixed, true)) {
+        tma_store_4d(&maps->rhs, sPr, l0, a0, fixed, 0);
+      }
       tma_store_commit_wait_read();
     }
   }
@@ -892,6 +906,7 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<PREC>()) batch_swee
     g.count_floors = b.count_floors;
     g.wait_ns = b.wait_ns;
     g.withhold = b.withhold;
+    g.check_tighten = b.check_tighten;
     g.src = b.src;
     g.k = b.k;
     const int t0 = blockIdx.x;

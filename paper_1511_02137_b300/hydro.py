@@ -14,9 +14,12 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libhydro.so")
+# HYDRO_CHECKED=1 in the environment selects the bounds-checked build of the same
+# library (build.build_checked(); tests only: it reports failed checks as HYDRO_ECHECK)
+LIB_PATH = os.path.join(_HERE, "libhydro_check.so" if os.environ.get("HYDRO_CHECKED") == "1" else "libhydro.so")
 
-HYDRO_OK, HYDRO_EINVAL, HYDRO_ENOMEM, HYDRO_ECUDA, HYDRO_EUNPHYSICAL, HYDRO_ECFL, HYDRO_ETIMEOUT, HYDRO_ESTATE = range(8)
+(HYDRO_OK, HYDRO_EINVAL, HYDRO_ENOMEM, HYDRO_ECUDA, HYDRO_EUNPHYSICAL, HYDRO_ECFL, HYDRO_ETIMEOUT, HYDRO_ESTATE,
+ HYDRO_ECHECK) = range(9)
 HYDRO_FP64, HYDRO_FP32, HYDRO_MIXED = 0, 1, 2
 HYDRO_OUTFLOW, HYDRO_PERIODIC = 0, 1
 HYDRO_PRIMITIVE, HYDRO_CONSERVED = 0, 1
@@ -37,14 +40,14 @@ class hydro_config(ctypes.Structure):
                 ("weno_eps", ctypes.c_double), ("cfl_limit", ctypes.c_double),
                 ("cuda_stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t), ("wait_limit_s", ctypes.c_double),
-                ("test_withhold_copies", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
+                ("test_withhold_copies", ctypes.c_int32), ("test_check_tighten", ctypes.c_int32)]
 
 
 class hydro_diag(ctypes.Structure):
     _fields_ = [("t", ctypes.c_double), ("steps", ctypes.c_int64), ("max_speed", ctypes.c_double),
                 ("floor_hits", ctypes.c_int64), ("dep_E", ctypes.c_double), ("dep_M", ctypes.c_double * 3),
                 ("njet", ctypes.c_int32), ("jet_cell", (ctypes.c_int32 * 3) * HYDRO_MAX_JETS),
-                ("status", ctypes.c_int32)]
+                ("status", ctypes.c_int32), ("check_site", ctypes.c_int32), ("check_index", ctypes.c_uint32)]
 
 
 class HydroError(RuntimeError):
@@ -237,7 +240,8 @@ def hydro_get_diag(ctx: Context) -> dict:
     _check(_lib().hydro_get_diag(ctx.handle, ctypes.byref(d)), "hydro_get_diag")
     return {"t": d.t, "steps": d.steps, "max_speed": d.max_speed, "floor_hits": d.floor_hits,
             "dep_E": d.dep_E, "dep_M": tuple(d.dep_M), "njet": d.njet,
-            "jet_cells": [tuple(d.jet_cell[i]) for i in range(d.njet)], "status": d.status}
+            "jet_cells": [tuple(d.jet_cell[i]) for i in range(d.njet)], "status": d.status,
+            "check_site": d.check_site, "check_index": d.check_index}
 
 
 def hydro_profile_enable(ctx: Context, on: bool = True) -> None:
@@ -368,7 +372,8 @@ def hydro_batch_get_diag(b: Batch, event: int) -> dict:
     _check(_lib().hydro_batch_get_diag(b.handle, event, ctypes.byref(d)), "hydro_batch_get_diag")
     return {"t": d.t, "steps": d.steps, "max_speed": d.max_speed, "floor_hits": d.floor_hits,
             "dep_E": d.dep_E, "dep_M": tuple(d.dep_M), "njet": d.njet,
-            "jet_cells": [tuple(d.jet_cell[i]) for i in range(d.njet)], "status": d.status}
+            "jet_cells": [tuple(d.jet_cell[i]) for i in range(d.njet)], "status": d.status,
+            "check_site": d.check_site, "check_index": d.check_index}
 
 
 def hydro_batch_destroy(b: Batch) -> None:

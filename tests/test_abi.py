@@ -41,6 +41,25 @@ def test_library_exports_every_declared_symbol(hy):
         assert hasattr(lib, name), name
 
 
+def test_bounds_checked_build_exports_the_same_symbols_and_takes_its_test_hook(hy):
+    """libhydro_check.so (-DHYDRO_CHECK) is the same library with bounds-checked
+    sweeps: it exports every declared call and accepts test_check_tighten = 1,
+    which the regular build rejects."""
+    from paper_1511_02137_b300 import build
+    lib = ctypes.CDLL(build.build_checked())
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+    n = ctypes.c_size_t()
+    c = hy.hydro_config_default(16, 16, 16, test_check_tighten=1)
+    lib.hydro_workspace_size.argtypes = [ctypes.POINTER(hy.hydro_config), ctypes.POINTER(ctypes.c_size_t)]
+    assert lib.hydro_workspace_size(ctypes.byref(c), ctypes.byref(n)) == hy.HYDRO_OK
+    assert hy._lib().hydro_workspace_size(ctypes.byref(c), ctypes.byref(n)) == hy.HYDRO_EINVAL
+    c.test_check_tighten = 2
+    assert lib.hydro_workspace_size(ctypes.byref(c), ctypes.byref(n)) == hy.HYDRO_EINVAL
+    lib.hydro_status_string.restype = ctypes.c_char_p
+    assert b"ECHECK" in lib.hydro_status_string(hy.HYDRO_ECHECK)
+
+
 def test_defaults_are_the_paper_values(hy):
     c = hy.hydro_config_default(256, 256, 256)
     assert (c.dx, c.dt, c.t0) == (0.1, 0.02, 1.0)
