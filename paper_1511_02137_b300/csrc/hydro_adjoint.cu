@@ -977,6 +977,7 @@ hydro_status hydro_adjoint_set_params(hydro_adjoint* a, double k_rad, double k_c
 }
 
 hydro_status hydro_adjoint_forward(hydro_adjoint* a, const double* d_prim5, double* J) {
+  NvtxRange call("hydro_adjoint_forward");
   if (!a || !d_prim5 || !J) return HYDRO_EINVAL;
   const size_t f5 = 5 * a->n * sizeof(double);
   cudaError_t err = cudaMemcpyAsync(a->prim, d_prim5, f5, cudaMemcpyDeviceToDevice, a->stream);
@@ -1020,6 +1021,7 @@ hydro_status hydro_adjoint_backward(hydro_adjoint* a, double dJ, double* grad_k_
                                     double* d_grad_e) {
   if (!a || !d_grad_e) return HYDRO_EINVAL;
   if (!a->forward_done) return HYDRO_ESTATE;
+  NvtxRange call("hydro_adjoint_backward");
   cudaError_t err = cudaMemsetAsync(a->kbar, 0, 2 * kMaxJets * sizeof(double), a->stream);
   // the fields past the combinations' kAdjFields stay zero (the seed zeroes lamA's)
   for (double* l : {a->lamB, a->lam0})

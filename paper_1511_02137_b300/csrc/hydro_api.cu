@@ -283,6 +283,8 @@ hydro_status hydro_add_jet(hydro_ctx* c, const double x0[3], const double dir[3]
 hydro_status hydro_step(hydro_ctx* c, int32_t nsteps) {
   if (!c || nsteps < 0) return HYDRO_EINVAL;
   if (!c->initialized) return HYDRO_ESTATE;
+  NvtxRange call("hydro_step");
+  static const char* const kStageName[3] = {"rk3 stage 1", "rk3 stage 2", "rk3 stage 3"};
   const hydro_config& g = c->cfg;
   static const double kStageC[3] = {0.0, 1.0, 0.5};              // stage times t_n + c_k dt
   static const double kStageW[3] = {1.0 / 6.0, 1.0 / 6.0, 4.0 / 6.0};  // weights of L in the step
@@ -316,6 +318,7 @@ hydro_status hydro_step(hydro_ctx* c, int32_t nsteps) {
     const int64_t n = c->steps;
     err = cudaMemsetAsync(&c->diag()->vmax_bits, 0, sizeof(unsigned long long), c->stream);
     for (int st = 0; st < 3 && err == cudaSuccess; ++st) {
+      NvtxRange stage(kStageName[st]);
       const double t = g.t0 + ((double)n + kStageC[st]) * g.dt;
       a.jets.n = c->njet;
       for (int j = 0; j < c->njet; ++j) {

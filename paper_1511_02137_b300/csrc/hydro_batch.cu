@@ -520,6 +520,7 @@ hydro_status hydro_batch_autotune(hydro_batch* b, int32_t variant_out[3], double
 }
 
 hydro_status hydro_batch_step(hydro_batch* b, int32_t nsteps) {
+  NvtxRange call("hydro_batch_step");
   if (!b || nsteps < 0) return HYDRO_EINVAL;
   if (!all_initialized(b)) return HYDRO_ESTATE;
   if (cudaStreamSynchronize(b->user) != cudaSuccess) return HYDRO_ECUDA;

@@ -6,6 +6,7 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "hydro.h"
 
@@ -78,6 +79,16 @@ inline unsigned long long wait_limit_ns(const hydro_config& c) {
 // the workspace alignment (256 bytes).
 enum : unsigned { kCheckGrid = 1u, kCheckWorkspace = 2u };
 bool config_valid(const hydro_config* c, unsigned what);
+
+// An NVTX range over a scope: names the library's calls and RK3 stages on a
+// profiler's timeline (ncu --nvtx, Nsight Systems); without an attached tool the
+// push and pop return at once.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Everything a sweep tile needs except the jet list.
 struct GridArgs {
