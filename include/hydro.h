@@ -125,7 +125,8 @@ typedef struct {
   int32_t status;               /* first error status raised on the device since creation */
   int32_t check_site;           /* bounds-checked build: the first failed check's site, 0 if none:
                                    1-3 a cell offset formed for the phase-3 operand copies, a
-                                   staged cell or an updated cell; 4 a TMA load, 5 a TMA store */
+                                   staged cell or an updated cell; 4 a TMA load, 5 a TMA store;
+                                   6-8 the adjoint's reverse sweeps (window, result, jet cell) */
   uint32_t check_index;         /* ... and the index it computed (for a TMA site: the coordinate) */
 } hydro_diag;
 

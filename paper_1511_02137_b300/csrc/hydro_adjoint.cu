@@ -32,6 +32,7 @@
 
 #include "hydro.h"
 #include "hydro_adjoint_math.cuh"
+#include "hydro_check.cuh"
 #include "hydro_internal.h"
 #include "hydro_math.cuh"
 
@@ -83,6 +84,7 @@ struct VjpArgs {
   double inv_dx, e_floor, eps_s;
   float inv_dx_f, eps_s_f, e_floor_f;   // the same rounded to FP32 on the host (mixed)
   double rad_per_k, coll_per_k, k_rad, k_coll, t4coef, inv_vol;
+  DevDiag* diag;        // status word (and, in the bounds-checked build, the failed check)
   JetStage jets;
 };
 
@@ -202,8 +204,9 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
       const int ga = a0 - 8 + s;
       const int gl = l0 + lane;
       const bool inside = ga >= 0 && ga < n_along && gl < n_lane;
-      const unsigned oa = offset(inside ? ga : 0, gl < n_lane ? gl : 0);
-      const unsigned o = offset(clampi(ga, n_along), gl < n_lane ? gl : n_lane - 1);
+      const unsigned oa = HYDRO_CELL_AT(offset(inside ? ga : 0, gl < n_lane ? gl : 0), N, kSiteAdjWindow, 0, p.diag);
+      const unsigned o =
+          HYDRO_CELL_AT(offset(clampi(ga, n_along), gl < n_lane ? gl : n_lane - 1), N, kSiteAdjWindow, 0, p.diag);
 #pragma unroll
       for (int q = 0; q < 5; ++q) {
         if constexpr (MIXED) av[rd][q] = inside ? p.lamf[q * N + oa] : P(0);
@@ -234,7 +237,7 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
         lane = c / SEG;
         j = c - lane * SEG;
         if (a0 + j >= n_along || l0 + lane >= n_lane) continue;
-        const unsigned o = offset(a0 + j, l0 + lane);
+        const unsigned o = HYDRO_CELL_AT(offset(a0 + j, l0 + lane), N, kSiteAdjResult, 0, p.diag);
         for (int k = 0; k < 5; ++k) r_out[k * N + o] = P(0);
       }
     }
@@ -417,7 +420,7 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
       if (own) rhob += P(0.5) * (P)own * sAhb[x] * Math::rcp((P)__popc(mask));
     }
     const int sc = sidx(lane, j + 8);
-    const unsigned o = offset(gcell, gl);
+    const unsigned o = HYDRO_CELL_AT(offset(gcell, gl), N, kSiteAdjResult, 0, p.diag);
     const P Mx = sU[NCS + sc], My = sU[2 * NCS + sc], Mz = sU[3 * NCS + sc], R = sU[4 * NCS + sc];
     P e, vx, vy, vz;
     C2PTape<P> tape;
@@ -469,7 +472,7 @@ __global__ void __launch_bounds__(adj_threads<PREC>()) vjp_kernel(const VjpArgs 
           continue;
         const int j = cl[2] - a0, lane = cl[0] - l0;
         const int sc = sidx(lane, j + 8);
-        const unsigned o = offset(cl[2], cl[0]);
+        const unsigned o = HYDRO_CELL_AT(offset(cl[2], cl[0]), N, kSiteAdjJet, 0, p.diag);
         // S0 = inv_vol (k_rad C T^3 l / hc^2 + k_coll C T^2 / hc), T = (e t4)^(1/4): S = (S0, n S0, 0).
         // T comes from the recovery the forward used at the jet cell: FP64 from the
         // FP64 state, or (mixed) FP32 from the shadow; its derivative in FP64.
@@ -776,6 +779,7 @@ cudaError_t vjp(hydro_adjoint* a, int64_t n, int st, const double* Uk, const flo
   p.lam = lam;
   p.r = a->r;
   p.kbar = a->kbar;
+  p.diag = a->diag;
   p.ascale = ascale;
   p.nx = g.nx;
   p.ny = g.ny;
@@ -1092,9 +1096,13 @@ hydro_status hydro_adjoint_backward(hydro_adjoint* a, double dJ, double* grad_k_
     err = cudaGetLastError();
   }
   double kb[2 * kMaxJets];
+  int status = 0;
   if (err == cudaSuccess) err = cudaMemcpyAsync(kb, a->kbar, sizeof(kb), cudaMemcpyDeviceToHost, a->stream);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(&status, &a->diag->status, sizeof(int), cudaMemcpyDeviceToHost, a->stream);
   if (err == cudaSuccess) err = cudaStreamSynchronize(a->stream);
   if (err != cudaSuccess) return HYDRO_ECUDA;
+  if (status) return (hydro_status)status;   // raised by the recomputation or, in the checked build, a check
   double gr = 0.0, gc = 0.0;
   for (int j = 0; j < a->njet; ++j) {
     gr += kb[2 * j];

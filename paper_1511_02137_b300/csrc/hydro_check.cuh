@@ -1,15 +1,16 @@
-// Bounds checks of the sweep tiles, compiled in with -DHYDRO_CHECK (the library
-// libhydro_check.so that build.build_checked() makes) as a stand-in for a memory
-// checker.  Every global-memory access of a tile is q N + o for a field q below
-// the buffer's field count (5, or 6 for the mixed shadow) and a cell offset o, so
-// checking o < N at the three places a tile forms it bounds every access; TMA
-// copies are checked against the copy rules (innermost coordinate a multiple of
-// 16 bytes; stores from non-negative coordinates).  A failed check records its
-// site and the offending value in the diagnostics block, sets HYDRO_ECHECK, and
-// keeps the access inside its buffer (the offset is redirected to the last
-// allowed cell) or skips the copy (its bounded wait then runs out).  Shared-memory
-// indices are not checked here: they follow from the compile-time tile layout.
-// In the regular build the checks compile to nothing.
+// Bounds checks of the sweep tiles and of the adjoint's reverse sweeps, compiled
+// in with -DHYDRO_CHECK (the library libhydro_check.so that build.build_checked()
+// makes) as a stand-in for a memory checker.  Every global-memory access of a
+// tile is q N + o for a field q below the buffer's field count (5, or 6 for the
+// mixed shadow) and a cell offset o, so checking o < N at the places a tile forms
+// it bounds every access; TMA copies are checked against the copy rules
+// (innermost coordinate a multiple of 16 bytes; stores from non-negative
+// coordinates).  A failed check records its site and the offending value in the
+// diagnostics block, sets HYDRO_ECHECK, and keeps the access inside its buffer
+// (the offset is redirected to the last allowed cell) or skips the copy (its
+// bounded wait then runs out).  Shared-memory indices are not checked here: they
+// follow from the compile-time tile layout.  In the regular build the checks
+// compile to nothing.
 #pragma once
 
 #include "hydro_internal.h"
@@ -23,6 +24,9 @@ enum CheckSite : int {
   kSiteUpdate = 3,     // phase 3: cell offset of an updated cell (accumulator, result, shadow, jet)
   kSiteTmaLoad = 4,    // a TMA load whose innermost coordinate is not at a 16-byte offset
   kSiteTmaStore = 5,   // a TMA store from such a coordinate or from a negative one
+  kSiteAdjWindow = 6,  // adjoint reverse sweep: cell offset of a window position (adjoint, state, r)
+  kSiteAdjResult = 7,  // adjoint reverse sweep: cell offset of an updated cell's result
+  kSiteAdjJet = 8,     // adjoint reverse sweep: the jet cell's offset
 };
 
 #ifdef HYDRO_CHECK
@@ -48,11 +52,13 @@ __device__ __forceinline__ bool checked_tma(int x, int esize, int c1, int c2, bo
   return ok;
 }
 
-#define HYDRO_CELL(o, n, site) ::hydro::checked_cell((o), (n), a.check_tighten, (site), a.diag)
+#define HYDRO_CELL_AT(o, n, site, tighten, diag) ::hydro::checked_cell((o), (n), (tighten), (site), (diag))
 #define HYDRO_TMA_OK(x, esize, c1, c2, store) ::hydro::checked_tma((x), (esize), (c1), (c2), (store), a.diag)
 #else
-#define HYDRO_CELL(o, n, site) (o)
+#define HYDRO_CELL_AT(o, n, site, tighten, diag) (o)
 #define HYDRO_TMA_OK(x, esize, c1, c2, store) true
 #endif
+// the sweep tiles' form: the grid arguments `a` carry the diagnostics block and the test hook
+#define HYDRO_CELL(o, n, site) HYDRO_CELL_AT((o), (n), (site), a.check_tighten, a.diag)
 
 }  // namespace hydro

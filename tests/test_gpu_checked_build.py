@@ -6,7 +6,9 @@ HYDRO_ECHECK with its site and value, and the access is kept inside its buffer.
 It stands in for a memory checker on this pool.  A child process loads the
 checked library (HYDRO_CHECKED=1) and runs every sweep configuration on ragged
 grids: precisions, WENO7 and WENO5, outflow and periodic boundaries, a jet, a
-batch of two grids and the allocation-free step.  No check may fail, and the
+batch of two grids, the allocation-free step and the adjoint (FP64 and mixed:
+forward with checkpoints, recomputation and the reverse sweeps, which carry
+their own checks).  No check may fail, and the
 fields must equal the regular library's bit for bit (the checks add no
 arithmetic).  The test hook that halves every checked bound then shows that
 failures are recorded: HYDRO_ECHECK with a site and an offset in the upper half
@@ -70,6 +72,21 @@ def _run_cases(hy, W):
     rc = fn(ctypes.byref(c), state.data_ptr(), 0, 2, None, 0, ctypes.byref(d))
     out["noalloc-fp64"] = (state.cpu().numpy().reshape(U0.shape),
                            {"status": rc or d.status, "check_site": d.check_site, "check_index": d.check_index})
+    # the adjoint (forward with checkpoints, recomputation, reverse sweeps): J and its gradients
+    from paper_1511_02137_b300 import adjoint as A
+    jet = W.JetSpec((-0.6, 0.0, 0.0), (1.0, 0.0, 0.0), 1.0)
+    wa = W.Workload(name="adjoint", n=(24, 20, 16), steps=6, sigma=(0.8, 1.0, 1.2), jets=(jet,))
+    pa = W.ellipsoidal_primitives(wa)
+    for p in ("fp64", "mixed"):
+        run = A.ConeEnergyRun(hy.hydro_config_default(*wa.n, precision=p), wa.steps, 2, wa.jets,
+                              torch.from_numpy(pa[1:].copy()).cuda(), apex=jet.x0, axis=jet.direction)
+        e = torch.from_numpy(pa[0].copy()).cuda().requires_grad_(True)
+        kr = torch.tensor(4.0, dtype=torch.float64, device="cuda", requires_grad=True)
+        kc = torch.tensor(2.5, dtype=torch.float64, device="cuda", requires_grad=True)
+        J = A.cone_energy(e, kr, kc, run)
+        J.backward()   # raises on any status the library returns (HYDRO_ECHECK included)
+        grads = np.concatenate([[J.item(), kr.grad.item(), kc.grad.item()], e.grad.cpu().numpy().ravel()])
+        out[f"adjoint-{p}"] = (grads, {"status": 0, "check_site": 0})
     return out
 
 
