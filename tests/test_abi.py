@@ -252,3 +252,27 @@ def test_eval_math_and_peak_reject_bad_arguments_without_touching_the_device(hy)
     m = ctypes.c_double()
     assert lib.hydro_alu_peak(7, 10, None, ctypes.byref(f), ctypes.byref(m)) == hy.HYDRO_EINVAL
     assert lib.hydro_alu_peak(0, 0, None, ctypes.byref(f), ctypes.byref(m)) == hy.HYDRO_EINVAL
+
+
+def test_field_buffer_marshalling_checks_type_size_and_layout(hy):
+    """The binding hands the C ABI a pointer only for a C-contiguous float64
+    buffer of exactly 5 x cells values: numpy arrays and CPU tensors (and CUDA
+    tensors on the context's device, checked on the GPU); anything else is
+    refused before the call."""
+    import numpy as np
+    import torch
+    n = 5 * 4 * 3 * 2
+    good = np.zeros(n)
+    assert hy._host_ptr(good, n, True) == good.ctypes.data
+    t = torch.zeros(n, dtype=torch.float64)
+    assert hy._host_ptr(t, n, False) == t.data_ptr()
+    for bad in (np.zeros(n, dtype=np.float32), np.zeros(n + 1), np.zeros((n, 2))[:, 0],
+                torch.zeros(n, dtype=torch.float32), torch.zeros(2 * n, dtype=torch.float64)[::2]):
+        with pytest.raises(ValueError):
+            hy._host_ptr(bad, n, False)
+    ro = np.zeros(n)
+    ro.setflags(write=False)
+    with pytest.raises(ValueError):
+        hy._host_ptr(ro, n, True)
+    with pytest.raises(TypeError):
+        hy._host_ptr([0.0] * n, n, False)
