@@ -17,7 +17,8 @@
  *  - Cell (i, j, k) has centre ((i + 1/2 - nx/2) dx, (j + 1/2 - ny/2) dx,
  *    (k + 1/2 - nz/2) dx): the grid is centred on the origin.
  *  - Every function returns a hydro_status and never aborts, prints or throws.
- *  - Host buffers are owned by the caller and only used during the call.
+ *  - Field buffers (host, or device where a call says so) are owned by the
+ *    caller and only used during the call.
  *  - All device work is issued on the stream given in hydro_config; every
  *    call that returns data synchronises that stream before returning.  The
  *    library does not link PyTorch: in C a NULL stream is the legacy default
@@ -135,8 +136,10 @@ typedef struct {
 void hydro_config_default(hydro_config* cfg, int32_t nx, int32_t ny, int32_t nz);
 
 /* Bytes of device workspace a context with this configuration needs: three
- * state copies and one right-hand-side accumulator (5 fields each) plus a
- * small diagnostics block.  HYDRO_EINVAL for an invalid configuration. */
+ * state copies and one right-hand-side accumulator (5 fields each), in FP64 the
+ * primitive cache of the sweeps (5 fields), in mixed precision the FP32
+ * shadows of the three states (6 fields each), and a small diagnostics block.
+ * HYDRO_EINVAL for an invalid configuration. */
 hydro_status hydro_workspace_size(const hydro_config* cfg, size_t* bytes);
 
 /* Validates cfg, sets up device memory and returns a new context in *out.
@@ -174,7 +177,8 @@ hydro_status hydro_add_jet(hydro_ctx* ctx, const double x0[3], const double dir[
  * first error raised: HYDRO_EUNPHYSICAL (NaN/Inf), HYDRO_ECFL, HYDRO_ECUDA,
  * HYDRO_ETIMEOUT (a bounded wait ran out: the state is invalid until the
  * next hydro_set_initial; the CUDA context stays usable); HYDRO_ESTATE before
- * hydro_set_initial; HYDRO_EINVAL for nsteps < 0. */
+ * hydro_set_initial; HYDRO_EINVAL for nsteps < 0; in the bounds-checked build
+ * also HYDRO_ECHECK. */
 hydro_status hydro_step(hydro_ctx* ctx, int32_t nsteps);
 
 /* Copies the current state to host5 as FP64 (FP32 storage is widened):
