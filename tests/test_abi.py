@@ -276,3 +276,40 @@ def test_field_buffer_marshalling_checks_type_size_and_layout(hy):
         hy._host_ptr(ro, n, True)
     with pytest.raises(TypeError):
         hy._host_ptr([0.0] * n, n, False)
+
+
+def test_header_compiles_as_c99_and_a_c_program_links_and_runs(hy, tmp_path):
+    """include/hydro.h is plain C: a C99 program that includes it, links
+    libhydro.so and calls the host-only entry points (defaults, workspace size,
+    validation, status strings) builds with gcc -Werror and runs without a GPU."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_hydro.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include <string.h>
+#include "hydro.h"
+int main(void) {
+  hydro_config c;
+  size_t bytes = 0;
+  hydro_config_default(&c, 64, 48, 32);
+  if (c.weno_order != 7 || c.precision != HYDRO_FP64 || c.dx != 0.1 || c.dt != 0.02) return 1;
+  if (hydro_workspace_size(&c, &bytes) != HYDRO_OK || bytes < 4u * 5u * 64u * 48u * 32u * 8u) return 2;
+  c.nx = 0;
+  if (hydro_workspace_size(&c, &bytes) != HYDRO_EINVAL) return 3;
+  if (strstr(hydro_status_string(HYDRO_ETIMEOUT), "HYDRO_ETIMEOUT") == NULL) return 4;
+  if (hydro_create(NULL, NULL) != HYDRO_EINVAL) return 5;
+  printf("ok %zu\n", bytes);
+  return 0;
+}
+""")
+    exe = tmp_path / "use_hydro"
+    libdir = os.path.dirname(hy.LIB_PATH)
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-o", str(exe), "-L", libdir, "-l:libhydro.so", "-Wl,-rpath," + libdir],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.startswith("ok "), (r.returncode, r.stdout, r.stderr)
