@@ -9,6 +9,7 @@ jump conditions of the shock for p = e/3 (textbook relativistic gas dynamics).
 from __future__ import annotations
 
 import math
+import warnings
 
 import numpy as np
 from scipy import optimize
@@ -50,7 +51,11 @@ def primitives_by_solve(U):
         return conserved(e, np.array([ux, uy, uz]))[:4] - U[:4]
 
     guess = np.array([U[0], 0.0, 0.0, 0.0])
-    sol = optimize.fsolve(resid, guess, xtol=1e-14, maxfev=10000)
+    with warnings.catch_warnings():
+        # at xtol = 1e-14 fsolve reports that it cannot improve further once the
+        # residual is at rounding level: that is the converged answer here
+        warnings.simplefilter("ignore", RuntimeWarning)
+        sol = optimize.fsolve(resid, guess, xtol=1e-14, maxfev=10000)
     gamma = math.sqrt(1.0 + sol[1:] @ sol[1:])
     return sol[0], sol[1:], U[4] / gamma
 
