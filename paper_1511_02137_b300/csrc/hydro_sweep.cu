@@ -4,12 +4,15 @@
 // combines it with the step's start state.  It runs as three sweeps, one per
 // axis, each a tiled kernel with one updated cell per thread:
 //
-//   phase 0  (FP32-flux y and z sweeps) start copying the tile's phase-3
-//            operands (accumulator, step state, mixed: stage state) into
-//            shared memory: one TMA box each, or per-thread cp.async copies;
+//   phase 0  (FP32-flux y and z sweeps, and the mixed x sweep) start copying
+//            the tile's phase-3 operands (accumulator; z: the step state U0)
+//            into shared memory: one TMA box each, or per-thread cp.async
+//            copies;
 //   phase 1  stage a halo-padded tile of cells into shared memory (interior
 //            tiles as one TMA box, edge tiles through clamped or wrapped
-//            coalesced loads), recover primitives in closed form, and keep U,
+//            coalesced loads; mixed precision stages the FP32 shadow of the
+//            stage state), recover primitives in closed form (the FP64 y and z
+//            sweeps read them from the x sweep's cache instead), and keep U,
 //            the half physical flux F_d/2 and the spectral radius rho_d of
 //            every cell;
 //   phase 2  one thread per interface: alpha = max rho_d over the interface's
@@ -20,7 +23,10 @@
 //            right-hand-side accumulator (x: write, y: add; FP32-flux tiles
 //            store the box by TMA); the z sweep adds the jet source at the jet
 //            cells and writes the stage combination a U0 + b (U + dt L) in
-//            storage precision.
+//            storage precision (mixed precision keeps the stage states as FP32
+//            increments over U0 in the accumulator: its z sweep forms U0 + delta
+//            in FP64 for the next FP32 shadow and, at the last stage, the new
+//            state).
 //
 // Ghost cells are never stored: halo loads clamp the index (outflow,
 // zero-gradient) or wrap it (periodic).  The x sweep of each stage counts
@@ -224,7 +230,8 @@ struct Prefetch {
   static constexpr int state_words = on && DIR == 2 ? (PREC == kMixedShadow ? 10 : 5) : 0;
 };
 
-// Single-grid WENO7 sweeps stage interior tiles with one TMA copy.  FP64 copies
+// The sweeps stage interior tiles with one TMA copy (single grids and batches,
+// WENO7 and WENO5; WENO5 x tiles excepted, see stage_by_tma).  FP64 copies
 // straight into the tile's U array; FP32 tiles interleave U with F_d/2, so their
 // copy lands in a separate staging box that phase 1 reads; the mixed shadow's x
 // and y sweeps copy the shadow the same way.  The mixed z tile, which also holds
