@@ -230,8 +230,9 @@ struct Prefetch {
   static constexpr int state_words = on && DIR == 2 ? (PREC == kMixedShadow ? 10 : 5) : 0;
 };
 
-// The sweeps stage interior tiles with one TMA copy (single grids and batches,
-// WENO7 and WENO5; WENO5 x tiles excepted, see stage_by_tma).  FP64 copies
+// The sweeps stage interior tiles with one TMA copy (single grids in WENO7 and
+// WENO5, whose x tiles are the exception, see stage_by_tma; batches, which run
+// WENO7).  FP64 copies
 // straight into the tile's U array; FP32 tiles interleave U with F_d/2, so their
 // copy lands in a separate staging box that phase 1 reads; the mixed shadow's x
 // and y sweeps copy the shadow the same way.  The mixed z tile, which also holds
