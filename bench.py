@@ -19,7 +19,11 @@ are sampled through NVML every 25 ms during each timed region.  The ALU
 peaks that the roofline fractions divide by are measured in the same run by
 FMA-throughput kernels (hydro_alu_peak).  With --gpus N > 1 (torchrun) every
 rank runs an independent replica (the path is not sharded) and the time is
-the max over ranks.
+the max over ranks.  The line also carries "e2e" (the same steps through the
+C ABI from pinned host buffers, copies included), "cpu_baseline" (the oracle
+on the host cores), "adjoint" (128^3 x 50 steps, backward / forward cost),
+"batched" (the 64-event ensemble) and "weno5" (the WENO5 variant of the
+workload), each with its own roofline where it has one.
 
 --impl reference times the FP64 CPU oracle on the host cores instead (one RK3
 step of a 128^3 sub-grid of the same workload per bench step).
