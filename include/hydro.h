@@ -325,13 +325,16 @@ hydro_status hydro_adjoint_set_params(hydro_adjoint* a, double k_rad, double k_c
 
 /* Runs the forward steps from the primitive fields in device memory d_prim5
  * (5 x nx*ny*nz doubles: e, u^x, u^y, u^z, n), keeping checkpoints, and
- * returns the observable in *J (host). */
+ * returns the observable in *J (host).  Statuses as hydro_step (a NaN state,
+ * HYDRO_EUNPHYSICAL; HYDRO_EINVAL for a bad initial state). */
 hydro_status hydro_adjoint_forward(hydro_adjoint* a, const double* d_prim5, double* J);
 
 /* Reverse sweep for an upstream derivative dJ (1 for the plain gradient):
  * writes dJ/dk_rad and dJ/dk_coll to the host doubles (may be NULL) and
  * dJ/de(x) at fixed u^i and n to d_grad_e (device, nx*ny*nz doubles).
- * HYDRO_ESTATE before hydro_adjoint_forward. */
+ * HYDRO_ESTATE before hydro_adjoint_forward; a status the device raised while
+ * recomputing the checkpointed segments (as hydro_step; in the bounds-checked
+ * build also HYDRO_ECHECK from the reverse sweeps). */
 hydro_status hydro_adjoint_backward(hydro_adjoint* a, double dJ, double* grad_k_rad, double* grad_k_coll,
                                     double* d_grad_e);
 
