@@ -37,3 +37,20 @@ def gpu_context(hy, w, precision="fp64", boundary="outflow", order=7, eps=1e-6, 
     for j in w.jets:
         hy.hydro_add_jet(ctx, j.x0, j.direction, j.t_start)
     return ctx
+
+
+def cone_mask(n, dx, apex, axis=(1.0, 0.0, 0.0), half_angle_deg=30.0, rmax=3.0):
+    """Cells [nz, ny, nx] whose centres lie in the cone of the adjoint's
+    observable: within rmax of the apex and within half_angle_deg of the axis
+    (centre of cell i at (i + 1/2 - n/2) dx on each axis)."""
+    import math
+    nx, ny, nz = n
+    a = np.asarray(axis, dtype=np.float64)
+    a = a / np.linalg.norm(a)
+    x = (np.arange(nx) + 0.5 - nx / 2) * dx - apex[0]
+    y = (np.arange(ny) + 0.5 - ny / 2) * dx - apex[1]
+    z = (np.arange(nz) + 0.5 - nz / 2) * dx - apex[2]
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    r2 = X * X + Y * Y + Z * Z
+    along = a[0] * X + a[1] * Y + a[2] * Z
+    return (r2 < rmax * rmax) & (along >= math.cos(math.radians(half_angle_deg)) * np.sqrt(r2))

@@ -9,12 +9,13 @@ mixed-precision adjoint (FP32 flux arithmetic) is checked against the same
 FP64 finite differences: central differences of its own FP32-flux forward at
 a relative step of 1e-6 would be dominated by FP32 rounding.
 """
-import math
 import statistics
 import time
 
 import numpy as np
 import pytest
+
+from harness import cone_mask
 
 pytestmark = pytest.mark.gpu
 
@@ -96,14 +97,7 @@ def test_adjoint_against_oracle_central_differences(env, orc):
     n, steps = (16, 14, 12), 4
     w, prim, run, e = _problem(env, n, steps=steps, every=3, sigma=(0.7, 0.8, 0.9), jet_x0=(-0.5, 0.0, 0.0))
     J0, ge, gkr, gkc = _value_and_grad(env, run, e)
-    nx, ny, nz = n
-    apex = np.array(w.jets[0].x0)
-    x = (np.arange(nx) + 0.5 - nx / 2) * w.dx - apex[0]
-    y = (np.arange(ny) + 0.5 - ny / 2) * w.dx - apex[1]
-    z = (np.arange(nz) + 0.5 - nz / 2) * w.dx - apex[2]
-    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
-    r2 = X * X + Y * Y + Z * Z
-    mask = (r2 < 9.0) & (X >= math.cos(math.radians(30.0)) * np.sqrt(r2))
+    mask = cone_mask(n, w.dx, w.jets[0].x0)
     jets = [orc.Jet(j.x0, j.direction, j.t_start) for j in w.jets]
 
     def J_oracle(e_field, kr, kc):
@@ -147,14 +141,7 @@ def test_adjoint_forward_is_the_step_of_the_context_api(env, precision, n):
     hy.hydro_step(ctx, steps)
     U = hy.hydro_read_fields(ctx, hy.HYDRO_CONSERVED)
     hy.hydro_destroy(ctx)
-    nx, ny, nz = n
-    apex = np.array(w.jets[0].x0)
-    x = (np.arange(nx) + 0.5 - nx / 2) * w.dx - apex[0]
-    y = (np.arange(ny) + 0.5 - ny / 2) * w.dx - apex[1]
-    z = (np.arange(nz) + 0.5 - nz / 2) * w.dx - apex[2]
-    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
-    r2 = X * X + Y * Y + Z * Z
-    mask = (r2 < 9.0) & (X >= math.cos(math.radians(30.0)) * np.sqrt(r2))
+    mask = cone_mask(n, w.dx, w.jets[0].x0)
     J_ctx = float(U[0][mask].sum()) * w.dx ** 3
     print(f"{precision} {n}: J adjoint {J!r}, context {J_ctx!r}, relative {abs(J / J_ctx - 1):.1e}")
     assert abs(J / J_ctx - 1) < 1e-13
