@@ -674,10 +674,6 @@ struct hydro_adjoint {
 
 namespace {
 
-const double kStageC[3] = {0.0, 1.0, 0.5};
-const double kStageW[3] = {1.0 / 6.0, 1.0 / 6.0, 4.0 / 6.0};
-const double kA[3] = {0.0, 0.75, 1.0 / 3.0};
-const double kB[3] = {1.0, 0.25, 2.0 / 3.0};
 constexpr unsigned kConeBlocks = 512;
 
 void jet_stage(const hydro_adjoint* a, double t, JetStage& js) {
@@ -685,17 +681,8 @@ void jet_stage(const hydro_adjoint* a, double t, JetStage& js) {
   const int N[3] = {a->cfg.nx, a->cfg.ny, a->cfg.nz};
   js.n = a->njet;
   for (int j = 0; j < a->njet; ++j) {
-    const double l = t - a->jt[j];
-    js.ell[j] = l;
-    bool inside = (l >= 0.0);
-    for (int ax = 0; ax < 3; ++ax) {
-      const double x = a->jx0[j][ax] + a->jn[j][ax] * l;
-      const double fl = std::floor(x / a->cfg.dx + 0.5 * (double)N[ax]);
-      if (!(fl >= 0.0 && fl < (double)N[ax])) inside = false;
-      js.cell[j][ax] = (fl >= 0.0 && fl < (double)N[ax]) ? (int)fl : -1;
-      js.dir[j][ax] = a->jn[j][ax];
-    }
-    if (!inside) js.cell[j][0] = js.cell[j][1] = js.cell[j][2] = -1;
+    jet_cell_at(a->jx0[j], a->jn[j], a->jt[j], t, a->cfg.dx, N, js.cell[j], &js.ell[j]);
+    for (int ax = 0; ax < 3; ++ax) js.dir[j][ax] = a->jn[j][ax];
   }
 }
 
@@ -748,8 +735,8 @@ cudaError_t forward_step(hydro_adjoint* a, int64_t n, AdjSet& S, int i, const do
     tma = encode_sweep_tmaps(g.precision, 7, bufs, S.rhs, g.nx, g.ny, g.nz, maps);
   }
   for (int st = 0; st < 3 && err == cudaSuccess; ++st) {
-    jet_stage(a, g.t0 + ((double)n + kStageC[st]) * g.dt, s.jets);
-    s.src.wdt_vol = g.dt * kStageW[st] * vol;
+    jet_stage(a, g.t0 + ((double)n + kRK3C[st]) * g.dt, s.jets);
+    s.src.wdt_vol = g.dt * kRK3W[st] * vol;
     if (mixed) {   // stage states as FP32 increments over U0 in the accumulator
       s.U = in;
       s.Uout = st == 2 ? out : nullptr;
@@ -759,8 +746,8 @@ cudaError_t forward_step(hydro_adjoint* a, int64_t n, AdjSet& S, int i, const do
       s.U = st == 0 ? in : S.stages[2 * i + st - 1];
       s.Uout = st == 2 ? out : S.stages[2 * i + st];
     }
-    s.a = kA[st];
-    s.b = kB[st];
+    s.a = kRK3A[st];
+    s.b = kRK3B[st];
     for (int d = 0; d < 3 && err == cudaSuccess; ++d)
       err = launch_sweep(g.precision, 7, d, s, stream, tma ? &maps[st][d] : nullptr);
   }
@@ -796,7 +783,7 @@ cudaError_t vjp(hydro_adjoint* a, int64_t n, int st, const double* Uk, const flo
   p.k_coll = g.k_coll;
   p.t4coef = g.hbarc * g.hbarc * g.hbarc / (M_PI * M_PI / 30.0 * g.dof);
   p.inv_vol = 1.0 / (g.dx * g.dx * g.dx);
-  jet_stage(a, g.t0 + ((double)n + kStageC[st]) * g.dt, p.jets);
+  jet_stage(a, g.t0 + ((double)n + kRK3C[st]) * g.dt, p.jets);
   cudaError_t err;
   if (g.precision == HYDRO_MIXED) {
     p.lamf = a->lamf;
@@ -821,14 +808,14 @@ constexpr int kAdjFields = 4;
 
 cudaError_t combine(hydro_adjoint* a, int mode, int st) {
   const size_t nf = kAdjFields * a->n;
-  const double fscale = kB[st == 0 ? 2 : st - 1] * a->cfg.dt;
+  const double fscale = kRK3B[st == 0 ? 2 : st - 1] * a->cfg.dt;
   if (a->cfg.precision == HYDRO_MIXED)
     adj_combine_kernel<float><<<grid_1d(nf), 256, 0, a->stream>>>(
-        mode, kA[st], kB[st], a->lamA, a->lamB, a->lam0, reinterpret_cast<const float*>(a->r), nf, a->lamf,
+        mode, kRK3A[st], kRK3B[st], a->lamA, a->lamB, a->lam0, reinterpret_cast<const float*>(a->r), nf, a->lamf,
         (float)fscale);
   else
-    adj_combine_kernel<double><<<grid_1d(nf), 256, 0, a->stream>>>(mode, kA[st], kB[st], a->lamA, a->lamB, a->lam0,
-                                                                   a->r, nf, nullptr, 0.0f);
+    adj_combine_kernel<double><<<grid_1d(nf), 256, 0, a->stream>>>(
+        mode, kRK3A[st], kRK3B[st], a->lamA, a->lamB, a->lam0, a->r, nf, nullptr, 0.0f);
   return cudaGetLastError();
 }
 
@@ -1035,7 +1022,7 @@ hydro_status hydro_adjoint_backward(hydro_adjoint* a, double dJ, double* grad_k_
     cone_seed_kernel<<<grid_1d(a->n), 256, 0, a->stream>>>(a->lamA, a->cone, dJ);
     err = cudaGetLastError();
     if (err == cudaSuccess && a->lamf) {
-      scale_to_float_kernel<<<grid_1d(5 * a->n), 256, 0, a->stream>>>(a->lamA, a->lamf, kB[2] * a->cfg.dt, 5 * a->n);
+      scale_to_float_kernel<<<grid_1d(5 * a->n), 256, 0, a->stream>>>(a->lamA, a->lamf, kRK3B[2] * a->cfg.dt, 5 * a->n);
       err = cudaGetLastError();
     }
   }
@@ -1079,13 +1066,13 @@ hydro_status hydro_adjoint_backward(hydro_adjoint* a, double dJ, double* grad_k_
       };
       auto Sk = [&](int st) -> const float* { return mixed ? S.shd[3 * s + st] : nullptr; };
       // stage 3: U = 1/3 U0 + 2/3 (U2 + dt L(U2))
-      err = vjp(a, n, 2, Uk(2), Sk(2), a->lamA, kB[2] * a->cfg.dt);
+      err = vjp(a, n, 2, Uk(2), Sk(2), a->lamA, kRK3B[2] * a->cfg.dt);
       if (err == cudaSuccess) err = combine(a, 0, 2);
       // stage 2: U2 = 3/4 U0 + 1/4 (U1 + dt L(U1))
-      if (err == cudaSuccess) err = vjp(a, n, 1, Uk(1), Sk(1), a->lamB, kB[1] * a->cfg.dt);
+      if (err == cudaSuccess) err = vjp(a, n, 1, Uk(1), Sk(1), a->lamB, kRK3B[1] * a->cfg.dt);
       if (err == cudaSuccess) err = combine(a, 1, 1);
       // stage 1: U1 = U0 + dt L(U0)
-      if (err == cudaSuccess) err = vjp(a, n, 0, Uk(0), Sk(0), a->lamA, kB[0] * a->cfg.dt);
+      if (err == cudaSuccess) err = vjp(a, n, 0, Uk(0), Sk(0), a->lamA, kRK3B[0] * a->cfg.dt);
       if (err == cudaSuccess) err = combine(a, 2, 0);
       std::swap(a->lamA, a->lam0);   // adjoint of the step's input becomes the next output adjoint
     }

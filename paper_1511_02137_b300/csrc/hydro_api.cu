@@ -150,19 +150,8 @@ hydro_status prof_resolve(hydro_ctx* c) {
 // index floor(x/dx + N/2) per axis.  Returns false when the jet has not started
 // or lies outside the grid.
 bool jet_cell(const hydro_ctx* c, int j, double t, int cell[3], double* ell) {
-  const double l = t - c->jt[j];
-  *ell = l;
   const int N[3] = {c->cfg.nx, c->cfg.ny, c->cfg.nz};
-  bool inside = (l >= 0.0);
-  for (int a = 0; a < 3; ++a) {
-    const double x = c->jx0[j][a] + c->jn[j][a] * l;
-    const double s = x / c->cfg.dx + 0.5 * (double)N[a];
-    const double fl = std::floor(s);
-    if (!(fl >= 0.0 && fl < (double)N[a])) inside = false;
-    cell[a] = (int)(fl >= 0.0 && fl < (double)N[a] ? fl : -1.0);
-  }
-  if (!inside) cell[0] = cell[1] = cell[2] = -1;
-  return inside;
+  return jet_cell_at(c->jx0[j], c->jn[j], c->jt[j], t, c->cfg.dx, N, cell, ell);
 }
 
 }  // namespace
@@ -286,10 +275,6 @@ hydro_status hydro_step(hydro_ctx* c, int32_t nsteps) {
   NvtxRange call("hydro_step");
   static const char* const kStageName[3] = {"rk3 stage 1", "rk3 stage 2", "rk3 stage 3"};
   const hydro_config& g = c->cfg;
-  static const double kStageC[3] = {0.0, 1.0, 0.5};              // stage times t_n + c_k dt
-  static const double kStageW[3] = {1.0 / 6.0, 1.0 / 6.0, 4.0 / 6.0};  // weights of L in the step
-  static const double kA[3] = {0.0, 0.75, 1.0 / 3.0};
-  static const double kB[3] = {1.0, 0.25, 2.0 / 3.0};
   void* U[3] = {c->U(c->lay.u0), c->U(c->lay.u1), c->U(c->lay.u2)};
   SweepArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -319,13 +304,13 @@ hydro_status hydro_step(hydro_ctx* c, int32_t nsteps) {
     err = cudaMemsetAsync(&c->diag()->vmax_bits, 0, sizeof(unsigned long long), c->stream);
     for (int st = 0; st < 3 && err == cudaSuccess; ++st) {
       NvtxRange stage(kStageName[st]);
-      const double t = g.t0 + ((double)n + kStageC[st]) * g.dt;
+      const double t = g.t0 + ((double)n + kRK3C[st]) * g.dt;
       a.jets.n = c->njet;
       for (int j = 0; j < c->njet; ++j) {
         jet_cell(c, j, t, a.jets.cell[j], &a.jets.ell[j]);
         for (int d = 0; d < 3; ++d) a.jets.dir[j][d] = c->jn[j][d];
       }
-      a.src.wdt_vol = g.dt * kStageW[st] * vol;
+      a.src.wdt_vol = g.dt * kRK3W[st] * vol;
       a.U = U[st];
       a.Uout = (st == 2) ? U[0] : U[st + 1];
       a.S = c->shadow(st);                        // NULL unless mixed precision
@@ -336,8 +321,8 @@ hydro_status hydro_step(hydro_ctx* c, int32_t nsteps) {
         a.U = U[0];
         a.Uout = st == 2 ? U[0] : nullptr;
       }
-      a.a = kA[st];
-      a.b = kB[st];
+      a.a = kRK3A[st];
+      a.b = kRK3B[st];
       a.reduce_speed = (st == 0);
       for (int dir = 0; dir < 3 && err == cudaSuccess; ++dir) {
         a.count_floors = (dir == 0);

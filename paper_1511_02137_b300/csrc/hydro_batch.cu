@@ -230,24 +230,11 @@ void fill_jet_stage(const hydro_batch* b, int e, double t, JetStage& js) {
   const int N[3] = {b->dims[3 * e], b->dims[3 * e + 1], b->dims[3 * e + 2]};
   js.n = (int)J.size();
   for (int j = 0; j < js.n; ++j) {
-    const double l = t - J[j].t_start;
-    js.ell[j] = l;
-    bool inside = (l >= 0.0);
-    for (int a = 0; a < 3; ++a) {
-      const double x = J[j].x0[a] + J[j].n[a] * l;
-      const double fl = std::floor(x / b->cfg.dx + 0.5 * (double)N[a]);
-      if (!(fl >= 0.0 && fl < (double)N[a])) inside = false;
-      js.cell[j][a] = (fl >= 0.0 && fl < (double)N[a]) ? (int)fl : -1;
-      js.dir[j][a] = J[j].n[a];
-    }
-    if (!inside) js.cell[j][0] = js.cell[j][1] = js.cell[j][2] = -1;
+    jet_cell_at(J[j].x0, J[j].n, J[j].t_start, t, b->cfg.dx, N, js.cell[j], &js.ell[j]);
+    for (int a = 0; a < 3; ++a) js.dir[j][a] = J[j].n[a];
   }
 }
 
-const double kStageC[3] = {0.0, 1.0, 0.5};
-const double kStageW[3] = {1.0 / 6.0, 1.0 / 6.0, 4.0 / 6.0};
-const double kA[3] = {0.0, 0.75, 1.0 / 3.0};
-const double kB[3] = {1.0, 0.25, 2.0 / 3.0};
 
 // Launches (or records, under capture) `n` steps whose jets sit at chunk rows 0..n-1.
 cudaError_t issue_steps(hydro_batch* b, int n) {
@@ -271,9 +258,9 @@ cudaError_t issue_steps(hydro_batch* b, int n) {
         a.S = b->shadow(st);
         a.Sout = b->shadow(st == 2 ? 0 : st + 1);
       }
-      a.a = kA[st];
-      a.b = kB[st];
-      a.src.wdt_vol = b->cfg.dt * kStageW[st] * vol;
+      a.a = kRK3A[st];
+      a.b = kRK3B[st];
+      a.src.wdt_vol = b->cfg.dt * kRK3W[st] * vol;
       a.jets = jt + ((size_t)s * 3 + st) * b->nev;
       a.reduce_speed = st == 0;
       for (int d = 0; d < 3 && err == cudaSuccess; ++d) {
@@ -531,7 +518,7 @@ hydro_status hydro_batch_step(hydro_batch* b, int32_t nsteps) {
     b->jet_host.resize((size_t)n * 3 * b->nev);
     for (int s = 0; s < n; ++s)
       for (int st = 0; st < 3; ++st) {
-        const double t = b->cfg.t0 + ((double)(b->steps + s) + kStageC[st]) * b->cfg.dt;
+        const double t = b->cfg.t0 + ((double)(b->steps + s) + kRK3C[st]) * b->cfg.dt;
         for (int e = 0; e < b->nev; ++e) fill_jet_stage(b, e, t, b->jet_host[((size_t)s * 3 + st) * b->nev + e]);
       }
     if (cudaMemcpyAsync(b->at(b->lay.jets), b->jet_host.data(), b->jet_host.size() * sizeof(JetStage),

@@ -1,6 +1,7 @@
 // Internal declarations shared by the host API and the kernel translation units.
 #pragma once
 
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 
@@ -79,6 +80,35 @@ inline unsigned long long wait_limit_ns(const hydro_config& c) {
 // the workspace alignment (256 bytes).
 enum : unsigned { kCheckGrid = 1u, kCheckWorkspace = 2u };
 bool config_valid(const hydro_config* c, unsigned what);
+
+// Shu-Osher SSP-RK3 (Sec. 1): stage k evaluates L at t_n + c_k dt on U_k and forms
+// U_{k+1} = a_k U^n + b_k (U_k + dt L(U_k)); w_k is the weight of L(U_k) in the
+// step (the RK3-weighted deposit diagnostics).
+constexpr double kRK3C[3] = {0.0, 1.0, 0.5};
+constexpr double kRK3W[3] = {1.0 / 6.0, 1.0 / 6.0, 4.0 / 6.0};
+constexpr double kRK3A[3] = {0.0, 0.75, 1.0 / 3.0};
+constexpr double kRK3B[3] = {1.0, 0.25, 2.0 / 3.0};
+
+// One jet at stage time t (host, FP64, without floating-point contraction: the
+// library's host code compiles with -ffp-contract=off, so every entry point gets
+// the same bits): path length l = t - t_start, position x = x0 + n l and cell
+// floor(x/dx + N/2) per axis.  Writes the cell, or -1 on every axis when the jet
+// has not started (l < 0) or lies outside the grid, and l; returns whether it
+// deposits.
+inline bool jet_cell_at(const double x0[3], const double n[3], double t_start, double t, double dx, const int N[3],
+                        int cell[3], double* ell) {
+  const double l = t - t_start;
+  *ell = l;
+  bool inside = (l >= 0.0);
+  for (int a = 0; a < 3; ++a) {
+    const double x = x0[a] + n[a] * l;
+    const double fl = std::floor(x / dx + 0.5 * (double)N[a]);
+    if (!(fl >= 0.0 && fl < (double)N[a])) inside = false;
+    cell[a] = (fl >= 0.0 && fl < (double)N[a]) ? (int)fl : -1;
+  }
+  if (!inside) cell[0] = cell[1] = cell[2] = -1;
+  return inside;
+}
 
 // An NVTX range over a scope: names the library's calls and RK3 stages on a
 // profiler's timeline (ncu --nvtx, Nsight Systems); without an attached tool the

@@ -121,10 +121,6 @@ extern "C" hydro_status hydro_step_noalloc(const hydro_config* cfg, void* d_stat
   if (err == cudaSuccess && mixed && nsteps > 0)
     err = hydro::launch_shadow(static_cast<const double*>(d_state), S[0], n, cfg->e_floor, stream);
 
-  static const double kStageC[3] = {0.0, 1.0, 0.5};
-  static const double kStageW[3] = {1.0 / 6.0, 1.0 / 6.0, 4.0 / 6.0};
-  static const double kA[3] = {0.0, 0.75, 1.0 / 3.0};
-  static const double kB[3] = {1.0, 0.25, 2.0 / 3.0};
   void* U[3] = {d_state, U1, U2};
   SweepArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -152,23 +148,13 @@ extern "C" hydro_status hydro_step_noalloc(const hydro_config* cfg, void* d_stat
     const int64_t step = step0 + s;
     err = cudaMemsetAsync(&diag->vmax_bits, 0, sizeof(unsigned long long), stream);
     for (int k = 0; k < 3 && err == cudaSuccess; ++k) {
-      const double t = cfg->t0 + ((double)step + kStageC[k]) * cfg->dt;
+      const double t = cfg->t0 + ((double)step + hydro::kRK3C[k]) * cfg->dt;
       a.jets.n = njet;
       for (int j = 0; j < njet; ++j) {
-        // cell floor(x/dx + N/2) of x = x0 + n (t - t_start), FP64 without contraction
-        const double l = t - jt[j];
-        a.jets.ell[j] = l;
-        bool inside = (l >= 0.0);
-        for (int ax = 0; ax < 3; ++ax) {
-          const double x = jx0[j][ax] + jn[j][ax] * l;
-          const double fl = std::floor(x / cfg->dx + 0.5 * (double)N[ax]);
-          if (!(fl >= 0.0 && fl < (double)N[ax])) inside = false;
-          a.jets.cell[j][ax] = (fl >= 0.0 && fl < (double)N[ax]) ? (int)fl : -1;
-          a.jets.dir[j][ax] = jn[j][ax];
-        }
-        if (!inside) a.jets.cell[j][0] = a.jets.cell[j][1] = a.jets.cell[j][2] = -1;
+        hydro::jet_cell_at(jx0[j], jn[j], jt[j], t, cfg->dx, N, a.jets.cell[j], &a.jets.ell[j]);
+        for (int ax = 0; ax < 3; ++ax) a.jets.dir[j][ax] = jn[j][ax];
       }
-      a.src.wdt_vol = cfg->dt * kStageW[k] * vol;
+      a.src.wdt_vol = cfg->dt * hydro::kRK3W[k] * vol;
       a.U = U[k];
       a.Uout = (k == 2) ? U[0] : U[k + 1];
       if (mixed) {   // stage states as FP32 increments over U0 in the accumulator, as hydro_step
@@ -177,8 +163,8 @@ extern "C" hydro_status hydro_step_noalloc(const hydro_config* cfg, void* d_stat
         a.S = S[k];
         a.Sout = S[k == 2 ? 0 : k + 1];
       }
-      a.a = kA[k];
-      a.b = kB[k];
+      a.a = hydro::kRK3A[k];
+      a.b = hydro::kRK3B[k];
       a.reduce_speed = (k == 0);
       for (int dir = 0; dir < 3 && err == cudaSuccess; ++dir) {
         a.count_floors = (dir == 0);
