@@ -699,10 +699,7 @@ SweepArgs sweep_base(const hydro_adjoint* a) {
   s.dt = g.dt;
   s.e_floor = g.e_floor;
   s.eps = g.weno_eps;
-  s.src.rad = g.k_rad * g.cr_over_cf / (g.hbarc * g.hbarc);
-  s.src.coll = g.k_coll * g.cr_over_cf / g.hbarc;
-  s.src.t4coef = g.hbarc * g.hbarc * g.hbarc / (M_PI * M_PI / 30.0 * g.dof);
-  s.src.inv_vol = 1.0 / (g.dx * g.dx * g.dx);
+  s.src = source_coef(g);
   s.wait_ns = wait_limit_ns(g);
   return s;
 }
@@ -781,8 +778,9 @@ cudaError_t vjp(hydro_adjoint* a, int64_t n, int st, const double* Uk, const flo
   p.coll_per_k = g.cr_over_cf / g.hbarc;
   p.k_rad = g.k_rad;
   p.k_coll = g.k_coll;
-  p.t4coef = g.hbarc * g.hbarc * g.hbarc / (M_PI * M_PI / 30.0 * g.dof);
-  p.inv_vol = 1.0 / (g.dx * g.dx * g.dx);
+  const SourceCoef sc = source_coef(g);
+  p.t4coef = sc.t4coef;
+  p.inv_vol = sc.inv_vol;
   jet_stage(a, g.t0 + ((double)n + kRK3C[st]) * g.dt, p.jets);
   cudaError_t err;
   if (g.precision == HYDRO_MIXED) {

@@ -290,11 +290,8 @@ hydro_status hydro_step(hydro_ctx* c, int32_t nsteps) {
   a.dt = g.dt;
   a.e_floor = g.e_floor;
   a.eps = g.weno_eps;
-  a.src.rad = g.k_rad * g.cr_over_cf / (g.hbarc * g.hbarc);
-  a.src.coll = g.k_coll * g.cr_over_cf / g.hbarc;
-  a.src.t4coef = g.hbarc * g.hbarc * g.hbarc / (M_PI * M_PI / 30.0 * g.dof);
+  a.src = source_coef(g);
   const double vol = g.dx * g.dx * g.dx;
-  a.src.inv_vol = 1.0 / vol;
   a.wait_ns = wait_limit_ns(g);
   a.withhold = g.test_withhold_copies;
   a.check_tighten = g.test_check_tighten;

@@ -215,10 +215,7 @@ BatchArgs base_args(hydro_batch* b) {
   a.wait_ns = wait_limit_ns(g);
   a.withhold = g.test_withhold_copies;
   a.check_tighten = g.test_check_tighten;
-  a.src.rad = g.k_rad * g.cr_over_cf / (g.hbarc * g.hbarc);
-  a.src.coll = g.k_coll * g.cr_over_cf / g.hbarc;
-  a.src.t4coef = g.hbarc * g.hbarc * g.hbarc / (M_PI * M_PI / 30.0 * g.dof);
-  a.src.inv_vol = 1.0 / (g.dx * g.dx * g.dx);
+  a.src = source_coef(g);
   return a;
 }
 

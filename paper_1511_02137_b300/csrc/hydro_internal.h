@@ -45,6 +45,17 @@ struct SourceCoef {
   double wdt_vol; // dt * RK3 weight of the stage * dx^3 (deposit diagnostic)
 };
 
+// The source constants of a configuration (Eq. 3 in natural units converted with
+// hbar c, deposited per cell volume); wdt_vol is per stage and left 0.
+inline SourceCoef source_coef(const hydro_config& g) {
+  SourceCoef s{};
+  s.rad = g.k_rad * g.cr_over_cf / (g.hbarc * g.hbarc);
+  s.coll = g.k_coll * g.cr_over_cf / g.hbarc;
+  s.t4coef = g.hbarc * g.hbarc * g.hbarc / (M_PI * M_PI / 30.0 * g.dof);
+  s.inv_vol = 1.0 / (g.dx * g.dx * g.dx);
+  return s;
+}
+
 // The launch constants in the forms the sweep kernels use, derived on the host
 // (derive_constants) so that no thread converts an FP64 argument: B300 runs FP64
 // arithmetic and FP64<->FP32 conversions at 1/64 of the FP32 rate.

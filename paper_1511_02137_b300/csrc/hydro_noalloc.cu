@@ -136,11 +136,8 @@ extern "C" hydro_status hydro_step_noalloc(const hydro_config* cfg, void* d_stat
   a.dt = cfg->dt;
   a.e_floor = cfg->e_floor;
   a.eps = cfg->weno_eps;
-  a.src.rad = cfg->k_rad * cfg->cr_over_cf / (cfg->hbarc * cfg->hbarc);
-  a.src.coll = cfg->k_coll * cfg->cr_over_cf / cfg->hbarc;
-  a.src.t4coef = cfg->hbarc * cfg->hbarc * cfg->hbarc / (M_PI * M_PI / 30.0 * cfg->dof);
+  a.src = hydro::source_coef(*cfg);
   const double vol = cfg->dx * cfg->dx * cfg->dx;
-  a.src.inv_vol = 1.0 / vol;
   a.wait_ns = hydro::wait_limit_ns(*cfg);   // (plain loads: no TMA copy waits here)
   a.check_tighten = cfg->test_check_tighten;
   const int N[3] = {cfg->nx, cfg->ny, cfg->nz};
