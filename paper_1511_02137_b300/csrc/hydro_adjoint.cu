@@ -691,16 +691,7 @@ SweepArgs sweep_base(const hydro_adjoint* a) {
   std::memset(&s, 0, sizeof(s));
   const hydro_config& g = a->cfg;
   s.diag = a->diag;
-  s.nx = g.nx;
-  s.ny = g.ny;
-  s.nz = g.nz;
-  s.periodic = 0;
-  s.inv_dx = 1.0 / g.dx;
-  s.dt = g.dt;
-  s.e_floor = g.e_floor;
-  s.eps = g.weno_eps;
-  s.src = source_coef(g);
-  s.wait_ns = wait_limit_ns(g);
+  grid_args_from_config(g, s);   // (outflow, no test hooks: the adjoint accepts no other)
   return s;
 }
 

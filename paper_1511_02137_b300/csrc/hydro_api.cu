@@ -282,19 +282,8 @@ hydro_status hydro_step(hydro_ctx* c, int32_t nsteps) {
   a.rhs = c->U(c->lay.rhs);
   a.P = g.precision == HYDRO_FP64 ? c->U(c->lay.prim) : nullptr;
   a.diag = c->diag();
-  a.nx = g.nx;
-  a.ny = g.ny;
-  a.nz = g.nz;
-  a.periodic = g.boundary == HYDRO_PERIODIC;
-  a.inv_dx = 1.0 / g.dx;
-  a.dt = g.dt;
-  a.e_floor = g.e_floor;
-  a.eps = g.weno_eps;
-  a.src = source_coef(g);
+  grid_args_from_config(g, a);
   const double vol = g.dx * g.dx * g.dx;
-  a.wait_ns = wait_limit_ns(g);
-  a.withhold = g.test_withhold_copies;
-  a.check_tighten = g.test_check_tighten;
   cudaError_t err = cudaSuccess;
   for (int32_t s = 0; s < nsteps && err == cudaSuccess; ++s) {
     const int64_t n = c->steps;

@@ -161,6 +161,24 @@ struct GridArgs {
   LaunchConst k;    // filled by the launchers from the fields above
 };
 
+// The fields of a sweep launch that follow from the configuration alone (grid,
+// boundary, step, floor, epsilon, source constants, wait limit, test hooks); the
+// buffers, the diagnostics block and the per-stage fields are the caller's.
+inline void grid_args_from_config(const hydro_config& g, GridArgs& a) {
+  a.nx = g.nx;
+  a.ny = g.ny;
+  a.nz = g.nz;
+  a.periodic = g.boundary == HYDRO_PERIODIC;
+  a.inv_dx = 1.0 / g.dx;
+  a.dt = g.dt;
+  a.e_floor = g.e_floor;
+  a.eps = g.weno_eps;
+  a.src = source_coef(g);
+  a.wait_ns = wait_limit_ns(g);
+  a.withhold = g.test_withhold_copies;
+  a.check_tighten = g.test_check_tighten;
+}
+
 // Arguments of a single-grid sweep launch.
 struct SweepArgs : GridArgs {
   JetStage jets;

@@ -128,18 +128,8 @@ extern "C" hydro_status hydro_step_noalloc(const hydro_config* cfg, void* d_stat
   a.rhs = rhs;
   a.P = prim;
   a.diag = diag;
-  a.nx = cfg->nx;
-  a.ny = cfg->ny;
-  a.nz = cfg->nz;
-  a.periodic = cfg->boundary == HYDRO_PERIODIC;
-  a.inv_dx = 1.0 / cfg->dx;
-  a.dt = cfg->dt;
-  a.e_floor = cfg->e_floor;
-  a.eps = cfg->weno_eps;
-  a.src = hydro::source_coef(*cfg);
+  hydro::grid_args_from_config(*cfg, a);   // (plain loads: no TMA copy and no wait here)
   const double vol = cfg->dx * cfg->dx * cfg->dx;
-  a.wait_ns = hydro::wait_limit_ns(*cfg);   // (plain loads: no TMA copy waits here)
-  a.check_tighten = cfg->test_check_tighten;
   const int N[3] = {cfg->nx, cfg->ny, cfg->nz};
   for (int32_t s = 0; s < nsteps && err == cudaSuccess; ++s) {
     const int64_t step = step0 + s;
